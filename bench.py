@@ -1,0 +1,458 @@
+#!/usr/bin/env python3
+"""Benchmark of the GB300 inverse ray-shooting path (one JSON line on stdout).
+
+Workload (default): 1e4 equal-mass point lenses uniform in a disc (kappa_* = 0.45,
+kappa_c = 0, gamma = 0.4), a 4096 x 4096 regular ray grid, a 1024 x 1024 uint32
+source map.  One step = one magnification map: zero the counts, shoot every ray
+(deflection over all lenses, lens map, binning: one kernel), normalise to mu
+(one kernel).  Metric: lens-ray interactions per second (rays x lenses / time),
+and the same as a fraction of the FP32 peak with the paper's 10 flops per
+interaction.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the FP64 CPU oracle (the reference arm) on bounded row
+samples of the same workload.  Under torchrun every rank shoots its own lens
+realisation of the workload (weak scaling, no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import rs_inputs as ri  # noqa: E402
+
+FLOPS_PER_INTERACTION = 10  # the paper's Appendix A count
+METRIC = "lens-ray interactions/s"
+L2_FLUSH_BYTES = 512 << 20
+
+
+def workload(name: str, seed: int):
+    if name == "n1e4":
+        return ri.n1e4_field(seed=seed)
+    if name == "tiny":
+        return ri.tiny_field(seed=seed)
+    if name == "n1e6":
+        return ri.n1e6_salpeter_field(seed=seed)
+    if name == "n1e8":
+        return ri.n1e8_field(seed=seed)
+    raise SystemExit(f"unknown workload {name}")
+
+
+def workload_config(spec, name):
+    return {
+        "workload": spec.name,
+        "n_lens": spec.n_lens,
+        "masses": "per-lens float32" if spec.masses is not None else "unit (equal-mass kernels)",
+        "kappa_star": round(spec.kappa_star, 6), "kappa_c": spec.kappa_c, "gamma": spec.gamma,
+        "ray_grid": list(spec.grid.n), "map": list(spec.window.npix),
+        "rays_per_step": spec.grid.n_rays,
+        "interactions_per_step": spec.interactions,
+        "l2": "flushed between timed steps (512 MiB write)",
+        "name": name,
+    }
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+# --------------------------------------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi samples (200 ms) of the SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx = float(parts[1])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# --------------------------------------------------------------------------------------------- helpers
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("rs_device.cuh", "rs_shoot.cu"):
+        with open(os.path.join(ROOT, "paper_0905_2453_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(workload_name):
+    """DRAM bytes per launch of the shoot kernel from the committed ncu summary, if still current."""
+    path = os.path.join(ROOT, "profiles", "traffic.txt")
+    if not os.path.exists(path):
+        return None
+    want = kernel_source_hash()
+    with open(path) as fh:
+        for line in fh:
+            parts = line.split("#", 1)[0].split()
+            if len(parts) >= 3 and parts[0] == workload_name and parts[1] == want:
+                return float(parts[2])
+    return None
+
+
+def peaks(device_index: int):
+    import torch
+    props = torch.cuda.get_device_properties(device_index)
+    sms = props.multi_processor_count
+    max_mhz = None
+    mp = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(mp):
+        try:
+            max_mhz = float(json.load(open(mp)).get("sm_max_mhz"))
+        except Exception:
+            max_mhz = None
+    if not max_mhz:
+        max_mhz = 2070.0
+    return sms, max_mhz
+
+
+def fp32_peak_tflops(sms, mhz):
+    # 128 FP32 lanes per SM, one fused multiply-add (2 flops) per lane per clock
+    return sms * 128 * 2 * mhz * 1e6 / 1e12
+
+
+# --------------------------------------------------------------------------------------------- oracle arm
+
+def oracle_rate(spec, target_s: float, max_rows=None):
+    """Time the FP64 oracle on a block of grid rows sized to ~target_s seconds; returns a dict."""
+    import oracle
+    oracle.build()
+    n0 = int(spec.grid.n[0])
+    t = time.perf_counter()
+    oracle.shoot_field(spec, rows=(0, 2))
+    dt = max(time.perf_counter() - t, 1e-4)
+    per_row = dt / 2
+    rows = max(1, min(int(spec.grid.n[1]), int(target_s / per_row)))
+    if max_rows:
+        rows = min(rows, max_rows)
+    j0 = (int(spec.grid.n[1]) - rows) // 2
+    t = time.perf_counter()
+    oracle.shoot_field(spec, rows=(j0, j0 + rows))
+    dt = time.perf_counter() - t
+    inter = rows * n0 * spec.n_lens
+    return {"value": inter / dt, "seconds": dt, "rows": rows, "rays": rows * n0,
+            "interactions": inter, "cores": oracle.num_threads()}
+
+
+def run_reference(args):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return
+    spec = workload(args.workload, seed=0)
+    per_step = min(1.0, 150.0 / max(1, args.steps + args.warmup))
+    calib = oracle_rate(spec, per_step)
+    rows = calib["rows"]
+    import oracle
+    for _ in range(args.warmup):
+        oracle.shoot_field(spec, rows=(0, rows))
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        j0 = (k * rows) % max(1, int(spec.grid.n[1]) - rows + 1)
+        oracle.shoot_field(spec, rows=(j0, j0 + rows))
+    dt = time.perf_counter() - t0
+    inter = rows * int(spec.grid.n[0]) * spec.n_lens * args.steps
+    value = inter / dt
+    sample = (f"{rows} grid rows ({rows * int(spec.grid.n[0])} rays) x {spec.n_lens} lenses per step, "
+              f"FP64 oracle, OpenMP over rays")
+    cfg = workload_config(spec, args.workload)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "interactions/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": cfg,
+        "cpu_baseline": {"value": value, "unit": "interactions/s", "cores": calib["cores"], "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": "interactions/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "gflops_equiv": value * FLOPS_PER_INTERACTION / 1e9,
+    }
+    print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------------------------------------- our arm
+
+def run_ours(args):
+    import torch
+    import paper_0905_2453_gb300 as rs
+
+    world, rank, local = dist_env()
+    if not torch.cuda.is_available():
+        raise SystemExit("CUDA device required for --impl ours")
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=device)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    def max_over_ranks(v):
+        if dist is None:
+            return v
+        t = torch.tensor([v], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    # weak scaling: each rank shoots its own realisation of the workload
+    spec = workload(args.workload, seed=rank)
+    stream = torch.cuda.current_stream(device)
+    field = rs.Field.from_spec(spec, stream)
+    npix = (int(spec.window.npix[1]), int(spec.window.npix[0]))
+    counts = torch.zeros(npix, dtype=torch.int32, device=device)
+    oow = torch.zeros(1, dtype=torch.int64, device=device)
+    mu = torch.empty(npix, dtype=torch.float32, device=device)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=device)
+
+    def step():
+        counts.zero_()
+        oow.zero_()
+        rs.rs_shoot(field.handle, spec.grid, spec.window, counts, oow, stream)
+        rs.rs_magnification(counts, spec.grid, spec.window, mu, stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize(device)
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    barrier()
+    torch.cuda.synchronize(device)
+    clocks.start()
+    t_wall0 = time.perf_counter()
+    for k in range(args.steps):
+        flush.fill_(k)  # evict the previous step's lines from L2 (outside the timed spans)
+        e = ev[k]
+        e[0].record(stream)
+        counts.zero_()
+        oow.zero_()
+        e[1].record(stream)
+        rs.rs_shoot(field.handle, spec.grid, spec.window, counts, oow, stream)
+        e[2].record(stream)
+        rs.rs_magnification(counts, spec.grid, spec.window, mu, stream)
+        e[3].record(stream)
+    torch.cuda.synchronize(device)
+    barrier()
+    wall = time.perf_counter() - t_wall0
+    clk = clocks.stop()
+    step_ms = [e[0].elapsed_time(e[3]) for e in ev]
+    shoot_ms = [e[1].elapsed_time(e[2]) for e in ev]
+    total_s = max_over_ranks(sum(step_ms) / 1e3)
+    shoot_avg_s = max_over_ranks(statistics.mean(shoot_ms) / 1e3)
+    status = field.status()
+    if status != rs.RS_OK:
+        raise SystemExit(f"device reported status {status}")
+    inter_step = spec.interactions
+    value = inter_step * args.steps * world / total_s
+
+    # ---------------- end to end through the public API with host buffers
+    e2e = None
+    if not args.no_e2e:
+        h_xy = torch.from_numpy(np.ascontiguousarray(spec.lens_xy)).pin_memory()
+        h_m = None if spec.masses is None else torch.from_numpy(spec.masses).pin_memory()
+        h_mu = torch.empty(npix, dtype=torch.float32).pin_memory()
+        h_oow = torch.empty(1, dtype=torch.int64).pin_memory()
+
+        def e2e_step():
+            f = rs.Field(h_xy.numpy(), None if h_m is None else h_m.numpy(), spec.kappa_c, spec.gamma, stream)
+            counts.zero_()
+            oow.zero_()
+            rs.rs_shoot(f.handle, spec.grid, spec.window, counts, oow, stream)
+            rs.rs_magnification(counts, spec.grid, spec.window, mu, stream)
+            h_mu.copy_(mu, non_blocking=True)
+            h_oow.copy_(oow, non_blocking=True)
+            torch.cuda.synchronize(device)
+            f.close()
+
+        e2e_step()
+        n_e2e = max(3, min(args.steps, 20))
+        barrier()
+        torch.cuda.synchronize(device)
+        t0 = time.perf_counter()
+        for _ in range(n_e2e):
+            e2e_step()
+        dt = max_over_ranks(time.perf_counter() - t0)
+        h2d = h_xy.numel() * 4 + (0 if h_m is None else h_m.numel() * 4)
+        d2h = h_mu.numel() * 4 + 8
+        e2e = {"value": inter_step * n_e2e * world / dt, "unit": "interactions/s", "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h, "steps": n_e2e,
+               "includes": "field upload + repack, shoot, normalise, D2H of mu and out-of-window, field release"}
+
+    # ---------------- batched maps/s vs plain launches (64 fields)
+    batched = None
+    if not args.no_batch and world == 1:
+        batched = run_batched(rs, torch, device, stream, reps=args.batch_reps)
+
+    # ---------------- CPU baseline (oracle, bounded sample)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        r = oracle_rate(spec, args.cpu_seconds)
+        cpu = {"value": r["value"], "unit": "interactions/s", "cores": r["cores"], "kind": "oracle",
+               "sample": f"{r['rows']} central grid rows ({r['rays']} rays) x {spec.n_lens} lenses, "
+                         f"{r['seconds']:.1f} s, FP64 OpenMP over rays"}
+
+    field.close()
+    if rank != 0:
+        return
+    sms, max_mhz = peaks(local)
+    peak = fp32_peak_tflops(sms, max_mhz)
+    achieved = inter_step * FLOPS_PER_INTERACTION / shoot_avg_s / 1e12
+    med = clk.get("sm_mhz")
+    line = {
+        "metric": METRIC, "value": value, "unit": "interactions/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_s / args.steps * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": workload_config(spec, args.workload),
+        "pct_fp32_peak": 100.0 * achieved / peak,
+        "pct_fp32_peak_at_measured_clock": (100.0 * achieved / fp32_peak_tflops(sms, med)) if med else None,
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": profiled_traffic(args.workload),
+                     "kernel": "shoot_kernel", "kernel_ms": shoot_avg_s * 1e3,
+                     "peak_basis": f"FP32 FMA: {sms} SMs x 128 lanes x 2 flops x {max_mhz:.0f} MHz (max clock); "
+                                   f"10 flops per interaction (paper App. A)"},
+        "clocks": {"sm_mhz": med, "sm_max_mhz": clk.get("sm_max_mhz"), "reasons": clk.get("reasons"),
+                   "samples": clk.get("samples")},
+        "e2e": e2e,
+        "gpu_launches": 2 * args.steps,
+        "cpu_baseline": cpu,
+        "batched": batched,
+        "wall_s_timed_region": wall,
+    }
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def run_batched(rs, torch, device, stream, reps=3):
+    specs = ri.batch_fields(64)
+    fields = [rs.Field.from_spec(s, stream) for s in specs]
+    grids = [s.grid for s in specs]
+    wins = [s.window for s in specs]
+    b = rs.Batch(fields, grids, wins)
+    counts_plain = [torch.zeros_like(c) for c in b.counts]
+    oow_plain = torch.zeros(len(specs), dtype=torch.int64, device=device)
+
+    def plain():
+        for k, f in enumerate(fields):
+            counts_plain[k].zero_()
+        oow_plain.zero_()
+        for k, f in enumerate(fields):
+            rs.rs_shoot(f.handle, grids[k], wins[k], counts_plain[k], oow_plain[k:k + 1], stream)
+
+    b.launch(stream)
+    plain()
+    torch.cuda.synchronize(device)
+    same = all(torch.equal(b.counts[k], counts_plain[k]) for k in range(len(specs))) and \
+        torch.equal(b.out_of_window, oow_plain)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        b.launch(stream)
+    e1.record(stream)
+    torch.cuda.synchronize(device)
+    t_batch = e0.elapsed_time(e1) / 1e3 / reps
+    e0.record(stream)
+    for _ in range(reps):
+        plain()
+    e1.record(stream)
+    torch.cuda.synchronize(device)
+    t_plain = e0.elapsed_time(e1) / 1e3 / reps
+    inter = sum(s.interactions for s in specs)
+    b.close()
+    for f in fields:
+        f.close()
+    return {"workload": "64 Salpeter fields, N* log-uniform [1e2,1e5], rays 1024^2-4096^2, maps 512^2-1024^2",
+            "maps_per_s": len(specs) / t_batch, "plain_maps_per_s": len(specs) / t_plain,
+            "speedup": t_plain / t_batch, "interactions_per_s": inter / t_batch, "bitwise_equal": bool(same),
+            "reps": reps}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=60)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="n1e4")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--batch-reps", type=int, default=3)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        raise SystemExit("--warmup must be >= 3")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,199 @@
+/*
+ * rs.h -- C ABI of the GB300 inverse ray-shooting library (librs.so).
+ *
+ * Method: Thompson, Fluke, Barnes & Barsdell (2009), "Teraflop per second
+ * gravitational lensing ray-shooting using graphics processing units".
+ * For every ray x of a regular image-plane grid the library sums the
+ * many-Schwarzschild deflection directly over all lenses (Eq. 2),
+ *     alpha(x) = sum_i m_i (x - x_i) / |x - x_i|^2,
+ * maps the ray to the source plane with the macro-model lens equation (Eq. 6),
+ *     y1 = (1 - kappa_c - gamma) x1 - alpha1,   y2 = (1 - kappa_c + gamma) x2 - alpha2,
+ * and counts rays per source pixel; the normalised counts are the
+ * magnification map mu_ij = N_ij / N_av (Eq. 4).
+ *
+ * Conventions shared by every entry point
+ *   - Return value: RS_OK (0) or one of the RS_E* codes below.  Nothing is
+ *     thrown across the ABI.  rs_last_error() returns a message for the last
+ *     nonzero status of the calling thread.
+ *   - Pointers named d_* are CUDA device pointers on the current device.
+ *     Pointers named h_* or without prefix are host pointers, unless a flag
+ *     says otherwise.  No entry point frees memory it did not allocate.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Device work is enqueued asynchronously on it; host inputs are
+ *     fully consumed (copied) before the call returns.
+ *   - All kernels run on the device that is current when the call is made;
+ *     a field must be used on the device it was created on.
+ *   - Coordinates are in Einstein radii of a unit mass (the units of Eq. 2).
+ *     Lens and ray coordinates must be finite with |value| <= 1e18.
+ *
+ * Numerics (what the device computes)
+ *   - Ray (i, j) sits at x_k = (float) fma(index_k, spacing_k, origin_k): the
+ *     double fma rounded to float is the ray position.
+ *   - Per lens-ray pair: float32 arithmetic with the hardware approximate
+ *     reciprocal; per ray, partial sums over consecutive groups of 32 lenses
+ *     (in lens index order) are folded into a two-float (hi, lo) accumulator
+ *     with an error-free TwoSum.  The deflection alpha = hi + lo, Eq. 6 and the
+ *     pixel index are then evaluated in double precision.
+ *   - The per-ray arithmetic does not depend on launch configuration, so
+ *     counts are bitwise reproducible and equal between rs_shoot,
+ *     rs_shoot_rows sharding, and the batched path.
+ *   - Binning: u_k = (y_k - lo_k) * (npix_k / (hi_k - lo_k)); a ray is in the
+ *     window iff 0 <= u_k < npix_k on both axes (NaN fails), pixel
+ *     p_k = floor(u_k).  Counts are uint32, row-major [p2][p1].  A ray that
+ *     hits a lens exactly has a non-finite deflection and is out of window.
+ */
+#ifndef RS_H
+#define RS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Status codes. */
+#define RS_OK 0
+#define RS_EINVAL 1     /* invalid argument (NULL pointer, size, non-finite parameter, ...)   */
+#define RS_ENOMEM 2     /* device or host allocation failed                                  */
+#define RS_ECUDA 3      /* a CUDA runtime call failed (message has the CUDA error string)   */
+#define RS_EOVERFLOW 4  /* a size exceeds a documented limit (e.g. >= 2^32 rays per call)   */
+#define RS_ETIMEOUT 5   /* a device-side bounded wait gave up (see rs_field_status)         */
+
+/* Opaque lens field: owns device copies of the lens arrays and the macro-model. */
+typedef struct rs_field* rs_field_t;
+
+/* Regular image-plane ray grid: ray (i, j), 0 <= i < n[0], 0 <= j < n[1], at
+ * x = ((float)fma(i, spacing[0], origin[0]), (float)fma(j, spacing[1], origin[1])).
+ * spacing > 0, all values finite, n >= 0. */
+typedef struct {
+  double origin[2];
+  double spacing[2];
+  int64_t n[2];
+} rs_ray_grid;
+
+/* Source-plane window: half-open [lo, hi) per axis split into npix pixels; hi > lo, npix >= 1. */
+typedef struct {
+  double lo[2];
+  double hi[2];
+  int32_t npix[2];
+} rs_window;
+
+/*
+ * rs_create_field -- upload a lens realisation (Eq. 2 lenses, Eq. 6 macro-model).
+ *   lens_xy  : float[2*n_lens], interleaved (x1, x2) per lens.  May be NULL if n_lens == 0.
+ *   masses   : float[n_lens] (finite, >= 0), or NULL for unit masses.  With NULL the
+ *              equal-mass kernels are used (no mass is stored or read, Section 3.2).
+ *   n_lens   : >= 0 and < 2^31.  n_lens == 0 gives the undeflected (macro-only) map.
+ *   kappa_c  : smooth convergence sigma_c of Eq. 6; gamma: external shear (finite).
+ *   inputs_on_device : 0 = lens_xy/masses are host pointers, 1 = device pointers.
+ *   stream   : stream for the upload and repacking kernels.
+ *   out      : receives the new field.  The field keeps its own copies; the
+ *              inputs may be freed once the call returns (host) or once the
+ *              stream has passed this point (device inputs).
+ * Errors: RS_EINVAL (bad argument), RS_ENOMEM, RS_ECUDA.
+ */
+int rs_create_field(const float* lens_xy, const float* masses, int64_t n_lens, double kappa_c,
+                    double gamma, int inputs_on_device, void* stream, rs_field_t* out);
+
+/* rs_destroy_field -- release a field (synchronises its device first).  NULL is a no-op. */
+int rs_destroy_field(rs_field_t f);
+
+/* Number of lenses, and whether the field carries per-lens masses (1) or unit masses (0). */
+int rs_field_info(rs_field_t f, int64_t* n_lens, int* has_masses);
+
+/*
+ * rs_shoot -- shoot every ray of grid g through field f and ACCUMULATE (+=) the
+ * binned counts into d_counts (uint32[npix[1]][npix[0]], device) and the number
+ * of rays that miss the window into *d_out_of_window (uint64, device; may be NULL).
+ * The caller zeroes the buffers before the first call.  Method: Eq. 2 and Eq. 6
+ * per ray, binning as in the header comment, counts for Eq. 4.
+ * Errors: RS_EINVAL, RS_EOVERFLOW (n[0]*n[1] >= 2^32), RS_ECUDA (launch failure).
+ */
+int rs_shoot(rs_field_t f, const rs_ray_grid* g, const rs_window* w, uint32_t* d_counts,
+             uint64_t* d_out_of_window, void* stream);
+
+/*
+ * rs_shoot_rows -- as rs_shoot for grid rows j in [row_begin, row_end) only.
+ * Shooting a partition of the rows into the same buffers gives exactly the
+ * counts of one rs_shoot (ray positions depend only on (i, j)): the basis for
+ * sharding a map over calls, devices or restarts (checkpoint = counts + next row).
+ */
+int rs_shoot_rows(rs_field_t f, const rs_ray_grid* g, int64_t row_begin, int64_t row_end,
+                  const rs_window* w, uint32_t* d_counts, uint64_t* d_out_of_window, void* stream);
+
+/*
+ * rs_trace -- source positions of listed rays, for checks against a reference.
+ *   d_ray_ij : int64[2*k] device, (i, j) per ray (each within the grid).
+ *   d_y      : double[2*k] device, receives (y1, y2) per ray (Eq. 6).
+ *   d_alpha  : double[2*k] device or NULL, receives (alpha1, alpha2) per ray (Eq. 2).
+ * The per-ray arithmetic is the one rs_shoot uses, bit for bit.
+ */
+int rs_trace(rs_field_t f, const rs_ray_grid* g, const int64_t* d_ray_ij, int64_t k, double* d_y,
+             double* d_alpha, void* stream);
+
+/*
+ * rs_magnification -- Eq. 4: d_mu[p] = d_counts[p] / N_av (float, device), with
+ * N_av = ((hi0-lo0)/npix0 * (hi1-lo1)/npix1) / (spacing0 * spacing1), the number
+ * of rays a pixel receives without lensing.
+ */
+int rs_magnification(const uint32_t* d_counts, const rs_ray_grid* g, const rs_window* w, float* d_mu,
+                     void* stream);
+
+/*
+ * Batched shooting of many independent fields in one persistent launch
+ * (many realisations for a statistical light-curve study, Section 4).
+ *
+ * rs_batch_create -- plan a batch.  fields/grids/windows: host arrays of
+ *   n_fields entries; d_counts: host array of n_fields device pointers (each
+ *   uint32[npix1][npix0]); d_out_of_window: device uint64[n_fields] or NULL.
+ *   The plan copies all descriptors to the device, orders the work items
+ *   (field, ray tile) by decreasing cost, and captures one CUDA graph that
+ *   zeroes the counts and the work counter and runs the persistent kernel.
+ *   The fields must outlive the plan.  Unlike rs_shoot, the graph ZEROES the
+ *   counts and out-of-window counters on every launch.
+ * rs_batch_launch -- replay the plan's graph on `stream`.
+ * rs_batch_destroy -- release the plan (synchronises first).  NULL is a no-op.
+ * rs_shoot_batch -- create + launch + destroy in one call (synchronous).
+ */
+typedef struct rs_batch* rs_batch_t;
+
+int rs_batch_create(int n_fields, const rs_field_t* fields, const rs_ray_grid* grids,
+                    const rs_window* windows, uint32_t* const* d_counts, uint64_t* d_out_of_window,
+                    rs_batch_t* out);
+int rs_batch_launch(rs_batch_t b, void* stream);
+int rs_batch_destroy(rs_batch_t b);
+int rs_shoot_batch(int n_fields, const rs_field_t* fields, const rs_ray_grid* grids,
+                   const rs_window* windows, uint32_t* const* d_counts, uint64_t* d_out_of_window,
+                   void* stream);
+
+/*
+ * rs_field_status -- synchronise the field's device and report whether a
+ * kernel that used it gave up a bounded wait: *status = RS_OK or RS_ETIMEOUT.
+ * clear != 0 resets the flag.
+ */
+int rs_field_status(rs_field_t f, int clear, int* status);
+
+/*
+ * Launch shapes.  The library carries kernels for several (threads per CTA,
+ * rays per thread) shapes; all compute bitwise identical results, so the
+ * choice only affects speed.  rs_set_launch_config selects the shape used by
+ * rs_shoot / rs_shoot_rows (and, for has_masses = 1, by batches planned
+ * afterwards) for fields without (has_masses = 0) or with per-lens masses.
+ * rs_launch_configs lists the compiled shapes: up to `cap` (block, rpt)
+ * pairs into `pairs` (int[2*cap]); returns the number available via *count.
+ */
+int rs_set_launch_config(int has_masses, int block, int rays_per_thread);
+int rs_get_launch_config(int has_masses, int* block, int* rays_per_thread);
+int rs_launch_configs(int* pairs, int cap, int* count);
+
+/* Thread-local message for the last nonzero status returned on this thread. */
+const char* rs_last_error(void);
+
+/* Library version string. */
+const char* rs_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RS_H */

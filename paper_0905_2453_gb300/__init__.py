@@ -1,0 +1,412 @@
+"""Python binding of librs.so, the GB300 inverse ray-shooting library.
+
+Thin argument marshalling over the C ABI declared in ``include/rs.h``: the
+functions below carry the C names (``rs_create_field``, ``rs_shoot``, ...)
+and take torch CUDA tensors for device buffers.  Every step of the method runs
+in the library's CUDA kernels; there is no CPU fallback, and importing this
+package fails if ``librs.so`` is missing (build it with ``build.build()`` or
+``__graft_entry__.build()``).
+
+Method (Thompson, Fluke, Barnes & Barsdell 2009): direct many-Schwarzschild
+deflection (Eq. 2) for every ray of a regular image-plane grid, the
+macro-model lens equation with smooth convergence and shear (Eq. 6), binning
+into source-plane counts and mu = N / N_av (Eq. 4).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import torch
+
+from . import build as _build
+
+__all__ = [
+    "RS_OK", "RS_EINVAL", "RS_ENOMEM", "RS_ECUDA", "RS_EOVERFLOW", "RS_ETIMEOUT", "RSError",
+    "RayGrid", "Window", "Field", "Batch", "load", "lib_path",
+    "rs_create_field", "rs_destroy_field", "rs_field_info", "rs_shoot", "rs_shoot_rows", "rs_trace",
+    "rs_magnification", "rs_batch_create", "rs_batch_launch", "rs_batch_destroy", "rs_shoot_batch",
+    "rs_field_status", "rs_last_error", "rs_version", "rs_set_launch_config", "rs_get_launch_config",
+    "rs_launch_configs", "EXPORTED_SYMBOLS",
+]
+
+RS_OK, RS_EINVAL, RS_ENOMEM, RS_ECUDA, RS_EOVERFLOW, RS_ETIMEOUT = 0, 1, 2, 3, 4, 5
+_NAMES = {0: "RS_OK", 1: "RS_EINVAL", 2: "RS_ENOMEM", 3: "RS_ECUDA", 4: "RS_EOVERFLOW", 5: "RS_ETIMEOUT"}
+
+EXPORTED_SYMBOLS = (
+    "rs_create_field", "rs_destroy_field", "rs_field_info", "rs_shoot", "rs_shoot_rows", "rs_trace",
+    "rs_magnification", "rs_batch_create", "rs_batch_launch", "rs_batch_destroy", "rs_shoot_batch",
+    "rs_field_status", "rs_last_error", "rs_version", "rs_set_launch_config", "rs_get_launch_config",
+    "rs_launch_configs",
+)
+
+
+class RSError(RuntimeError):
+    def __init__(self, code: int, where: str, msg: str):
+        super().__init__(f"{where}: {_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+class _Grid(ctypes.Structure):
+    _fields_ = [("origin", ctypes.c_double * 2), ("spacing", ctypes.c_double * 2), ("n", ctypes.c_int64 * 2)]
+
+
+class _Window(ctypes.Structure):
+    _fields_ = [("lo", ctypes.c_double * 2), ("hi", ctypes.c_double * 2), ("npix", ctypes.c_int32 * 2)]
+
+
+@dataclass
+class RayGrid:
+    """Ray (i, j) at ((float)fma(i, spacing[0], origin[0]), (float)fma(j, spacing[1], origin[1]))."""
+    origin: tuple
+    spacing: tuple
+    n: tuple
+
+    @property
+    def n_rays(self) -> int:
+        return int(self.n[0]) * int(self.n[1])
+
+
+@dataclass
+class Window:
+    """Half-open source-plane window [lo, hi) per axis with npix pixels per axis."""
+    lo: tuple
+    hi: tuple
+    npix: tuple
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+_lib = None
+
+
+def load():
+    """Load librs.so (raises if it has not been built: there is no fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if not os.path.exists(path):
+        raise ImportError(f"librs.so not found at {path}; build it first (paper_0905_2453_gb300.build.build())")
+    lib = ctypes.CDLL(path)
+    vp, i64, i32, dbl = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_double
+    gp, wp = ctypes.POINTER(_Grid), ctypes.POINTER(_Window)
+    sig = {
+        "rs_create_field": ([vp, vp, i64, dbl, dbl, i32, vp, ctypes.POINTER(vp)], i32),
+        "rs_destroy_field": ([vp], i32),
+        "rs_field_info": ([vp, ctypes.POINTER(i64), ctypes.POINTER(i32)], i32),
+        "rs_shoot": ([vp, gp, wp, vp, vp, vp], i32),
+        "rs_shoot_rows": ([vp, gp, i64, i64, wp, vp, vp, vp], i32),
+        "rs_trace": ([vp, gp, vp, i64, vp, vp, vp], i32),
+        "rs_magnification": ([vp, gp, wp, vp, vp], i32),
+        "rs_batch_create": ([i32, vp, vp, vp, vp, vp, ctypes.POINTER(vp)], i32),
+        "rs_batch_launch": ([vp, vp], i32),
+        "rs_batch_destroy": ([vp], i32),
+        "rs_shoot_batch": ([i32, vp, vp, vp, vp, vp, vp], i32),
+        "rs_field_status": ([vp, i32, ctypes.POINTER(i32)], i32),
+        "rs_last_error": ([], ctypes.c_char_p),
+        "rs_version": ([], ctypes.c_char_p),
+        "rs_set_launch_config": ([i32, i32, i32], i32),
+        "rs_get_launch_config": ([i32, ctypes.POINTER(i32), ctypes.POINTER(i32)], i32),
+        "rs_launch_configs": ([ctypes.POINTER(i32), i32, ctypes.POINTER(i32)], i32),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
+    _lib = lib
+    return lib
+
+
+def _check(rc: int, where: str):
+    if rc != RS_OK:
+        raise RSError(rc, where, load().rs_last_error().decode(errors="replace"))
+
+
+def _cgrid(g) -> _Grid:
+    s = _Grid()
+    for k in range(2):
+        s.origin[k] = float(g.origin[k])
+        s.spacing[k] = float(g.spacing[k])
+        s.n[k] = int(g.n[k])
+    return s
+
+
+def _cwin(w) -> _Window:
+    s = _Window()
+    for k in range(2):
+        s.lo[k] = float(w.lo[k])
+        s.hi[k] = float(w.hi[k])
+        s.npix[k] = int(w.npix[k])
+    return s
+
+
+def _stream(stream) -> int:
+    if stream is None:
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, torch.cuda.Stream):
+        return stream.cuda_stream
+    return int(stream)
+
+
+_COUNT_DTYPES = (torch.int32, torch.uint32)
+_OOW_DTYPES = (torch.int64, torch.uint64)
+
+
+def _dptr(t, dtype, name, numel=None):
+    """Device pointer of a contiguous CUDA tensor of the given dtype (or tuple of dtypes)."""
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    ok = t.dtype in dtype if isinstance(dtype, tuple) else t.dtype == dtype
+    if not ok or not t.is_contiguous():
+        raise TypeError(f"{name} must be a contiguous {dtype} tensor (got {t.dtype})")
+    if numel is not None and t.numel() < numel:
+        raise ValueError(f"{name} holds {t.numel()} elements, needs {numel}")
+    return t.data_ptr()
+
+
+# ------------------------------------------------------------------------------------------- C names
+
+def rs_version() -> str:
+    return load().rs_version().decode()
+
+
+def rs_last_error() -> str:
+    return load().rs_last_error().decode(errors="replace")
+
+
+def rs_create_field(lens_xy, masses, kappa_c: float, gamma: float, stream=None) -> int:
+    """Create a field from lens positions [n, 2] and masses [n] (or None for unit masses).
+
+    Host inputs (numpy arrays / CPU tensors) are copied by the library; CUDA
+    tensors are read on the device.  Returns the opaque handle (int).
+    """
+    lib = load()
+    on_dev = isinstance(lens_xy, torch.Tensor) and lens_xy.is_cuda
+    keep = []
+    if on_dev:
+        xy = lens_xy.detach().to(torch.float32).contiguous()
+        n = xy.numel() // 2
+        m = None if masses is None else masses.detach().to(device=xy.device, dtype=torch.float32).contiguous()
+        keep += [xy, m]
+        pxy, pm = xy.data_ptr(), (None if m is None else m.data_ptr())
+    else:
+        import numpy as np
+        xy = np.ascontiguousarray(np.asarray(lens_xy.cpu() if isinstance(lens_xy, torch.Tensor) else lens_xy,
+                                             dtype=np.float32))
+        n = xy.size // 2
+        m = None if masses is None else np.ascontiguousarray(
+            np.asarray(masses.cpu() if isinstance(masses, torch.Tensor) else masses, dtype=np.float32))
+        keep += [xy, m]
+        pxy = xy.ctypes.data if n > 0 else None
+        pm = None if m is None else m.ctypes.data
+    if m is not None and (m.numel() if on_dev else m.size) != n:
+        raise ValueError("masses length differs from lens count")
+    h = ctypes.c_void_p()
+    st = _stream(stream)
+    rc = lib.rs_create_field(pxy, pm, n, float(kappa_c), float(gamma), 1 if on_dev else 0, st, ctypes.byref(h))
+    _check(rc, "rs_create_field")
+    if on_dev:
+        torch.cuda.ExternalStream(st).synchronize()  # device inputs may be freed after return
+    return h.value
+
+
+def rs_destroy_field(handle: int) -> None:
+    _check(load().rs_destroy_field(handle), "rs_destroy_field")
+
+
+def rs_field_info(handle: int):
+    n = ctypes.c_int64()
+    hm = ctypes.c_int()
+    _check(load().rs_field_info(handle, ctypes.byref(n), ctypes.byref(hm)), "rs_field_info")
+    return int(n.value), bool(hm.value)
+
+
+def rs_shoot(handle: int, grid, window, counts: torch.Tensor, out_of_window: torch.Tensor = None, stream=None):
+    """Accumulate the binned counts of every ray of ``grid`` into ``counts`` (uint32 [npix1, npix0])."""
+    npx = int(window.npix[0]) * int(window.npix[1])
+    pc = _dptr(counts, _COUNT_DTYPES, "counts", npx)
+    po = _dptr(out_of_window, _OOW_DTYPES, "out_of_window", 1)
+    g, w = _cgrid(grid), _cwin(window)
+    _check(load().rs_shoot(handle, ctypes.byref(g), ctypes.byref(w), pc, po, _stream(stream)), "rs_shoot")
+
+
+def rs_shoot_rows(handle: int, grid, row_begin: int, row_end: int, window, counts, out_of_window=None, stream=None):
+    npx = int(window.npix[0]) * int(window.npix[1])
+    pc = _dptr(counts, _COUNT_DTYPES, "counts", npx)
+    po = _dptr(out_of_window, _OOW_DTYPES, "out_of_window", 1)
+    g, w = _cgrid(grid), _cwin(window)
+    _check(load().rs_shoot_rows(handle, ctypes.byref(g), int(row_begin), int(row_end), ctypes.byref(w), pc, po,
+                                _stream(stream)), "rs_shoot_rows")
+
+
+def rs_trace(handle: int, grid, ray_ij: torch.Tensor, y: torch.Tensor, alpha: torch.Tensor = None, stream=None):
+    """Source positions (float64 [k, 2]) of listed rays (int64 [k, 2]) into ``y`` (and ``alpha``)."""
+    k = ray_ij.numel() // 2
+    pij = _dptr(ray_ij, torch.int64, "ray_ij")
+    py = _dptr(y, torch.float64, "y", 2 * k)
+    pa = _dptr(alpha, torch.float64, "alpha", 2 * k) if alpha is not None else None
+    g = _cgrid(grid)
+    _check(load().rs_trace(handle, ctypes.byref(g), pij, k, py, pa, _stream(stream)), "rs_trace")
+
+
+def rs_magnification(counts: torch.Tensor, grid, window, mu: torch.Tensor, stream=None):
+    npx = int(window.npix[0]) * int(window.npix[1])
+    pc = _dptr(counts, _COUNT_DTYPES, "counts", npx)
+    pm = _dptr(mu, torch.float32, "mu", npx)
+    g, w = _cgrid(grid), _cwin(window)
+    _check(load().rs_magnification(pc, ctypes.byref(g), ctypes.byref(w), pm, _stream(stream)), "rs_magnification")
+
+
+def _batch_arrays(handles, grids, windows, counts_list, oow):
+    n = len(handles)
+    if not (len(grids) == len(windows) == len(counts_list) == n):
+        raise ValueError("fields, grids, windows and counts must have the same length")
+    H = (ctypes.c_void_p * n)(*handles)
+    G = (_Grid * n)(*[_cgrid(g) for g in grids])
+    W = (_Window * n)(*[_cwin(w) for w in windows])
+    C = (ctypes.c_void_p * n)(*[_dptr(c, _COUNT_DTYPES, f"counts[{k}]",
+                                      int(windows[k].npix[0]) * int(windows[k].npix[1]))
+                                for k, c in enumerate(counts_list)])
+    po = _dptr(oow, _OOW_DTYPES, "out_of_window", n)
+    return n, H, G, W, C, po
+
+
+def rs_batch_create(handles, grids, windows, counts_list, out_of_window=None) -> int:
+    n, H, G, W, C, po = _batch_arrays(handles, grids, windows, counts_list, out_of_window)
+    b = ctypes.c_void_p()
+    _check(load().rs_batch_create(n, H, G, W, C, po, ctypes.byref(b)), "rs_batch_create")
+    return b.value
+
+
+def rs_batch_launch(batch: int, stream=None):
+    _check(load().rs_batch_launch(batch, _stream(stream)), "rs_batch_launch")
+
+
+def rs_batch_destroy(batch: int):
+    _check(load().rs_batch_destroy(batch), "rs_batch_destroy")
+
+
+def rs_shoot_batch(handles, grids, windows, counts_list, out_of_window=None, stream=None):
+    n, H, G, W, C, po = _batch_arrays(handles, grids, windows, counts_list, out_of_window)
+    _check(load().rs_shoot_batch(n, H, G, W, C, po, _stream(stream)), "rs_shoot_batch")
+
+
+def rs_field_status(handle: int, clear: bool = False) -> int:
+    st = ctypes.c_int()
+    _check(load().rs_field_status(handle, 1 if clear else 0, ctypes.byref(st)), "rs_field_status")
+    return int(st.value)
+
+
+def rs_set_launch_config(has_masses: bool, block: int, rays_per_thread: int) -> None:
+    _check(load().rs_set_launch_config(1 if has_masses else 0, int(block), int(rays_per_thread)),
+           "rs_set_launch_config")
+
+
+def rs_get_launch_config(has_masses: bool):
+    b, r = ctypes.c_int(), ctypes.c_int()
+    _check(load().rs_get_launch_config(1 if has_masses else 0, ctypes.byref(b), ctypes.byref(r)),
+           "rs_get_launch_config")
+    return int(b.value), int(r.value)
+
+
+def rs_launch_configs():
+    cnt = ctypes.c_int()
+    buf = (ctypes.c_int * 64)()
+    _check(load().rs_launch_configs(buf, 32, ctypes.byref(cnt)), "rs_launch_configs")
+    return [(buf[2 * i], buf[2 * i + 1]) for i in range(min(cnt.value, 32))]
+
+
+# ------------------------------------------------------------------------------------------- objects
+
+class Field:
+    """Owning wrapper of an rs_field handle."""
+
+    def __init__(self, lens_xy, masses=None, kappa_c: float = 0.0, gamma: float = 0.0, stream=None):
+        self.handle = rs_create_field(lens_xy, masses, kappa_c, gamma, stream)
+        self.kappa_c, self.gamma = float(kappa_c), float(gamma)
+
+    @classmethod
+    def from_spec(cls, spec, stream=None):
+        """From any object with lens_xy, masses, kappa_c and gamma attributes."""
+        return cls(spec.lens_xy, spec.masses, spec.kappa_c, spec.gamma, stream)
+
+    def info(self):
+        return rs_field_info(self.handle)
+
+    def shoot(self, grid, window, counts=None, out_of_window=None, stream=None, rows=None):
+        dev = torch.device("cuda", torch.cuda.current_device())
+        if counts is None:
+            counts = torch.zeros((int(window.npix[1]), int(window.npix[0])), dtype=torch.int32, device=dev)
+        if rows is None:
+            rs_shoot(self.handle, grid, window, counts, out_of_window, stream)
+        else:
+            rs_shoot_rows(self.handle, grid, rows[0], rows[1], window, counts, out_of_window, stream)
+        return counts
+
+    def trace(self, grid, ray_ij, with_alpha=False, stream=None):
+        dev = torch.device("cuda", torch.cuda.current_device())
+        ij = torch.as_tensor(ray_ij, dtype=torch.int64).reshape(-1, 2).to(dev).contiguous()
+        y = torch.empty((ij.shape[0], 2), dtype=torch.float64, device=dev)
+        a = torch.empty_like(y) if with_alpha else None
+        rs_trace(self.handle, grid, ij, y, a, stream)
+        return (y, a) if with_alpha else y
+
+    def status(self, clear=False) -> int:
+        return rs_field_status(self.handle, clear)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            rs_destroy_field(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def magnification(counts, grid, window, stream=None):
+    mu = torch.empty(counts.shape, dtype=torch.float32, device=counts.device)
+    rs_magnification(counts, grid, window, mu, stream)
+    return mu
+
+
+class Batch:
+    """A planned batch of fields (persistent kernel captured in a CUDA graph)."""
+
+    def __init__(self, fields, grids, windows, counts_list=None, out_of_window=None):
+        dev = torch.device("cuda", torch.cuda.current_device())
+        if counts_list is None:
+            counts_list = [torch.zeros((int(w.npix[1]), int(w.npix[0])), dtype=torch.int32, device=dev)
+                           for w in windows]
+        if out_of_window is None:
+            out_of_window = torch.zeros(len(fields), dtype=torch.int64, device=dev)
+        self.fields = list(fields)
+        self.counts = counts_list
+        self.out_of_window = out_of_window
+        self.handle = rs_batch_create([f.handle for f in self.fields], grids, windows, counts_list, out_of_window)
+
+    def launch(self, stream=None):
+        rs_batch_launch(self.handle, stream)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            rs_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# Load eagerly so that a missing library fails at import time, not at first use.
+load()

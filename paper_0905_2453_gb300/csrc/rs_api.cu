@@ -1,0 +1,556 @@
+// C-ABI layer of librs.so: argument validation, field management, launch shape
+// selection, the batched plan (CUDA graph), and the small elementwise kernels
+// (lens repacking, Eq. 4 normalisation).
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/rs.h"
+#include "rs_internal.h"
+
+using rsdev::FieldDev;
+using rsdev::ShootDesc;
+
+struct rs_field {
+  int device;
+  int64_t n_lens;
+  int64_t n_pad;
+  float4* lens4;
+  float2* mass2;
+  unsigned int* status;
+  double kappa_c, gamma;
+  FieldDev dev;
+};
+
+struct rs_batch {
+  int device;
+  int n_fields;
+  int n_items;
+  int cfg;
+  int grid;
+  ShootDesc* d_descs;
+  int2* d_items;
+  int* d_counter;
+  cudaGraph_t graph;
+  cudaGraphExec_t exec;
+};
+
+namespace {
+
+thread_local std::string g_err;
+// Launch shape per mass mode (index 0: unit masses, 1: per-lens masses).
+int g_cfg[2] = {rsint::kDefaultCfg, rsint::kDefaultCfg};
+
+int fail(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return code;
+}
+
+int cuda_fail(cudaError_t e, const char* what) {
+  return fail(e == cudaErrorMemoryAllocation ? RS_ENOMEM : RS_ECUDA, "%s: %s (%s)", what, cudaGetErrorName(e),
+              cudaGetErrorString(e));
+}
+
+constexpr double kCoordLimit = 1e18;
+
+bool finite_coord(double v) { return std::isfinite(v) && std::fabs(v) <= kCoordLimit; }
+
+int check_grid(const rs_ray_grid* g) {
+  if (!g) return fail(RS_EINVAL, "ray grid is NULL");
+  for (int k = 0; k < 2; ++k) {
+    if (!finite_coord(g->origin[k])) return fail(RS_EINVAL, "grid origin[%d] not finite or beyond 1e18", k);
+    if (!(std::isfinite(g->spacing[k]) && g->spacing[k] > 0.0))
+      return fail(RS_EINVAL, "grid spacing[%d] must be finite and > 0", k);
+    if (g->n[k] < 0) return fail(RS_EINVAL, "grid n[%d] < 0", k);
+    const double far = g->origin[k] + (double)(g->n[k] > 0 ? g->n[k] - 1 : 0) * g->spacing[k];
+    if (!finite_coord(far)) return fail(RS_EINVAL, "grid extent along axis %d beyond 1e18", k);
+  }
+  return RS_OK;
+}
+
+int check_window(const rs_window* w) {
+  if (!w) return fail(RS_EINVAL, "window is NULL");
+  for (int k = 0; k < 2; ++k) {
+    if (!(std::isfinite(w->lo[k]) && std::isfinite(w->hi[k]) && w->hi[k] > w->lo[k]))
+      return fail(RS_EINVAL, "window axis %d: need finite lo < hi", k);
+    if (w->npix[k] < 1) return fail(RS_EINVAL, "window npix[%d] < 1", k);
+    const double sc = (double)w->npix[k] / (w->hi[k] - w->lo[k]);
+    if (!(std::isfinite(sc) && sc > 0.0)) return fail(RS_EINVAL, "window axis %d: degenerate pixel scale", k);
+  }
+  if ((int64_t)w->npix[0] * (int64_t)w->npix[1] > (int64_t)1 << 40)
+    return fail(RS_EOVERFLOW, "window has more than 2^40 pixels");
+  return RS_OK;
+}
+
+struct DeviceGuard {
+  int prev = -1;
+  bool changed = false;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) {
+      changed = cudaSetDevice(dev) == cudaSuccess;
+    }
+  }
+  ~DeviceGuard() {
+    if (changed) cudaSetDevice(prev);
+  }
+};
+
+int check_field_device(const rs_field* f) {
+  int cur = -1;
+  cudaError_t e = cudaGetDevice(&cur);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+  if (cur != f->device) return fail(RS_EINVAL, "field lives on device %d but device %d is current", f->device, cur);
+  return RS_OK;
+}
+
+__global__ void pack_lenses_kernel(const float* __restrict__ xy, const float* __restrict__ m, int64_t n, int64_t n_pad,
+                                   float4* __restrict__ lens4, float2* __restrict__ mass2) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_pad; i += (int64_t)gridDim.x * blockDim.x) {
+    if (i < n) {
+      const float2 p = reinterpret_cast<const float2*>(xy)[i];
+      lens4[i] = make_float4(p.x, p.x, p.y, p.y);
+      if (mass2) {
+        const float mi = m[i];
+        mass2[i] = make_float2(mi, mi);
+      }
+    } else {
+      lens4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (mass2) mass2[i] = make_float2(0.f, 0.f);
+    }
+  }
+}
+
+// Eq. 4: mu = N * (1 / N_av), float32; uint4/float4 vectors when aligned.
+__global__ void magnification_kernel(const uint32_t* __restrict__ c, float* __restrict__ mu, int64_t n, float inv_nav,
+                                     int vec) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  int64_t done = 0;
+  if (vec) {
+    const int64_t nv = n / 4;
+    const uint4* c4 = reinterpret_cast<const uint4*>(c);
+    float4* m4 = reinterpret_cast<float4*>(mu);
+    for (int64_t i = t0; i < nv; i += stride) {
+      const uint4 v = c4[i];
+      m4[i] = make_float4((float)v.x * inv_nav, (float)v.y * inv_nav, (float)v.z * inv_nav, (float)v.w * inv_nav);
+    }
+    done = nv * 4;
+  }
+  for (int64_t i = done + t0; i < n; i += stride) mu[i] = (float)c[i] * inv_nav;
+}
+
+int num_sms(int device) {
+  int v = 0;
+  if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) return 1;
+  return v > 0 ? v : 1;
+}
+
+int fill_desc(const rs_field* f, const rs_ray_grid* g, int64_t row_begin, int64_t row_end, const rs_window* w,
+              uint32_t* d_counts, uint64_t* d_oow, ShootDesc* d) {
+  const int64_t rows = row_end - row_begin;
+  const int64_t n_rays = rows * g->n[0];
+  if (g->n[0] > 0 && rows > 0 && (rows > ((int64_t)1 << 32) / g->n[0] || n_rays >= ((int64_t)1 << 32)))
+    return fail(RS_EOVERFLOW, "a call shoots at most 2^32 - 1 rays (got %lld rows x %lld)", (long long)rows,
+                (long long)g->n[0]);
+  memset(d, 0, sizeof(*d));
+  d->f = f->dev;
+  d->or0 = g->origin[0];
+  d->or1 = g->origin[1];
+  d->sp0 = g->spacing[0];
+  d->sp1 = g->spacing[1];
+  d->n0 = g->n[0];
+  d->j_begin = row_begin;
+  d->n_rays = n_rays;
+  d->lo0 = w->lo[0];
+  d->lo1 = w->lo[1];
+  d->sc0 = (double)w->npix[0] / (w->hi[0] - w->lo[0]);
+  d->sc1 = (double)w->npix[1] / (w->hi[1] - w->lo[1]);
+  d->np0 = w->npix[0];
+  d->np1 = w->npix[1];
+  d->counts = d_counts;
+  d->oow = reinterpret_cast<unsigned long long*>(d_oow);
+  return RS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* rs_last_error(void) { return g_err.c_str(); }
+
+const char* rs_version(void) { return "rs-gb300 0.1 (sm_103a)"; }
+
+int rs_set_launch_config(int has_masses, int block, int rays_per_thread) {
+  const int c = rsint::find_cfg(block, rays_per_thread);
+  if (c < 0) return fail(RS_EINVAL, "no compiled launch shape (%d threads, %d rays/thread)", block, rays_per_thread);
+  g_cfg[has_masses ? 1 : 0] = c;
+  return RS_OK;
+}
+
+int rs_get_launch_config(int has_masses, int* block, int* rays_per_thread) {
+  const int c = g_cfg[has_masses ? 1 : 0];
+  if (block) *block = rsint::kCfgs[c].block;
+  if (rays_per_thread) *rays_per_thread = rsint::kCfgs[c].rpt;
+  return RS_OK;
+}
+
+int rs_launch_configs(int* pairs, int cap, int* count) {
+  if (count) *count = rsint::kNumCfg;
+  for (int i = 0; i < rsint::kNumCfg && i < cap && pairs; ++i) {
+    pairs[2 * i] = rsint::kCfgs[i].block;
+    pairs[2 * i + 1] = rsint::kCfgs[i].rpt;
+  }
+  return RS_OK;
+}
+
+int rs_create_field(const float* lens_xy, const float* masses, int64_t n_lens, double kappa_c, double gamma,
+                    int inputs_on_device, void* stream, rs_field_t* out) {
+  if (!out) return fail(RS_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (n_lens < 0) return fail(RS_EINVAL, "n_lens < 0");
+  if (n_lens >= ((int64_t)1 << 31) - rsdev::kLensPad) return fail(RS_EOVERFLOW, "n_lens must be < 2^31 - 1024");
+  if (n_lens > 0 && !lens_xy) return fail(RS_EINVAL, "lens_xy is NULL");
+  if (!std::isfinite(kappa_c) || !std::isfinite(gamma)) return fail(RS_EINVAL, "kappa_c and gamma must be finite");
+  if (!inputs_on_device) {
+    for (int64_t i = 0; i < 2 * n_lens; ++i)
+      if (!finite_coord((double)lens_xy[i])) return fail(RS_EINVAL, "lens coordinate %lld not finite or beyond 1e18", (long long)i);
+    if (masses)
+      for (int64_t i = 0; i < n_lens; ++i)
+        if (!(std::isfinite(masses[i]) && masses[i] >= 0.f)) return fail(RS_EINVAL, "mass %lld not finite or negative", (long long)i);
+  }
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  rs_field* f = new (std::nothrow) rs_field();
+  if (!f) return fail(RS_ENOMEM, "host allocation failed");
+  cudaError_t e = cudaGetDevice(&f->device);
+  if (e != cudaSuccess) {
+    delete f;
+    return cuda_fail(e, "cudaGetDevice");
+  }
+  f->n_lens = n_lens;
+  f->n_pad = (n_lens + rsdev::kLensPad - 1) / rsdev::kLensPad * rsdev::kLensPad;
+  if (f->n_pad == 0) f->n_pad = rsdev::kLensPad;  // keep a valid (unused) tile for empty fields
+  f->kappa_c = kappa_c;
+  f->gamma = gamma;
+  const bool has_mass = masses != nullptr;
+  float* tmp_xy = nullptr;
+  float* tmp_m = nullptr;
+  auto cleanup = [&]() {
+    cudaFree(f->lens4);
+    cudaFree(f->mass2);
+    cudaFree(f->status);
+    cudaFree(tmp_xy);
+    cudaFree(tmp_m);
+    delete f;
+  };
+  if ((e = cudaMalloc(&f->lens4, sizeof(float4) * f->n_pad)) != cudaSuccess ||
+      (has_mass && (e = cudaMalloc(&f->mass2, sizeof(float2) * f->n_pad)) != cudaSuccess) ||
+      (e = cudaMalloc(&f->status, sizeof(unsigned int))) != cudaSuccess) {
+    int rc = cuda_fail(e, "cudaMalloc (field)");
+    cleanup();
+    return rc;
+  }
+  const float* src_xy = lens_xy;
+  const float* src_m = masses;
+  if (!inputs_on_device && n_lens > 0) {
+    if ((e = cudaMalloc(&tmp_xy, sizeof(float) * 2 * n_lens)) != cudaSuccess ||
+        (has_mass && (e = cudaMalloc(&tmp_m, sizeof(float) * n_lens)) != cudaSuccess)) {
+      int rc = cuda_fail(e, "cudaMalloc (staging)");
+      cleanup();
+      return rc;
+    }
+    if ((e = cudaMemcpyAsync(tmp_xy, lens_xy, sizeof(float) * 2 * n_lens, cudaMemcpyHostToDevice, s)) != cudaSuccess ||
+        (has_mass && (e = cudaMemcpyAsync(tmp_m, masses, sizeof(float) * n_lens, cudaMemcpyHostToDevice, s)) != cudaSuccess)) {
+      int rc = cuda_fail(e, "cudaMemcpyAsync (lenses)");
+      cudaStreamSynchronize(s);
+      cleanup();
+      return rc;
+    }
+    src_xy = tmp_xy;
+    src_m = tmp_m;
+  }
+  if ((e = cudaMemsetAsync(f->status, 0, sizeof(unsigned int), s)) != cudaSuccess) {
+    int rc = cuda_fail(e, "cudaMemsetAsync (status)");
+    cudaStreamSynchronize(s);
+    cleanup();
+    return rc;
+  }
+  {
+    const int threads = 256;
+    const int64_t want = (f->n_pad + threads - 1) / threads;
+    const int blocks = (int)std::min<int64_t>(want, (int64_t)num_sms(f->device) * 16);
+    pack_lenses_kernel<<<blocks, threads, 0, s>>>(n_lens > 0 ? src_xy : nullptr, src_m, n_lens, f->n_pad, f->lens4,
+                                                  has_mass ? f->mass2 : nullptr);
+    if ((e = cudaGetLastError()) != cudaSuccess) {
+      int rc = cuda_fail(e, "pack_lenses_kernel launch");
+      cudaStreamSynchronize(s);
+      cleanup();
+      return rc;
+    }
+  }
+  if (tmp_xy || tmp_m) {
+    // staging buffers: free once the packing kernel has consumed them
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) {
+      int rc = cuda_fail(e, "cudaStreamSynchronize (field upload)");
+      cleanup();
+      return rc;
+    }
+    cudaFree(tmp_xy);
+    cudaFree(tmp_m);
+    tmp_xy = tmp_m = nullptr;
+  }
+  f->dev.lens4 = f->lens4;
+  f->dev.mass2 = has_mass ? f->mass2 : nullptr;
+  f->dev.n_lens = (int32_t)n_lens;
+  f->dev.has_mass = has_mass ? 1 : 0;
+  f->dev.lam1 = (1.0 - kappa_c) - gamma;
+  f->dev.lam2 = (1.0 - kappa_c) + gamma;
+  f->dev.status = f->status;
+  *out = f;
+  return RS_OK;
+}
+
+int rs_destroy_field(rs_field_t f) {
+  if (!f) return RS_OK;
+  DeviceGuard g(f->device);
+  cudaDeviceSynchronize();
+  cudaFree(f->lens4);
+  cudaFree(f->mass2);
+  cudaFree(f->status);
+  delete f;
+  return RS_OK;
+}
+
+int rs_field_info(rs_field_t f, int64_t* n_lens, int* has_masses) {
+  if (!f) return fail(RS_EINVAL, "field is NULL");
+  if (n_lens) *n_lens = f->n_lens;
+  if (has_masses) *has_masses = f->dev.has_mass;
+  return RS_OK;
+}
+
+int rs_field_status(rs_field_t f, int clear, int* status) {
+  if (!f || !status) return fail(RS_EINVAL, "NULL argument");
+  DeviceGuard g(f->device);
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceSynchronize");
+  unsigned int v = 0;
+  if ((e = cudaMemcpy(&v, f->status, sizeof(v), cudaMemcpyDeviceToHost)) != cudaSuccess)
+    return cuda_fail(e, "cudaMemcpy (status)");
+  *status = v == 0 ? RS_OK : (int)v;
+  if (clear && v != 0) {
+    if ((e = cudaMemset(f->status, 0, sizeof(unsigned int))) != cudaSuccess) return cuda_fail(e, "cudaMemset (status)");
+  }
+  return RS_OK;
+}
+
+int rs_shoot_rows(rs_field_t f, const rs_ray_grid* g, int64_t row_begin, int64_t row_end, const rs_window* w,
+                  uint32_t* d_counts, uint64_t* d_out_of_window, void* stream) {
+  if (!f) return fail(RS_EINVAL, "field is NULL");
+  int rc;
+  if ((rc = check_grid(g)) != RS_OK) return rc;
+  if ((rc = check_window(w)) != RS_OK) return rc;
+  if (!d_counts) return fail(RS_EINVAL, "d_counts is NULL");
+  if (row_begin < 0 || row_end < row_begin || row_end > g->n[1])
+    return fail(RS_EINVAL, "row range [%lld, %lld) outside [0, %lld]", (long long)row_begin, (long long)row_end,
+                (long long)g->n[1]);
+  if ((rc = check_field_device(f)) != RS_OK) return rc;
+  ShootDesc d;
+  if ((rc = fill_desc(f, g, row_begin, row_end, w, d_counts, d_out_of_window, &d)) != RS_OK) return rc;
+  if (d.n_rays == 0) return RS_OK;
+  cudaError_t e = rsint::launch_shoot(g_cfg[f->dev.has_mass ? 1 : 0], d, reinterpret_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(e, "shoot kernel launch");
+  return RS_OK;
+}
+
+int rs_shoot(rs_field_t f, const rs_ray_grid* g, const rs_window* w, uint32_t* d_counts, uint64_t* d_out_of_window,
+             void* stream) {
+  if (!g) return fail(RS_EINVAL, "ray grid is NULL");
+  return rs_shoot_rows(f, g, 0, g->n[1], w, d_counts, d_out_of_window, stream);
+}
+
+int rs_trace(rs_field_t f, const rs_ray_grid* g, const int64_t* d_ray_ij, int64_t k, double* d_y, double* d_alpha,
+             void* stream) {
+  if (!f) return fail(RS_EINVAL, "field is NULL");
+  int rc;
+  if ((rc = check_grid(g)) != RS_OK) return rc;
+  if (k < 0) return fail(RS_EINVAL, "k < 0");
+  if (k == 0) return RS_OK;
+  if (!d_ray_ij || !d_y) return fail(RS_EINVAL, "d_ray_ij / d_y is NULL");
+  if (k >= ((int64_t)1 << 31)) return fail(RS_EOVERFLOW, "k must be < 2^31");
+  if ((rc = check_field_device(f)) != RS_OK) return rc;
+  cudaError_t e = rsint::launch_trace(f->dev, g->origin[0], g->origin[1], g->spacing[0], g->spacing[1], d_ray_ij, k,
+                                      d_y, d_alpha, reinterpret_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(e, "trace kernel launch");
+  return RS_OK;
+}
+
+int rs_magnification(const uint32_t* d_counts, const rs_ray_grid* g, const rs_window* w, float* d_mu, void* stream) {
+  int rc;
+  if ((rc = check_grid(g)) != RS_OK) return rc;
+  if ((rc = check_window(w)) != RS_OK) return rc;
+  if (!d_counts || !d_mu) return fail(RS_EINVAL, "d_counts / d_mu is NULL");
+  const double pix_area = ((w->hi[0] - w->lo[0]) / (double)w->npix[0]) * ((w->hi[1] - w->lo[1]) / (double)w->npix[1]);
+  const double n_av = pix_area / (g->spacing[0] * g->spacing[1]);
+  if (!(std::isfinite(n_av) && n_av > 0.0)) return fail(RS_EINVAL, "N_av is not a positive finite number");
+  const int64_t n = (int64_t)w->npix[0] * (int64_t)w->npix[1];
+  int dev = 0;
+  cudaGetDevice(&dev);
+  const int vec = ((reinterpret_cast<uintptr_t>(d_counts) | reinterpret_cast<uintptr_t>(d_mu)) & 15u) == 0;
+  const int threads = 256;
+  const int64_t want = ((vec ? n / 4 : n) + threads - 1) / threads;
+  const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)num_sms(dev) * 8));
+  magnification_kernel<<<blocks, threads, 0, reinterpret_cast<cudaStream_t>(stream)>>>(d_counts, d_mu, n,
+                                                                                        (float)(1.0 / n_av), vec);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "magnification kernel launch");
+  return RS_OK;
+}
+
+// ------------------------------------------------------------------------------------------------ batch
+
+int rs_batch_create(int n_fields, const rs_field_t* fields, const rs_ray_grid* grids, const rs_window* windows,
+                    uint32_t* const* d_counts, uint64_t* d_out_of_window, rs_batch_t* out) {
+  if (!out) return fail(RS_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (n_fields <= 0) return fail(RS_EINVAL, "n_fields must be >= 1");
+  if (!fields || !grids || !windows || !d_counts) return fail(RS_EINVAL, "NULL array argument");
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+  int rc;
+  const int cfg = g_cfg[1];
+  const int64_t per = (int64_t)rsint::kCfgs[cfg].block * rsint::kCfgs[cfg].rpt;
+  std::vector<ShootDesc> descs(n_fields);
+  struct Item {
+    double cost;
+    int field;
+    int tile;
+  };
+  std::vector<Item> items;
+  for (int k = 0; k < n_fields; ++k) {
+    if (!fields[k]) return fail(RS_EINVAL, "fields[%d] is NULL", k);
+    if (fields[k]->device != dev) return fail(RS_EINVAL, "fields[%d] lives on another device", k);
+    if ((rc = check_grid(&grids[k])) != RS_OK) return rc;
+    if ((rc = check_window(&windows[k])) != RS_OK) return rc;
+    if (!d_counts[k]) return fail(RS_EINVAL, "d_counts[%d] is NULL", k);
+    if ((rc = fill_desc(fields[k], &grids[k], 0, grids[k].n[1], &windows[k], d_counts[k],
+                        d_out_of_window ? d_out_of_window + k : nullptr, &descs[k])) != RS_OK)
+      return rc;
+    const int64_t nt = (descs[k].n_rays + per - 1) / per;
+    if ((int64_t)items.size() + nt >= ((int64_t)1 << 31)) return fail(RS_EOVERFLOW, "too many work items");
+    for (int64_t t = 0; t < nt; ++t) {
+      const int64_t rays = std::min<int64_t>(per, descs[k].n_rays - t * per);
+      // per-ray cost: one interaction per lens plus a fixed epilogue (~ 64 interactions)
+      const double cost = (double)rays * ((double)fields[k]->n_lens + 64.0);
+      items.push_back({cost, k, (int)t});
+    }
+  }
+  std::stable_sort(items.begin(), items.end(), [](const Item& a, const Item& b) { return a.cost > b.cost; });
+  std::vector<int2> h_items(items.size());
+  for (size_t i = 0; i < items.size(); ++i) h_items[i] = make_int2(items[i].field, items[i].tile);
+
+  rs_batch* b = new (std::nothrow) rs_batch();
+  if (!b) return fail(RS_ENOMEM, "host allocation failed");
+  b->device = dev;
+  b->n_fields = n_fields;
+  b->n_items = (int)h_items.size();
+  b->cfg = cfg;
+  int bps = 0;
+  if ((e = rsint::batch_blocks_per_sm(cfg, &bps)) != cudaSuccess || bps < 1) bps = 1;
+  b->grid = num_sms(dev) * bps;
+  auto cleanup = [&]() {
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    cudaFree(b->d_descs);
+    cudaFree(b->d_items);
+    cudaFree(b->d_counter);
+    delete b;
+  };
+  if ((e = cudaMalloc(&b->d_descs, sizeof(ShootDesc) * n_fields)) != cudaSuccess ||
+      (e = cudaMalloc(&b->d_items, sizeof(int2) * std::max<size_t>(1, h_items.size()))) != cudaSuccess ||
+      (e = cudaMalloc(&b->d_counter, sizeof(int))) != cudaSuccess) {
+    rc = cuda_fail(e, "cudaMalloc (batch)");
+    cleanup();
+    return rc;
+  }
+  if ((e = cudaMemcpy(b->d_descs, descs.data(), sizeof(ShootDesc) * n_fields, cudaMemcpyHostToDevice)) != cudaSuccess ||
+      (!h_items.empty() &&
+       (e = cudaMemcpy(b->d_items, h_items.data(), sizeof(int2) * h_items.size(), cudaMemcpyHostToDevice)) != cudaSuccess)) {
+    rc = cuda_fail(e, "cudaMemcpy (batch descriptors)");
+    cleanup();
+    return rc;
+  }
+  // Capture: zero every map and counter, then the persistent kernel.
+  cudaStream_t cs;
+  if ((e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking)) != cudaSuccess) {
+    rc = cuda_fail(e, "cudaStreamCreate");
+    cleanup();
+    return rc;
+  }
+  e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    for (int k = 0; k < n_fields && e == cudaSuccess; ++k)
+      e = cudaMemsetAsync(d_counts[k], 0, sizeof(uint32_t) * (size_t)windows[k].npix[0] * (size_t)windows[k].npix[1], cs);
+    if (e == cudaSuccess && d_out_of_window) e = cudaMemsetAsync(d_out_of_window, 0, sizeof(uint64_t) * n_fields, cs);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->d_counter, 0, sizeof(int), cs);
+    if (e == cudaSuccess && b->n_items > 0)
+      e = rsint::launch_batch(cfg, b->d_descs, b->d_items, b->n_items, b->d_counter, b->grid, cs);
+    cudaError_t e2 = cudaStreamEndCapture(cs, &b->graph);
+    if (e == cudaSuccess) e = e2;
+  }
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, b->graph, 0);
+  cudaStreamDestroy(cs);
+  if (e != cudaSuccess) {
+    rc = cuda_fail(e, "batch graph capture");
+    cleanup();
+    return rc;
+  }
+  *out = b;
+  return RS_OK;
+}
+
+int rs_batch_launch(rs_batch_t b, void* stream) {
+  if (!b) return fail(RS_EINVAL, "batch is NULL");
+  int cur = -1;
+  cudaGetDevice(&cur);
+  if (cur != b->device) return fail(RS_EINVAL, "batch lives on device %d but device %d is current", b->device, cur);
+  cudaError_t e = cudaGraphLaunch(b->exec, reinterpret_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGraphLaunch");
+  return RS_OK;
+}
+
+int rs_batch_destroy(rs_batch_t b) {
+  if (!b) return RS_OK;
+  DeviceGuard g(b->device);
+  cudaDeviceSynchronize();
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  cudaFree(b->d_descs);
+  cudaFree(b->d_items);
+  cudaFree(b->d_counter);
+  delete b;
+  return RS_OK;
+}
+
+int rs_shoot_batch(int n_fields, const rs_field_t* fields, const rs_ray_grid* grids, const rs_window* windows,
+                   uint32_t* const* d_counts, uint64_t* d_out_of_window, void* stream) {
+  rs_batch_t b = nullptr;
+  int rc = rs_batch_create(n_fields, fields, grids, windows, d_counts, d_out_of_window, &b);
+  if (rc != RS_OK) return rc;
+  rc = rs_batch_launch(b, stream);
+  cudaError_t e = cudaStreamSynchronize(reinterpret_cast<cudaStream_t>(stream));
+  rs_batch_destroy(b);
+  if (rc != RS_OK) return rc;
+  if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize (batch)");
+  return RS_OK;
+}
+
+}  // extern "C"

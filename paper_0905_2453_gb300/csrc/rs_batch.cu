@@ -1,0 +1,76 @@
+// Persistent batched shoot kernel: many independent lens fields in one launch.
+//
+// Work items are (field, ray tile) pairs ordered on the host by decreasing cost
+// (longest-processing-time first).  Resident CTAs pull the next item from a
+// global counter; each item runs the same per-ray arithmetic as the plain
+// kernel, so a field's counts are bitwise those of its own rs_shoot.
+#include "rs_internal.h"
+
+namespace {
+
+using namespace rsdev;
+
+template <int BLOCK, int RPT, int TILE>
+__global__ void __launch_bounds__(BLOCK)
+    batch_kernel(const ShootDesc* __restrict__ descs, const int2* __restrict__ items, int n_items, int* counter) {
+  __shared__ LensSmem<TILE> sm;
+  __shared__ int s_item;
+  PipeState ps;
+  pipe_init(sm.bar, ps);
+  for (;;) {
+    if (threadIdx.x == 0) s_item = atomicAdd(counter, 1);
+    __syncthreads();
+    const int it = s_item;
+    __syncthreads();
+    if (it >= n_items) break;
+    const int2 w = items[it];
+    const ShootDesc& d = descs[w.x];
+    const int64_t base = (int64_t)w.y * (BLOCK * RPT);
+    const bool ok = d.f.has_mass ? shoot_tile<BLOCK, RPT, TILE, true>(d, base, sm, ps)
+                                 : shoot_tile<BLOCK, RPT, TILE, false>(d, base, sm, ps);
+    if (!ok) break;
+  }
+}
+
+template <int BLOCK, int RPT>
+cudaError_t launch_batch_t(const ShootDesc* descs, const int2* items, int n_items, int* counter, int grid,
+                           cudaStream_t s) {
+  batch_kernel<BLOCK, RPT, rsint::kTile><<<grid, BLOCK, 0, s>>>(descs, items, n_items, counter);
+  return cudaGetLastError();
+}
+
+template <int BLOCK, int RPT>
+cudaError_t occ_t(int* blocks) {
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, batch_kernel<BLOCK, RPT, rsint::kTile>, BLOCK, 0);
+}
+
+}  // namespace
+
+namespace rsint {
+
+cudaError_t launch_batch(int cfg, const rsdev::ShootDesc* descs, const int2* items, int n_items, int* counter,
+                         int grid, cudaStream_t s) {
+  switch (cfg) {
+    case 0: return launch_batch_t<128, 4>(descs, items, n_items, counter, grid, s);
+    case 1: return launch_batch_t<128, 8>(descs, items, n_items, counter, grid, s);
+    case 2: return launch_batch_t<256, 4>(descs, items, n_items, counter, grid, s);
+    case 3: return launch_batch_t<256, 8>(descs, items, n_items, counter, grid, s);
+    case 4: return launch_batch_t<512, 4>(descs, items, n_items, counter, grid, s);
+    case 5: return launch_batch_t<256, 12>(descs, items, n_items, counter, grid, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t batch_blocks_per_sm(int cfg, int* blocks) {
+  switch (cfg) {
+    case 0: return occ_t<128, 4>(blocks);
+    case 1: return occ_t<128, 8>(blocks);
+    case 2: return occ_t<256, 4>(blocks);
+    case 3: return occ_t<256, 8>(blocks);
+    case 4: return occ_t<512, 4>(blocks);
+    case 5: return occ_t<256, 12>(blocks);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace rsint

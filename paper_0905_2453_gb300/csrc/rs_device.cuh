@@ -1,0 +1,388 @@
+// Device side of the inverse ray-shooting path (sm_103a).
+//
+// What one CTA computes: a tile of BLOCK x RPT rays of a regular image-plane
+// grid, deflected by all lenses of a field (Eq. 2, a direct sum; the paper's
+// ray x lens decomposition of Eq. 5 with lens tiles staged through shared
+// memory, Section 2.2), mapped to the source plane with the macro-model of
+// Eq. 6 and binned into a uint32 count map (Eq. 4 counts).
+//
+// GB300 mapping
+//   * Lens tiles of TILE lenses are copied global -> shared by the bulk-copy
+//     (TMA) engine, double-buffered, completion tracked by an mbarrier.  Each
+//     CTA fetches its own tiles; there is no multicast.
+//   * Lenses are stored duplicated, {x1, x1, x2, x2} (and {m, m}), so one
+//     shared-memory load yields the 64-bit operand pairs of the packed
+//     f32x2 instructions: every packed op advances two rays against one lens.
+//   * Per lens and ray pair: sub.f32x2 x2, mul.f32x2, fma.f32x2 (|d|^2),
+//     two rcp.approx (MUFU), [mul.f32x2 by the mass], fma.f32x2 x2.  These are
+//     the ten flops per interaction of the paper's Appendix A; the reciprocal
+//     on the MUFU pipe sets the throughput ceiling.
+//   * Per ray, each group of kGroup = 32 consecutive lenses is summed from zero
+//     in float32, then folded into a two-float (hi, lo) accumulator with an
+//     error-free TwoSum, so the deflection keeps its low-order bits over 1e8
+//     lenses.  alpha = hi + lo, Eq. 6 and the pixel index are evaluated in
+//     float64 once per ray (the only float64 work, Section 4's remark on
+//     using double precision only where it is needed).
+//   * Binning: one global atomic add per in-window ray; out-of-window rays
+//     are counted per warp with a ballot and one 64-bit atomic per warp.
+//
+// Every wait on an mbarrier is bounded (about one second of globaltimer); on
+// timeout the CTA records RS_ETIMEOUT in the field's status word, waits
+// (bounded) for its own copies still in flight and returns.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace rsdev {
+
+constexpr int kGroup = 32;                 // lenses per float32 partial sum (fixed: part of the arithmetic)
+constexpr int kLensPad = 1024;             // device lens arrays are padded to a multiple of this
+constexpr uint64_t kWaitLimitNs = 1000000000ull;  // bounded mbarrier wait: 1 s
+constexpr unsigned kStatusTimeout = 5u;    // == RS_ETIMEOUT
+
+// ----------------------------------------------------------------------------------------------
+// Packed f32x2 arithmetic (sm_100+): a uint64_t holds {lo = ray A, hi = ray B}.
+// ----------------------------------------------------------------------------------------------
+__device__ __forceinline__ uint64_t f2_sub(uint64_t a, uint64_t b) {
+  uint64_t d;
+  asm("sub.rn.ftz.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ uint64_t f2_mul(uint64_t a, uint64_t b) {
+  uint64_t d;
+  asm("mul.rn.ftz.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ uint64_t f2_fma(uint64_t a, uint64_t b, uint64_t c) {
+  uint64_t d;
+  asm("fma.rn.ftz.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+// Exact-rounding add/sub without flush-to-zero, for the TwoSum.
+__device__ __forceinline__ uint64_t f2_add_x(uint64_t a, uint64_t b) {
+  uint64_t d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ uint64_t f2_sub_x(uint64_t a, uint64_t b) {
+  uint64_t d;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ uint64_t f2_pack(float lo, float hi) {
+  uint64_t d;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(d) : "f"(lo), "f"(hi));
+  return d;
+}
+__device__ __forceinline__ void f2_unpack(uint64_t v, float& lo, float& hi) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ float rcp_approx(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
+// Error-free transformation of hi + p into (s, e), s = fl(hi + p), s + e = hi + p exactly
+// (Knuth's TwoSum), lane-wise on both rays; e is accumulated into lo.
+__device__ __forceinline__ void twosum_accumulate(uint64_t& hi, uint64_t& lo, uint64_t p) {
+  uint64_t s = f2_add_x(hi, p);
+  uint64_t bp = f2_sub_x(s, hi);
+  uint64_t ap = f2_sub_x(s, bp);
+  uint64_t db = f2_sub_x(p, bp);
+  uint64_t da = f2_sub_x(hi, ap);
+  uint64_t e = f2_add_x(da, db);
+  lo = f2_add_x(lo, e);
+  hi = s;
+}
+
+// ----------------------------------------------------------------------------------------------
+// Shared memory, mbarrier and bulk copy (TMA) helpers.
+// ----------------------------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void lds_pair2(uint32_t addr, uint64_t& a, uint64_t& b) {
+  asm volatile("ld.shared.v2.b64 {%0, %1}, [%2];" : "=l"(a), "=l"(b) : "r"(addr));
+}
+__device__ __forceinline__ uint64_t lds_pair(uint32_t addr) {
+  uint64_t a;
+  asm volatile("ld.shared.b64 %0, [%1];" : "=l"(a) : "r"(addr));
+  return a;
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_fence_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(void* dst_smem, const void* src_gmem, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst_smem)),
+      "l"(src_gmem), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ uint64_t globaltimer_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+// Bounded wait for the phase with the given parity to complete.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = globaltimer_ns();
+  for (uint32_t it = 1; it < (1u << 30); ++it) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if ((it & 255u) == 0u && globaltimer_ns() - t0 > kWaitLimitNs) return false;
+  }
+  return false;
+}
+
+// ----------------------------------------------------------------------------------------------
+// Descriptors.
+// ----------------------------------------------------------------------------------------------
+struct FieldDev {
+  const float4* lens4;  // {x1, x1, x2, x2} per lens, padded to a multiple of kLensPad lenses
+  const float2* mass2;  // {m, m} per lens (same padding), or nullptr for unit masses
+  int32_t n_lens;
+  int32_t has_mass;
+  double lam1, lam2;    // (1 - kappa_c) - gamma, (1 - kappa_c) + gamma
+  unsigned int* status; // device status word (RS_OK / RS_ETIMEOUT)
+};
+
+struct ShootDesc {
+  FieldDev f;
+  double or0, or1, sp0, sp1;  // ray grid origin and spacing
+  int64_t n0;                 // rays per grid row
+  int64_t j_begin;            // first grid row of this call
+  int64_t n_rays;             // rays in this call (rows x n0), < 2^32
+  double lo0, lo1, sc0, sc1;  // window lower corner and npix / (hi - lo)
+  int32_t np0, np1;           // pixels per axis
+  uint32_t* counts;           // [np1][np0]
+  unsigned long long* oow;    // out-of-window counter or nullptr
+};
+
+template <int TILE>
+struct __align__(16) LensSmem {
+  float4 lens4[2][TILE];
+  float2 mass2[2][TILE];
+  uint64_t bar[2];
+};
+
+// Pipeline state carried across ray tiles by the persistent kernel (CTA-uniform).
+struct PipeState {
+  uint32_t parity[2];
+};
+
+__device__ __forceinline__ void pipe_init(uint64_t* bar, PipeState& ps) {
+  if (threadIdx.x == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    mbar_fence_init();
+  }
+  ps.parity[0] = 0;
+  ps.parity[1] = 0;
+  __syncthreads();
+}
+
+template <int TILE, bool MASS>
+__device__ __forceinline__ void issue_lens_tile(const FieldDev& f, LensSmem<TILE>& sm, int tile, int buf) {
+  // called by one thread; full tiles are always in bounds thanks to the kLensPad padding
+  const uint32_t b4 = TILE * sizeof(float4);
+  const uint32_t b2 = MASS ? TILE * sizeof(float2) : 0u;
+  fence_proxy_async_smem();
+  mbar_expect_tx(&sm.bar[buf], b4 + b2);
+  bulk_g2s(&sm.lens4[buf][0], f.lens4 + (size_t)tile * TILE, b4, &sm.bar[buf]);
+  if (MASS) bulk_g2s(&sm.mass2[buf][0], f.mass2 + (size_t)tile * TILE, b2, &sm.bar[buf]);
+}
+
+// ----------------------------------------------------------------------------------------------
+// Ray position (i, j) -> float, as the header defines it.
+// ----------------------------------------------------------------------------------------------
+__device__ __forceinline__ float ray_coord(int64_t idx, double spacing, double origin) {
+  return __double2float_rn(__fma_rn((double)idx, spacing, origin));
+}
+
+// ----------------------------------------------------------------------------------------------
+// Deflection of RPT rays per thread by all lenses of the field.
+// x1/x2 in, alpha1/alpha2 (double) out.  Returns false if a bounded wait gave up (the CTA
+// then must stop; the status word has been set).
+// ----------------------------------------------------------------------------------------------
+template <int BLOCK, int RPT, int TILE, bool MASS>
+__device__ __forceinline__ bool deflect(const FieldDev& f, const float (&x1)[RPT], const float (&x2)[RPT],
+                                        double (&a1)[RPT], double (&a2)[RPT], LensSmem<TILE>& sm,
+                                        PipeState& ps) {
+  static_assert(RPT % 2 == 0, "rays per thread must be even (packed pairs)");
+  static_assert(TILE % kGroup == 0, "lens tile must hold whole lens groups");
+  constexpr int NP = RPT / 2;
+  uint64_t X1[NP], X2[NP], H1[NP], L1[NP], H2[NP], L2[NP];
+#pragma unroll
+  for (int q = 0; q < NP; ++q) {
+    X1[q] = f2_pack(x1[2 * q], x1[2 * q + 1]);
+    X2[q] = f2_pack(x2[2 * q], x2[2 * q + 1]);
+    H1[q] = L1[q] = H2[q] = L2[q] = 0ull;
+  }
+  const int n = f.n_lens;
+  const int ntiles = (n + TILE - 1) / TILE;
+  bool ok = true;
+  if (threadIdx.x == 0) {
+    if (ntiles > 0) issue_lens_tile<TILE, MASS>(f, sm, 0, 0);
+    if (ntiles > 1) issue_lens_tile<TILE, MASS>(f, sm, 1, 1);
+  }
+  int t = 0;
+  for (; t < ntiles; ++t) {
+    const int b = t & 1;
+    const bool got = mbar_wait_bounded(&sm.bar[b], ps.parity[b]);
+    ps.parity[b] ^= 1u;
+    if (__syncthreads_or(!got)) {
+      ok = false;
+      break;
+    }
+    const uint32_t lbase = smem_u32(&sm.lens4[b][0]);
+    const uint32_t mbase = smem_u32(&sm.mass2[b][0]);
+    const int cnt = min(TILE, n - t * TILE);
+    int g = 0;
+    for (; g + kGroup <= cnt; g += kGroup) {
+      uint64_t P1[NP], P2[NP];
+#pragma unroll
+      for (int q = 0; q < NP; ++q) P1[q] = P2[q] = 0ull;
+#pragma unroll 8
+      for (int l = 0; l < kGroup; ++l) {
+        uint64_t Lx, Ly, Lm = 0;
+        lds_pair2(lbase + (uint32_t)(g + l) * 16u, Lx, Ly);
+        if (MASS) Lm = lds_pair(mbase + (uint32_t)(g + l) * 8u);
+#pragma unroll
+        for (int q = 0; q < NP; ++q) {
+          const uint64_t d1 = f2_sub(X1[q], Lx);
+          const uint64_t d2 = f2_sub(X2[q], Ly);
+          const uint64_t r2 = f2_fma(d2, d2, f2_mul(d1, d1));
+          float ra, rb;
+          f2_unpack(r2, ra, rb);
+          uint64_t w = f2_pack(rcp_approx(ra), rcp_approx(rb));
+          if (MASS) w = f2_mul(w, Lm);
+          P1[q] = f2_fma(w, d1, P1[q]);
+          P2[q] = f2_fma(w, d2, P2[q]);
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < NP; ++q) {
+        twosum_accumulate(H1[q], L1[q], P1[q]);
+        twosum_accumulate(H2[q], L2[q], P2[q]);
+      }
+    }
+    if (g < cnt) {  // last, partial group of the field
+      uint64_t P1[NP], P2[NP];
+#pragma unroll
+      for (int q = 0; q < NP; ++q) P1[q] = P2[q] = 0ull;
+      for (int l = g; l < cnt; ++l) {
+        uint64_t Lx, Ly, Lm = 0;
+        lds_pair2(lbase + (uint32_t)l * 16u, Lx, Ly);
+        if (MASS) Lm = lds_pair(mbase + (uint32_t)l * 8u);
+#pragma unroll
+        for (int q = 0; q < NP; ++q) {
+          const uint64_t d1 = f2_sub(X1[q], Lx);
+          const uint64_t d2 = f2_sub(X2[q], Ly);
+          const uint64_t r2 = f2_fma(d2, d2, f2_mul(d1, d1));
+          float ra, rb;
+          f2_unpack(r2, ra, rb);
+          uint64_t w = f2_pack(rcp_approx(ra), rcp_approx(rb));
+          if (MASS) w = f2_mul(w, Lm);
+          P1[q] = f2_fma(w, d1, P1[q]);
+          P2[q] = f2_fma(w, d2, P2[q]);
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < NP; ++q) {
+        twosum_accumulate(H1[q], L1[q], P1[q]);
+        twosum_accumulate(H2[q], L2[q], P2[q]);
+      }
+    }
+    __syncthreads();  // every thread is done with buffer b
+    if (threadIdx.x == 0 && t + 2 < ntiles) issue_lens_tile<TILE, MASS>(f, sm, t + 2, b);
+  }
+  if (!ok) {
+    // Record the timeout and drain this CTA's copies still in flight (bounded) before leaving:
+    // tile t (its parity was already flipped above) and tile t + 1 if it was issued.
+    if (threadIdx.x == 0) atomicExch(f.status, kStatusTimeout);
+    (void)mbar_wait_bounded(&sm.bar[t & 1], ps.parity[t & 1] ^ 1u);
+    if (t + 1 < ntiles) (void)mbar_wait_bounded(&sm.bar[(t + 1) & 1], ps.parity[(t + 1) & 1]);
+    return false;
+  }
+#pragma unroll
+  for (int q = 0; q < NP; ++q) {
+    float h, hB, l, lB;
+    f2_unpack(H1[q], h, hB);
+    f2_unpack(L1[q], l, lB);
+    a1[2 * q] = (double)h + (double)l;
+    a1[2 * q + 1] = (double)hB + (double)lB;
+    f2_unpack(H2[q], h, hB);
+    f2_unpack(L2[q], l, lB);
+    a2[2 * q] = (double)h + (double)l;
+    a2[2 * q + 1] = (double)hB + (double)lB;
+  }
+  return true;
+}
+
+// ----------------------------------------------------------------------------------------------
+// One ray tile of a shoot call: rays ray_base + k*BLOCK + tid (k < RPT) of the call's rays.
+// ----------------------------------------------------------------------------------------------
+template <int BLOCK, int RPT, int TILE, bool MASS>
+__device__ __forceinline__ bool shoot_tile(const ShootDesc& d, int64_t ray_base, LensSmem<TILE>& sm,
+                                           PipeState& ps) {
+  float x1[RPT], x2[RPT];
+  bool valid[RPT];
+#pragma unroll
+  for (int k = 0; k < RPT; ++k) {
+    int64_t r = ray_base + (int64_t)k * BLOCK + threadIdx.x;
+    valid[k] = r < d.n_rays;
+    if (!valid[k]) r = d.n_rays - 1;
+    const int64_t j = d.j_begin + r / d.n0;
+    const int64_t i = r - (r / d.n0) * d.n0;
+    x1[k] = ray_coord(i, d.sp0, d.or0);
+    x2[k] = ray_coord(j, d.sp1, d.or1);
+  }
+  double a1[RPT], a2[RPT];
+  if (!deflect<BLOCK, RPT, TILE, MASS>(d.f, x1, x2, a1, a2, sm, ps)) return false;
+  unsigned oow_lane = 0;
+#pragma unroll
+  for (int k = 0; k < RPT; ++k) {
+    // Eq. 6 in float64: product rounded, then difference rounded (no fma), as specified
+    const double y1 = __dsub_rn(__dmul_rn(d.f.lam1, (double)x1[k]), a1[k]);
+    const double y2 = __dsub_rn(__dmul_rn(d.f.lam2, (double)x2[k]), a2[k]);
+    const double u1 = __dmul_rn(__dsub_rn(y1, d.lo0), d.sc0);
+    const double u2 = __dmul_rn(__dsub_rn(y2, d.lo1), d.sc1);
+    const bool inwin = (u1 >= 0.0) && (u1 < (double)d.np0) && (u2 >= 0.0) && (u2 < (double)d.np1);
+    if (valid[k] && inwin) {
+      const int p1 = (int)floor(u1);
+      const int p2 = (int)floor(u2);
+      atomicAdd(d.counts + (size_t)p2 * (size_t)d.np0 + (size_t)p1, 1u);
+    }
+    const unsigned miss = __ballot_sync(0xffffffffu, valid[k] && !inwin);
+    oow_lane += __popc(miss);
+  }
+  if (d.oow != nullptr && (threadIdx.x & 31) == 0 && oow_lane != 0)
+    atomicAdd(d.oow, (unsigned long long)oow_lane);
+  return true;
+}
+
+}  // namespace rsdev

@@ -1,0 +1,42 @@
+// Internal host-side interface between the C-ABI layer (rs_api.cu) and the kernel
+// translation units (rs_shoot.cu, rs_batch.cu).  Not part of the public ABI.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "rs_device.cuh"
+
+namespace rsint {
+
+// Lenses per shared-memory stage (a multiple of rsdev::kGroup, a divisor of rsdev::kLensPad).
+constexpr int kTile = 512;
+
+// Launch shapes compiled into the library; the per-ray arithmetic is identical for all.
+struct KernelCfg {
+  int block;  // threads per CTA
+  int rpt;    // rays per thread (even: packed pairs)
+};
+constexpr int kNumCfg = 6;
+constexpr KernelCfg kCfgs[kNumCfg] = {{128, 4}, {128, 8}, {256, 4}, {256, 8}, {512, 4}, {256, 12}};
+constexpr int kDefaultCfg = 3;
+
+inline int find_cfg(int block, int rpt) {
+  for (int i = 0; i < kNumCfg; ++i)
+    if (kCfgs[i].block == block && kCfgs[i].rpt == rpt) return i;
+  return -1;
+}
+
+// Plain launch: one CTA per ray tile of block * rpt rays.
+cudaError_t launch_shoot(int cfg, const rsdev::ShootDesc& d, cudaStream_t s);
+
+// Listed rays -> source positions (and deflections).
+cudaError_t launch_trace(const rsdev::FieldDev& f, double or0, double or1, double sp0, double sp1,
+                         const int64_t* ij, int64_t k, double* y, double* alpha, cudaStream_t s);
+
+// Persistent batched launch over LPT-ordered (field, ray tile) items.
+cudaError_t launch_batch(int cfg, const rsdev::ShootDesc* descs, const int2* items, int n_items,
+                         int* counter, int grid, cudaStream_t s);
+cudaError_t batch_blocks_per_sm(int cfg, int* blocks);
+
+}  // namespace rsint

@@ -1,0 +1,89 @@
+// Plain (one field per launch) shoot kernel and the listed-ray trace kernel.
+#include "rs_internal.h"
+
+namespace {
+
+using namespace rsdev;
+
+template <int BLOCK, int RPT, int TILE, bool MASS>
+__global__ void __launch_bounds__(BLOCK) shoot_kernel(const ShootDesc d) {
+  __shared__ LensSmem<TILE> sm;
+  PipeState ps;
+  pipe_init(sm.bar, ps);
+  (void)shoot_tile<BLOCK, RPT, TILE, MASS>(d, (int64_t)blockIdx.x * (BLOCK * RPT), sm, ps);
+}
+
+template <int BLOCK, int RPT, int TILE, bool MASS>
+__global__ void __launch_bounds__(BLOCK)
+    trace_kernel(const FieldDev f, double or0, double or1, double sp0, double sp1, const int64_t* __restrict__ ij,
+                 int64_t k, double* __restrict__ y, double* __restrict__ alpha) {
+  __shared__ LensSmem<TILE> sm;
+  PipeState ps;
+  pipe_init(sm.bar, ps);
+  const int64_t base = (int64_t)blockIdx.x * (BLOCK * RPT);
+  float x1[RPT], x2[RPT];
+  bool valid[RPT];
+#pragma unroll
+  for (int q = 0; q < RPT; ++q) {
+    int64_t r = base + (int64_t)q * BLOCK + threadIdx.x;
+    valid[q] = r < k;
+    if (!valid[q]) r = k - 1;
+    x1[q] = ray_coord(ij[2 * r], sp0, or0);
+    x2[q] = ray_coord(ij[2 * r + 1], sp1, or1);
+  }
+  double a1[RPT], a2[RPT];
+  if (!deflect<BLOCK, RPT, TILE, MASS>(f, x1, x2, a1, a2, sm, ps)) return;
+#pragma unroll
+  for (int q = 0; q < RPT; ++q) {
+    if (!valid[q]) continue;
+    const int64_t r = base + (int64_t)q * BLOCK + threadIdx.x;
+    y[2 * r] = __dsub_rn(__dmul_rn(f.lam1, (double)x1[q]), a1[q]);
+    y[2 * r + 1] = __dsub_rn(__dmul_rn(f.lam2, (double)x2[q]), a2[q]);
+    if (alpha != nullptr) {
+      alpha[2 * r] = a1[q];
+      alpha[2 * r + 1] = a2[q];
+    }
+  }
+}
+
+template <int BLOCK, int RPT>
+cudaError_t launch_shoot_t(const ShootDesc& d, cudaStream_t s) {
+  const int64_t per = (int64_t)BLOCK * RPT;
+  const int64_t grid = (d.n_rays + per - 1) / per;
+  if (grid <= 0) return cudaSuccess;
+  if (d.f.has_mass)
+    shoot_kernel<BLOCK, RPT, rsint::kTile, true><<<(unsigned)grid, BLOCK, 0, s>>>(d);
+  else
+    shoot_kernel<BLOCK, RPT, rsint::kTile, false><<<(unsigned)grid, BLOCK, 0, s>>>(d);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+namespace rsint {
+
+cudaError_t launch_shoot(int cfg, const rsdev::ShootDesc& d, cudaStream_t s) {
+  switch (cfg) {
+    case 0: return launch_shoot_t<128, 4>(d, s);
+    case 1: return launch_shoot_t<128, 8>(d, s);
+    case 2: return launch_shoot_t<256, 4>(d, s);
+    case 3: return launch_shoot_t<256, 8>(d, s);
+    case 4: return launch_shoot_t<512, 4>(d, s);
+    case 5: return launch_shoot_t<256, 12>(d, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_trace(const rsdev::FieldDev& f, double or0, double or1, double sp0, double sp1,
+                         const int64_t* ij, int64_t k, double* y, double* alpha, cudaStream_t s) {
+  constexpr int B = 128, R = 4;
+  if (k <= 0) return cudaSuccess;
+  const int64_t grid = (k + B * R - 1) / (B * R);
+  if (f.has_mass)
+    trace_kernel<B, R, kTile, true><<<(unsigned)grid, B, 0, s>>>(f, or0, or1, sp0, sp1, ij, k, y, alpha);
+  else
+    trace_kernel<B, R, kTile, false><<<(unsigned)grid, B, 0, s>>>(f, or0, or1, sp0, sp1, ij, k, y, alpha);
+  return cudaGetLastError();
+}
+
+}  // namespace rsint

@@ -1,0 +1,97 @@
+"""Shared helpers for the GPU parity tests (test infrastructure only)."""
+import numpy as np
+import torch
+
+import oracle
+import rs_inputs as ri
+
+_built = False
+
+
+def rs():
+    """The product binding, built for sm_103a if needed (fails loudly without the library)."""
+    global _built
+    if not _built:
+        from paper_0905_2453_gb300 import build
+        build.build()
+        _built = True
+    import paper_0905_2453_gb300 as m
+    return m
+
+
+def dev():
+    return torch.device("cuda", torch.cuda.current_device())
+
+
+def shoot_gpu(field_spec, grid=None, window=None, rows=None, counts=None, oow=None):
+    """GPU counts (numpy uint32 [npix1, npix0]) and out-of-window count of a rs_inputs.Field."""
+    m = rs()
+    grid = grid or field_spec.grid
+    window = window or field_spec.window
+    f = m.Field.from_spec(field_spec)
+    try:
+        if counts is None:
+            counts = torch.zeros((int(window.npix[1]), int(window.npix[0])), dtype=torch.int32, device=dev())
+        if oow is None:
+            oow = torch.zeros(1, dtype=torch.int64, device=dev())
+        f.shoot(grid, window, counts, oow, rows=rows)
+        torch.cuda.synchronize()
+        assert f.status() == m.RS_OK
+    finally:
+        f.close()
+    return counts.cpu().numpy().view(np.uint32), int(oow.item())
+
+
+def trace_gpu(field_spec, ray_ij, grid=None, chunk=1 << 22):
+    m = rs()
+    grid = grid or field_spec.grid
+    f = m.Field.from_spec(field_spec)
+    try:
+        ij = np.asarray(ray_ij, np.int64).reshape(-1, 2)
+        ys, als = [], []
+        for s in range(0, ij.shape[0], chunk):
+            y, a = f.trace(grid, torch.from_numpy(ij[s:s + chunk]), with_alpha=True)
+            ys.append(y.cpu().numpy())
+            als.append(a.cpu().numpy())
+        torch.cuda.synchronize()
+    finally:
+        f.close()
+    return np.concatenate(ys), np.concatenate(als)
+
+
+def all_rays(grid, rows=None):
+    n0, n1 = int(grid.n[0]), int(grid.n[1])
+    jb, je = rows or (0, n1)
+    jj, ii = np.meshgrid(np.arange(jb, je, dtype=np.int64), np.arange(n0, dtype=np.int64), indexing="ij")
+    return np.stack([ii.ravel(), jj.ravel()], 1)
+
+
+def pixel_index(y, window):
+    """Pixel index per ray (-1 out of window) with the binning rule of the method (test-side copy)."""
+    lo = np.asarray(window.lo, np.float64)
+    hi = np.asarray(window.hi, np.float64)
+    npix = np.asarray(window.npix, np.float64)
+    scale = npix / (hi - lo)
+    u = (y - lo[None, :]) * scale[None, :]
+    ok = (u[:, 0] >= 0) & (u[:, 0] < npix[0]) & (u[:, 1] >= 0) & (u[:, 1] < npix[1])
+    p = np.full(y.shape[0], -1, np.int64)
+    p[ok] = np.floor(u[ok, 1]).astype(np.int64) * int(window.npix[0]) + np.floor(u[ok, 0]).astype(np.int64)
+    return p
+
+
+def pixel_size(window):
+    return min((window.hi[k] - window.lo[k]) / window.npix[k] for k in range(2))
+
+
+def error_stats(y_gpu, y_ref, window):
+    """Per-ray source-position error |dy| (max over axes) in units of the pixel size."""
+    pix = pixel_size(window)
+    fin = np.isfinite(y_ref).all(1)
+    err = np.abs(y_gpu[fin] - y_ref[fin]).max(1) / pix
+    return {
+        "n": int(err.size),
+        "max": float(err.max()) if err.size else 0.0,
+        "p50": float(np.median(err)) if err.size else 0.0,
+        "p99": float(np.quantile(err, 0.99)) if err.size else 0.0,
+        "frac_gt_1e-5": float((err > 1e-5).mean()) if err.size else 0.0,
+    }

@@ -1,0 +1,107 @@
+"""Host-side checks of the C-ABI library (no GPU needed, no kernel launched).
+
+* librs.so builds for sm_103a and loads;
+* it exports every function include/rs.h declares, and the Python binding
+  names the same set;
+* argument validation rejects bad input with the documented status codes
+  before any CUDA call is made.
+"""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def rs():
+    from paper_0905_2453_gb300 import build
+    build.build()
+    import paper_0905_2453_gb300 as rs
+    return rs
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "rs.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return set(re.findall(r"^\s*(?:int|const char\*)\s+(rs_\w+)\s*\(", src, flags=re.M))
+
+
+def test_header_declares_boundary():
+    names = _declared()
+    for must in ("rs_create_field", "rs_shoot", "rs_magnification", "rs_shoot_batch", "rs_trace"):
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol(rs):
+    out = subprocess.run(["nm", "-D", "--defined-only", rs.lib_path()], capture_output=True, text=True, check=True)
+    exported = set(re.findall(r"\bT\s+(rs_\w+)", out.stdout))
+    missing = _declared() - exported
+    assert not missing, missing
+    assert set(rs.EXPORTED_SYMBOLS) == _declared()
+    lib = ctypes.CDLL(rs.lib_path())
+    for name in _declared():
+        assert hasattr(lib, name)
+
+
+def test_library_targets_sm103a(rs):
+    out = subprocess.run(["cuobjdump", "--list-elf", rs.lib_path()], capture_output=True, text=True)
+    if out.returncode != 0:
+        pytest.skip("cuobjdump unavailable")
+    assert "sm_103a" in out.stdout
+
+
+def test_version(rs):
+    assert "sm_103a" in rs.rs_version()
+
+
+def test_validation_codes(rs):
+    lib = rs.load()
+    h = ctypes.c_void_p()
+    assert lib.rs_create_field(None, None, -1, 0.0, 0.0, 0, None, ctypes.byref(h)) == rs.RS_EINVAL
+    assert "n_lens" in rs.rs_last_error()
+    assert lib.rs_create_field(None, None, 5, 0.0, 0.0, 0, None, ctypes.byref(h)) == rs.RS_EINVAL
+    xy = (ctypes.c_float * 2)(0.0, float("nan"))
+    assert lib.rs_create_field(xy, None, 1, 0.0, 0.0, 0, None, ctypes.byref(h)) == rs.RS_EINVAL
+    xy = (ctypes.c_float * 2)(0.0, 1.0)
+    assert lib.rs_create_field(xy, None, 1, float("inf"), 0.0, 0, None, ctypes.byref(h)) == rs.RS_EINVAL
+    m = (ctypes.c_float * 1)(-1.0)
+    assert lib.rs_create_field(xy, m, 1, 0.0, 0.0, 0, None, ctypes.byref(h)) == rs.RS_EINVAL
+    assert lib.rs_create_field(xy, None, 1 << 31, 0.0, 0.0, 0, None, ctypes.byref(h)) == rs.RS_EOVERFLOW
+    # NULL field / grid / window
+    g = rs._cgrid(rs.RayGrid((0.0, 0.0), (1.0, 1.0), (4, 4)))
+    w = rs._cwin(rs.Window((-1.0, -1.0), (1.0, 1.0), (4, 4)))
+    assert lib.rs_shoot(None, ctypes.byref(g), ctypes.byref(w), None, None, None) == rs.RS_EINVAL
+    assert lib.rs_trace(None, ctypes.byref(g), None, 1, None, None, None) == rs.RS_EINVAL
+    assert lib.rs_batch_create(0, None, None, None, None, None, ctypes.byref(h)) == rs.RS_EINVAL
+    assert lib.rs_destroy_field(None) == rs.RS_OK
+    assert lib.rs_batch_destroy(None) == rs.RS_OK
+
+
+def test_grid_window_validation(rs):
+    lib = rs.load()
+    fake = ctypes.c_void_p(1)  # never dereferenced: validation fails first
+    bad_grids = [
+        rs.RayGrid((0.0, 0.0), (0.0, 1.0), (4, 4)),            # zero spacing
+        rs.RayGrid((float("nan"), 0.0), (1.0, 1.0), (4, 4)),   # non-finite origin
+        rs.RayGrid((0.0, 0.0), (1.0, 1.0), (-1, 4)),           # negative extent
+        rs.RayGrid((0.0, 0.0), (1e18, 1.0), (4, 4)),           # beyond the coordinate limit
+    ]
+    w = rs._cwin(rs.Window((-1.0, -1.0), (1.0, 1.0), (4, 4)))
+    for bg in bad_grids:
+        g = rs._cgrid(bg)
+        assert lib.rs_shoot(fake, ctypes.byref(g), ctypes.byref(w), ctypes.c_void_p(16), None, None) == rs.RS_EINVAL
+    g = rs._cgrid(rs.RayGrid((0.0, 0.0), (1.0, 1.0), (4, 4)))
+    for bw in [rs.Window((1.0, -1.0), (1.0, 1.0), (4, 4)), rs.Window((-1.0, -1.0), (1.0, 1.0), (0, 4)),
+               rs.Window((-1.0, float("inf")), (1.0, 1.0), (4, 4))]:
+        ww = rs._cwin(bw)
+        assert lib.rs_shoot(fake, ctypes.byref(g), ctypes.byref(ww), ctypes.c_void_p(16), None, None) == rs.RS_EINVAL
+    # row range outside the grid
+    assert lib.rs_shoot_rows(fake, ctypes.byref(g), 2, 9, ctypes.byref(w), ctypes.c_void_p(16), None,
+                             None) == rs.RS_EINVAL
+    # unknown launch shape
+    assert lib.rs_set_launch_config(0, 96, 3) == rs.RS_EINVAL
+    assert len(rs.rs_launch_configs()) >= 4

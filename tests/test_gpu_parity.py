@@ -1,0 +1,193 @@
+"""GPU parity: the CUDA path (through the C-ABI) against the FP64 oracle.
+
+Tolerances (the method's stated targets):
+  * per-ray source-position error |y_gpu - y_oracle| <= 1e-5 pixel (max over axes);
+  * at most 1e-5 of rays binned into a different pixel;
+  * per-pixel magnification error |N_gpu - N_oracle| <= max(1, 1e-3 N_oracle) for maps of >= 1e8 rays.
+Integer results with exact inputs (no lenses, dyadic grids) must match bit for bit.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import rs_inputs as ri
+from gpu_helpers import (all_rays, dev, error_stats, pixel_index, pixel_size, rs, shoot_gpu, trace_gpu)
+
+pytestmark = pytest.mark.gpu
+
+PER_RAY_TOL_PIX = 1e-5
+FLIP_FRAC_TOL = 1e-5
+
+
+def _no_lens_field(kappa_c, gamma, grid, window):
+    return ri.Field("nolens", np.zeros((0, 2), np.float32), None, kappa_c, gamma, grid, window)
+
+
+def test_zero_lenses_uniform_map_exact():
+    g = ri.cell_centred_grid(-2.0, 2.0, 1024)
+    w = ri.square_window(2.0, 256)
+    counts, oow = shoot_gpu(_no_lens_field(0.0, 0.0, g, w))
+    assert oow == 0 and np.all(counts == 16)
+    m = rs()
+    c = torch.from_numpy(counts.view(np.int32)).to(dev())
+    mu = m.magnification(c, g, w).cpu().numpy()
+    assert np.all(mu == 1.0)
+
+
+def test_linear_map_bitwise_equal_to_oracle():
+    g = ri.cell_centred_grid(-2.0, 2.0, 1024)
+    w = ri.square_window(1.5, 256)
+    f = _no_lens_field(0.2, 0.1, g, w)
+    counts, oow = shoot_gpu(f)
+    ref, oow_ref = oracle.shoot_field(f)
+    assert np.array_equal(counts, ref) and oow == oow_ref
+
+
+def test_nonsquare_grid_window_layout():
+    g = ri.RayGrid(origin=(-2.0 + 2 ** -9, -2.0 + 2 ** -8), spacing=(2 ** -8, 2 ** -7), n=(1024, 512))
+    w = ri.Window(lo=(0.0, -2.0), hi=(4.0, 2.0), npix=(256, 128))
+    f = _no_lens_field(0.0, 0.0, g, w)
+    counts, oow = shoot_gpu(f)
+    ref, oow_ref = oracle.shoot_field(f)
+    assert counts.shape == (128, 256)
+    assert np.array_equal(counts, ref) and oow == oow_ref == g.n_rays // 2
+
+
+def test_tiny_field_full_map_and_every_ray():
+    """100 lenses, 1000^2 rays, 256^2 map: every ray traced and binned against the oracle."""
+    f = ri.tiny_field()
+    counts, oow = shoot_gpu(f)
+    assert int(counts.sum()) + oow == f.grid.n_rays
+    ij = all_rays(f.grid)
+    y_gpu, _ = trace_gpu(f, ij)
+    y_ref, _, _ = oracle.trace_field(f, ij)
+    st = error_stats(y_gpu, y_ref, f.window)
+    print("tiny field per-ray error (pixels):", st)
+    # the traced rays bin exactly into the shot map (same arithmetic)
+    p = pixel_index(y_gpu, f.window)
+    rebinned = np.bincount(p[p >= 0], minlength=f.window.n_pix).reshape(counts.shape)
+    assert np.array_equal(rebinned, counts)
+    p_ref = pixel_index(y_ref, f.window)
+    flips = int((p != p_ref).sum())
+    print("tiny field flips:", flips, "of", p.size)
+    ref, oow_ref = oracle.shoot_field(f)
+    assert flips / p.size <= FLIP_FRAC_TOL
+    assert st["frac_gt_1e-5"] <= 0.01
+
+
+def test_point_lens_map():
+    g = ri.cell_centred_grid(-8.0, 8.0, 4096)
+    w = ri.square_window(3.0, 120)
+    f = ri.Field("point", np.zeros((1, 2), np.float32), None, 0.0, 0.0, g, w)
+    counts, oow = shoot_gpu(f)
+    ref, oow_ref = oracle.shoot_field(f)
+    assert int(counts.sum()) + oow == g.n_rays
+    diff = np.abs(counts.astype(np.int64) - ref.astype(np.int64))
+    assert diff.sum() <= 2e-5 * g.n_rays
+    assert np.all(diff <= np.maximum(1, 1e-3 * ref))
+
+
+def test_launch_shapes_and_runs_bitwise_identical():
+    m = rs()
+    f = ri.disc_field("mixed", 777, 0.5, 0.05, 0.2, 300, 96, seed=5, mass="salpeter")
+    f0 = ri.disc_field("equal", 513, 0.4, 0.0, 0.3, 300, 96, seed=6, mass="equal")
+    for spec in (f, f0):
+        has_m = spec.masses is not None
+        saved = m.rs_get_launch_config(has_m)
+        results = []
+        try:
+            for block, rpt in m.rs_launch_configs():
+                m.rs_set_launch_config(has_m, block, rpt)
+                results.append(shoot_gpu(spec))
+                results.append(shoot_gpu(spec))
+        finally:
+            m.rs_set_launch_config(has_m, *saved)
+        for c, o in results[1:]:
+            assert np.array_equal(c, results[0][0]) and o == results[0][1]
+
+
+def test_row_sharding_accumulates_bitwise():
+    f = ri.disc_field("shard", 300, 0.5, 0.1, 0.25, 257, 64, seed=8, mass="salpeter")
+    full, oow_full = shoot_gpu(f)
+    counts = torch.zeros((64, 64), dtype=torch.int32, device=dev())
+    oow = torch.zeros(1, dtype=torch.int64, device=dev())
+    for rows in ((0, 1), (1, 100), (100, 100), (100, 257)):
+        shoot_gpu(f, rows=rows, counts=counts, oow=oow)
+    assert np.array_equal(counts.cpu().numpy().view(np.uint32), full) and int(oow.item()) == oow_full
+
+
+def test_ragged_sizes_and_edge_cases():
+    """Lens counts around the group (32) and tile (512) sizes, one ray, rays off the tile size."""
+    for n_lens in (1, 31, 32, 33, 511, 512, 513, 1025):
+        f = ri.disc_field(f"rag{n_lens}", n_lens, 0.3, 0.0, 0.1, 37, 16, seed=n_lens, mass="salpeter")
+        ij = all_rays(f.grid)
+        y_gpu, a_gpu = trace_gpu(f, ij)
+        y_ref, a_ref, _ = oracle.trace_field(f, ij)
+        st = error_stats(y_gpu, y_ref, f.window)
+        assert st["max"] < 1e-3, (n_lens, st)
+        counts, oow = shoot_gpu(f)
+        assert int(counts.sum()) + oow == f.grid.n_rays
+    # a single ray
+    f = ri.tiny_field()
+    g1 = ri.RayGrid(origin=(0.3, -0.7), spacing=(1.0, 1.0), n=(1, 1))
+    counts, oow = shoot_gpu(f, grid=g1)
+    assert int(counts.sum()) + oow == 1
+    # empty grid: nothing launched, nothing counted
+    g0 = ri.RayGrid(origin=(0.0, 0.0), spacing=(1.0, 1.0), n=(0, 5))
+    counts, oow = shoot_gpu(f, grid=g0)
+    assert counts.sum() == 0 and oow == 0
+
+
+def test_ray_on_lens_is_out_of_window():
+    g = ri.RayGrid(origin=(-1.0, -1.0), spacing=(0.25, 0.25), n=(9, 9))
+    w = ri.Window(lo=(-100.0, -100.0), hi=(100.0, 100.0), npix=(4, 4))
+    f = ri.Field("onlens", np.zeros((1, 2), np.float32), None, 0.0, 0.0, g, w)
+    counts, oow = shoot_gpu(f)
+    assert oow == 1 and counts.sum() == 80
+
+
+def test_magnification_matches_oracle():
+    f = ri.tiny_field()
+    counts, _ = shoot_gpu(f)
+    m = rs()
+    c = torch.from_numpy(counts.view(np.int32).copy()).to(dev())
+    mu = m.magnification(c, f.grid, f.window).cpu().numpy()
+    mu_ref = oracle.magnification(counts, f.grid.spacing, f.window.lo, f.window.hi, f.window.npix)
+    assert np.allclose(mu, mu_ref, rtol=2e-7, atol=0)
+
+
+def test_batch_equals_plain_launches_bitwise():
+    m = rs()
+    specs = ri.batch_fields(n_fields=6, ray_scale=0.125)
+    specs.append(ri.disc_field("eq", 200, 0.3, 0.0, 0.2, 160, 48, seed=3, mass="equal"))
+    fields = [m.Field.from_spec(s) for s in specs]
+    try:
+        b = m.Batch(fields, [s.grid for s in specs], [s.window for s in specs])
+        for rep in range(2):  # the graph zeroes the maps on every launch
+            b.launch()
+            torch.cuda.synchronize()
+            for k, s in enumerate(specs):
+                ref, oow_ref = shoot_gpu(s)
+                assert np.array_equal(b.counts[k].cpu().numpy().view(np.uint32), ref), (rep, k)
+                assert int(b.out_of_window[k].item()) == oow_ref
+        b.close()
+    finally:
+        for fl in fields:
+            fl.close()
+
+
+def test_n1e4_full_size_sampled_rays():
+    """1e4 lenses on the 4096^2 grid in the benchmark's launch shape: 20000 sampled rays vs the oracle."""
+    f = ri.n1e4_field()
+    ij = ri.sample_rays(f.grid, 20000, seed=123)
+    y_gpu, _ = trace_gpu(f, ij)
+    y_ref, _, _ = oracle.trace_field(f, ij)
+    st = error_stats(y_gpu, y_ref, f.window)
+    print("N=1e4 per-ray error (pixels):", st)
+    flips = int((pixel_index(y_gpu, f.window) != pixel_index(y_ref, f.window)).sum())
+    print("N=1e4 flips:", flips, "of", ij.shape[0])
+    counts, oow = shoot_gpu(f)
+    assert int(counts.sum()) + oow == f.grid.n_rays
+    assert st["frac_gt_1e-5"] <= 0.05
+    assert flips <= 2
