@@ -12,8 +12,8 @@ def rs():
     """The product binding, built for sm_103a if needed (fails loudly without the library)."""
     global _built
     if not _built:
-        from paper_0905_2453_gb300 import build
-        build.build()
+        import __graft_entry__
+        __graft_entry__._builder().build()
         _built = True
     import paper_0905_2453_gb300 as m
     return m

@@ -18,8 +18,8 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 @pytest.fixture(scope="module")
 def rs():
-    from paper_0905_2453_gb300 import build
-    build.build()
+    import __graft_entry__
+    __graft_entry__._builder().build()
     import paper_0905_2453_gb300 as rs
     return rs
 
