@@ -24,16 +24,21 @@
  *   - All kernels run on the device that is current when the call is made;
  *     a field must be used on the device it was created on.
  *   - Coordinates are in Einstein radii of a unit mass (the units of Eq. 2).
- *     Lens and ray coordinates must be finite with |value| <= 1e18.
+ *     Lens and ray coordinates must be finite with |value| <= 1e9 (squared
+ *     distances and their pairwise products then stay within float32 range).
  *
  * Numerics (what the device computes)
  *   - Ray (i, j) sits at x_k = (float) fma(index_k, spacing_k, origin_k): the
  *     double fma rounded to float is the ray position.
  *   - Per lens-ray pair: float32 arithmetic with the hardware approximate
- *     reciprocal; per ray, partial sums over consecutive groups of 32 lenses
- *     (in lens index order) are folded into a two-float (hi, lo) accumulator
- *     with an error-free TwoSum.  The deflection alpha = hi + lo, Eq. 6 and the
- *     pixel index are then evaluated in double precision.
+ *     reciprocal.  Lenses are taken in consecutive pairs; for a fixed subset of
+ *     the pairs (three of every four with unit masses, every other pair with
+ *     per-lens masses) one reciprocal of the product of the two squared
+ *     distances serves both lenses (Montgomery's simultaneous inversion).
+ *     Per ray, partial sums over consecutive groups of 32 lenses (in lens index
+ *     order) are folded into a two-float (hi, lo) accumulator with an
+ *     error-free TwoSum.  The deflection alpha = hi + lo, Eq. 6 and the pixel
+ *     index are then evaluated in double precision.
  *   - The per-ray arithmetic does not depend on launch configuration, so
  *     counts are bitwise reproducible and equal between rs_shoot,
  *     rs_shoot_rows sharding, and the batched path.

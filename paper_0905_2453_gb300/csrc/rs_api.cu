@@ -60,19 +60,19 @@ int cuda_fail(cudaError_t e, const char* what) {
               cudaGetErrorString(e));
 }
 
-constexpr double kCoordLimit = 1e18;
+constexpr double kCoordLimit = 1e9;
 
 bool finite_coord(double v) { return std::isfinite(v) && std::fabs(v) <= kCoordLimit; }
 
 int check_grid(const rs_ray_grid* g) {
   if (!g) return fail(RS_EINVAL, "ray grid is NULL");
   for (int k = 0; k < 2; ++k) {
-    if (!finite_coord(g->origin[k])) return fail(RS_EINVAL, "grid origin[%d] not finite or beyond 1e18", k);
+    if (!finite_coord(g->origin[k])) return fail(RS_EINVAL, "grid origin[%d] not finite or beyond 1e9", k);
     if (!(std::isfinite(g->spacing[k]) && g->spacing[k] > 0.0))
       return fail(RS_EINVAL, "grid spacing[%d] must be finite and > 0", k);
     if (g->n[k] < 0) return fail(RS_EINVAL, "grid n[%d] < 0", k);
     const double far = g->origin[k] + (double)(g->n[k] > 0 ? g->n[k] - 1 : 0) * g->spacing[k];
-    if (!finite_coord(far)) return fail(RS_EINVAL, "grid extent along axis %d beyond 1e18", k);
+    if (!finite_coord(far)) return fail(RS_EINVAL, "grid extent along axis %d beyond 1e9", k);
   }
   return RS_OK;
 }
@@ -169,7 +169,7 @@ int fill_desc(const rs_field* f, const rs_ray_grid* g, int64_t row_begin, int64_
   d->sp1 = g->spacing[1];
   d->n0 = g->n[0];
   d->j_begin = row_begin;
-  d->n_rays = n_rays;
+  d->n_rows = rows;
   d->lo0 = w->lo[0];
   d->lo1 = w->lo[1];
   d->sc0 = (double)w->npix[0] / (w->hi[0] - w->lo[0]);
@@ -222,7 +222,7 @@ int rs_create_field(const float* lens_xy, const float* masses, int64_t n_lens, d
   if (!std::isfinite(kappa_c) || !std::isfinite(gamma)) return fail(RS_EINVAL, "kappa_c and gamma must be finite");
   if (!inputs_on_device) {
     for (int64_t i = 0; i < 2 * n_lens; ++i)
-      if (!finite_coord((double)lens_xy[i])) return fail(RS_EINVAL, "lens coordinate %lld not finite or beyond 1e18", (long long)i);
+      if (!finite_coord((double)lens_xy[i])) return fail(RS_EINVAL, "lens coordinate %lld not finite or beyond 1e9", (long long)i);
     if (masses)
       for (int64_t i = 0; i < n_lens; ++i)
         if (!(std::isfinite(masses[i]) && masses[i] >= 0.f)) return fail(RS_EINVAL, "mass %lld not finite or negative", (long long)i);
@@ -364,7 +364,7 @@ int rs_shoot_rows(rs_field_t f, const rs_ray_grid* g, int64_t row_begin, int64_t
   if ((rc = check_field_device(f)) != RS_OK) return rc;
   ShootDesc d;
   if ((rc = fill_desc(f, g, row_begin, row_end, w, d_counts, d_out_of_window, &d)) != RS_OK) return rc;
-  if (d.n_rays == 0) return RS_OK;
+  if (d.n_rows == 0 || d.n0 == 0) return RS_OK;
   cudaError_t e = rsint::launch_shoot(g_cfg[f->dev.has_mass ? 1 : 0], d, reinterpret_cast<cudaStream_t>(stream));
   if (e != cudaSuccess) return cuda_fail(e, "shoot kernel launch");
   return RS_OK;
@@ -427,7 +427,8 @@ int rs_batch_create(int n_fields, const rs_field_t* fields, const rs_ray_grid* g
   if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
   int rc;
   const int cfg = g_cfg[1];
-  const int64_t per = (int64_t)rsint::kCfgs[cfg].block * rsint::kCfgs[cfg].rpt;
+  const int warps = rsint::kCfgs[cfg].block / 32;
+  const int64_t seg = 32 * (int64_t)rsint::kCfgs[cfg].rpt;
   std::vector<ShootDesc> descs(n_fields);
   struct Item {
     double cost;
@@ -444,12 +445,17 @@ int rs_batch_create(int n_fields, const rs_field_t* fields, const rs_ray_grid* g
     if ((rc = fill_desc(fields[k], &grids[k], 0, grids[k].n[1], &windows[k], d_counts[k],
                         d_out_of_window ? d_out_of_window + k : nullptr, &descs[k])) != RS_OK)
       return rc;
-    const int64_t nt = (descs[k].n_rays + per - 1) / per;
+    const int64_t n0 = descs[k].n0, nr = descs[k].n_rows;
+    if (n0 == 0 || nr == 0) continue;
+    const int64_t ncol = (n0 + seg - 1) / seg;
+    const int64_t nt = ((nr + warps - 1) / warps) * ncol;
     if ((int64_t)items.size() + nt >= ((int64_t)1 << 31)) return fail(RS_EOVERFLOW, "too many work items");
     for (int64_t t = 0; t < nt; ++t) {
-      const int64_t rays = std::min<int64_t>(per, descs[k].n_rays - t * per);
+      const int64_t trow = t / ncol, tcol = t - trow * ncol;
+      const int64_t rows = std::min<int64_t>(warps, nr - trow * warps);
+      const int64_t cols = std::min<int64_t>(seg, n0 - tcol * seg);
       // per-ray cost: one interaction per lens plus a fixed epilogue (~ 64 interactions)
-      const double cost = (double)rays * ((double)fields[k]->n_lens + 64.0);
+      const double cost = (double)(rows * cols) * ((double)fields[k]->n_lens + 64.0);
       items.push_back({cost, k, (int)t});
     }
   }

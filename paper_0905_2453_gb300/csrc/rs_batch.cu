@@ -10,8 +10,8 @@ namespace {
 
 using namespace rsdev;
 
-template <int BLOCK, int RPT, int TILE>
-__global__ void __launch_bounds__(BLOCK)
+template <int WARPS, int RPT, int TILE>
+__global__ void __launch_bounds__(WARPS * 32)
     batch_kernel(const ShootDesc* __restrict__ descs, const int2* __restrict__ items, int n_items, int* counter) {
   __shared__ LensSmem<TILE> sm;
   __shared__ int s_item;
@@ -25,23 +25,23 @@ __global__ void __launch_bounds__(BLOCK)
     if (it >= n_items) break;
     const int2 w = items[it];
     const ShootDesc& d = descs[w.x];
-    const int64_t base = (int64_t)w.y * (BLOCK * RPT);
-    const bool ok = d.f.has_mass ? shoot_tile<BLOCK, RPT, TILE, true>(d, base, sm, ps)
-                                 : shoot_tile<BLOCK, RPT, TILE, false>(d, base, sm, ps);
+    const bool ok = d.f.has_mass ? shoot_tile<WARPS, RPT, TILE, true>(d, (int64_t)w.y, sm, ps)
+                                 : shoot_tile<WARPS, RPT, TILE, false>(d, (int64_t)w.y, sm, ps);
     if (!ok) break;
   }
 }
 
-template <int BLOCK, int RPT>
+template <int WARPS, int RPT>
 cudaError_t launch_batch_t(const ShootDesc* descs, const int2* items, int n_items, int* counter, int grid,
                            cudaStream_t s) {
-  batch_kernel<BLOCK, RPT, rsint::kTile><<<grid, BLOCK, 0, s>>>(descs, items, n_items, counter);
+  batch_kernel<WARPS, RPT, rsint::kTile><<<grid, WARPS * 32, 0, s>>>(descs, items, n_items, counter);
   return cudaGetLastError();
 }
 
-template <int BLOCK, int RPT>
+template <int WARPS, int RPT>
 cudaError_t occ_t(int* blocks) {
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, batch_kernel<BLOCK, RPT, rsint::kTile>, BLOCK, 0);
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, batch_kernel<WARPS, RPT, rsint::kTile>, WARPS * 32,
+                                                       0);
 }
 
 }  // namespace
@@ -51,24 +51,24 @@ namespace rsint {
 cudaError_t launch_batch(int cfg, const rsdev::ShootDesc* descs, const int2* items, int n_items, int* counter,
                          int grid, cudaStream_t s) {
   switch (cfg) {
-    case 0: return launch_batch_t<128, 4>(descs, items, n_items, counter, grid, s);
-    case 1: return launch_batch_t<128, 8>(descs, items, n_items, counter, grid, s);
-    case 2: return launch_batch_t<256, 4>(descs, items, n_items, counter, grid, s);
-    case 3: return launch_batch_t<256, 8>(descs, items, n_items, counter, grid, s);
-    case 4: return launch_batch_t<512, 4>(descs, items, n_items, counter, grid, s);
-    case 5: return launch_batch_t<256, 12>(descs, items, n_items, counter, grid, s);
+    case 0: return launch_batch_t<4, 4>(descs, items, n_items, counter, grid, s);
+    case 1: return launch_batch_t<4, 8>(descs, items, n_items, counter, grid, s);
+    case 2: return launch_batch_t<8, 4>(descs, items, n_items, counter, grid, s);
+    case 3: return launch_batch_t<8, 8>(descs, items, n_items, counter, grid, s);
+    case 4: return launch_batch_t<16, 4>(descs, items, n_items, counter, grid, s);
+    case 5: return launch_batch_t<8, 12>(descs, items, n_items, counter, grid, s);
     default: return cudaErrorInvalidValue;
   }
 }
 
 cudaError_t batch_blocks_per_sm(int cfg, int* blocks) {
   switch (cfg) {
-    case 0: return occ_t<128, 4>(blocks);
-    case 1: return occ_t<128, 8>(blocks);
-    case 2: return occ_t<256, 4>(blocks);
-    case 3: return occ_t<256, 8>(blocks);
-    case 4: return occ_t<512, 4>(blocks);
-    case 5: return occ_t<256, 12>(blocks);
+    case 0: return occ_t<4, 4>(blocks);
+    case 1: return occ_t<4, 8>(blocks);
+    case 2: return occ_t<8, 4>(blocks);
+    case 3: return occ_t<8, 8>(blocks);
+    case 4: return occ_t<16, 4>(blocks);
+    case 5: return occ_t<8, 12>(blocks);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -175,7 +175,7 @@ struct ShootDesc {
   double or0, or1, sp0, sp1;  // ray grid origin and spacing
   int64_t n0;                 // rays per grid row
   int64_t j_begin;            // first grid row of this call
-  int64_t n_rays;             // rays in this call (rows x n0), < 2^32
+  int64_t n_rows;             // grid rows in this call (rows x n0 < 2^32 rays)
   double lo0, lo1, sc0, sc1;  // window lower corner and npix / (hi - lo)
   int32_t np0, np1;           // pixels per axis
   uint32_t* counts;           // [np1][np0]
@@ -224,16 +224,116 @@ __device__ __forceinline__ float ray_coord(int64_t idx, double spacing, double o
 }
 
 // ----------------------------------------------------------------------------------------------
-// Deflection of RPT rays per thread by all lenses of the field.
-// x1/x2 in, alpha1/alpha2 (double) out.  Returns false if a bounded wait gave up (the CTA
-// then must stop; the status word has been set).
+// Lens-pair step.  Two consecutive lenses a, b against one ray pair (lanes A, B of each operand).
+// d1 = x1 - x1_lens; r2 = d1^2 + d2^2 with d2^2 (S2) supplied; w = m / r2; P += w * (d1, d2).
+//
+// MONT: one reciprocal serves both lenses (Montgomery's simultaneous inversion):
+//   inv = 1 / (r2a * r2b),  1/r2a = r2b * inv,  1/r2b = r2a * inv.
+// Two MUFU operations per ray pair instead of four, for three extra packed multiplies on the
+// FMA pipe.  With |coordinates| <= 1e9 the product stays below 6.4e37 (no overflow); it can
+// only underflow when the ray is within ~3e-10 of one of the two lenses, a ray whose own
+// deflection is then ~1e9 (out of any window), and only that ray is affected.
 // ----------------------------------------------------------------------------------------------
-template <int BLOCK, int RPT, int TILE, bool MASS>
+template <bool MONT, bool MASS>
+__device__ __forceinline__ void lens_pair_step(uint64_t X1, uint64_t Lxa, uint64_t Lxb, uint64_t D2a, uint64_t S2a,
+                                               uint64_t D2b, uint64_t S2b, uint64_t Ma, uint64_t Mb, uint64_t& P1,
+                                               uint64_t& P2) {
+  const uint64_t d1a = f2_sub(X1, Lxa);
+  const uint64_t d1b = f2_sub(X1, Lxb);
+  const uint64_t r2a = f2_fma(d1a, d1a, S2a);
+  const uint64_t r2b = f2_fma(d1b, d1b, S2b);
+  uint64_t wa, wb;
+  if (MONT) {
+    const uint64_t pr = f2_mul(r2a, r2b);
+    float p0, p1;
+    f2_unpack(pr, p0, p1);
+    const uint64_t inv = f2_pack(rcp_approx(p0), rcp_approx(p1));
+    wa = f2_mul(r2b, inv);
+    wb = f2_mul(r2a, inv);
+  } else {
+    float a0, a1, b0, b1;
+    f2_unpack(r2a, a0, a1);
+    f2_unpack(r2b, b0, b1);
+    wa = f2_pack(rcp_approx(a0), rcp_approx(a1));
+    wb = f2_pack(rcp_approx(b0), rcp_approx(b1));
+  }
+  if (MASS) {
+    wa = f2_mul(wa, Ma);
+    wb = f2_mul(wb, Mb);
+  }
+  P1 = f2_fma(wa, d1a, P1);
+  P2 = f2_fma(wa, D2a, P2);
+  P1 = f2_fma(wb, d1b, P1);
+  P2 = f2_fma(wb, D2b, P2);
+}
+
+// A single lens (the odd last lens of a field), direct reciprocal.
+template <bool MASS>
+__device__ __forceinline__ void lens_single_step(uint64_t X1, uint64_t Lx, uint64_t D2, uint64_t S2, uint64_t M,
+                                                 uint64_t& P1, uint64_t& P2) {
+  const uint64_t d1 = f2_sub(X1, Lx);
+  const uint64_t r2 = f2_fma(d1, d1, S2);
+  float a0, a1;
+  f2_unpack(r2, a0, a1);
+  uint64_t w = f2_pack(rcp_approx(a0), rcp_approx(a1));
+  if (MASS) w = f2_mul(w, M);
+  P1 = f2_fma(w, d1, P1);
+  P2 = f2_fma(w, D2, P2);
+}
+
+// Which lens pairs of a group use the shared reciprocal: pair index p within its group.
+// Unit masses: three of every four pairs; per-lens masses (one more multiply per lens): every
+// other pair.  These ratios balance the FMA and MUFU pipes; they are fixed, so every ray of a
+// field always gets the same arithmetic.
+template <bool MASS>
+__device__ __forceinline__ constexpr bool mont_pair(int p) {
+  return MASS ? ((p & 1) == 0) : ((p & 3) != 3);
+}
+
+// Loads lens l of the current shared-memory buffer: Lx = {x1, x1}, Ly = {x2, x2}, M = {m, m}.
+template <bool MASS>
+__device__ __forceinline__ void load_lens(uint32_t lbase, uint32_t mbase, int l, uint64_t& Lx, uint64_t& Ly,
+                                          uint64_t& M) {
+  lds_pair2(lbase + (uint32_t)l * 16u, Lx, Ly);
+  M = MASS ? lds_pair(mbase + (uint32_t)l * 8u) : 0ull;
+}
+
+// One lens pair (lenses l, l + 1) against all ray pairs of the thread.
+// ROW: all rays of the thread share x2 (one grid row): d2 and d2^2 are formed once per lens.
+template <int NP, bool MONT, bool MASS, bool ROW>
+__device__ __forceinline__ void lens_pair_all(uint32_t lbase, uint32_t mbase, int l, const uint64_t (&X1)[NP],
+                                              const uint64_t (&X2)[NP], uint64_t X2D, uint64_t (&P1)[NP],
+                                              uint64_t (&P2)[NP]) {
+  uint64_t Lxa, Lya, Ma, Lxb, Lyb, Mb;
+  load_lens<MASS>(lbase, mbase, l, Lxa, Lya, Ma);
+  load_lens<MASS>(lbase, mbase, l + 1, Lxb, Lyb, Mb);
+  if (ROW) {
+    const uint64_t D2a = f2_sub(X2D, Lya), D2b = f2_sub(X2D, Lyb);
+    const uint64_t S2a = f2_mul(D2a, D2a), S2b = f2_mul(D2b, D2b);
+#pragma unroll
+    for (int q = 0; q < NP; ++q) lens_pair_step<MONT, MASS>(X1[q], Lxa, Lxb, D2a, S2a, D2b, S2b, Ma, Mb, P1[q], P2[q]);
+  } else {
+#pragma unroll
+    for (int q = 0; q < NP; ++q) {
+      const uint64_t D2a = f2_sub(X2[q], Lya), D2b = f2_sub(X2[q], Lyb);
+      const uint64_t S2a = f2_mul(D2a, D2a), S2b = f2_mul(D2b, D2b);
+      lens_pair_step<MONT, MASS>(X1[q], Lxa, Lxb, D2a, S2a, D2b, S2b, Ma, Mb, P1[q], P2[q]);
+    }
+  }
+}
+
+// ----------------------------------------------------------------------------------------------
+// Deflection of RPT rays per thread by all lenses of the field (Eq. 2).
+// X1/X2: packed ray coordinates (pairs of rays); X2D = {x2, x2} when ROW (all rays share x2).
+// alpha1/alpha2 (double) out.  Returns false if a bounded wait gave up (the CTA must then stop;
+// the status word has been set).  The arithmetic per ray depends only on the ray and the field.
+// ----------------------------------------------------------------------------------------------
+template <int RPT, int TILE, bool MASS, bool ROW>
 __device__ __forceinline__ bool deflect(const FieldDev& f, const float (&x1)[RPT], const float (&x2)[RPT],
                                         double (&a1)[RPT], double (&a2)[RPT], LensSmem<TILE>& sm,
                                         PipeState& ps) {
   static_assert(RPT % 2 == 0, "rays per thread must be even (packed pairs)");
-  static_assert(TILE % kGroup == 0, "lens tile must hold whole lens groups");
+  static_assert(TILE % kGroup == 0 && kGroup % 8 == 0, "lens tile must hold whole lens groups");
   constexpr int NP = RPT / 2;
   uint64_t X1[NP], X2[NP], H1[NP], L1[NP], H2[NP], L2[NP];
 #pragma unroll
@@ -242,6 +342,7 @@ __device__ __forceinline__ bool deflect(const FieldDev& f, const float (&x1)[RPT
     X2[q] = f2_pack(x2[2 * q], x2[2 * q + 1]);
     H1[q] = L1[q] = H2[q] = L2[q] = 0ull;
   }
+  const uint64_t X2D = f2_pack(x2[0], x2[0]);
   const int n = f.n_lens;
   const int ntiles = (n + TILE - 1) / TILE;
   bool ok = true;
@@ -266,23 +367,13 @@ __device__ __forceinline__ bool deflect(const FieldDev& f, const float (&x1)[RPT
       uint64_t P1[NP], P2[NP];
 #pragma unroll
       for (int q = 0; q < NP; ++q) P1[q] = P2[q] = 0ull;
-#pragma unroll 8
-      for (int l = 0; l < kGroup; ++l) {
-        uint64_t Lx, Ly, Lm = 0;
-        lds_pair2(lbase + (uint32_t)(g + l) * 16u, Lx, Ly);
-        if (MASS) Lm = lds_pair(mbase + (uint32_t)(g + l) * 8u);
-#pragma unroll
-        for (int q = 0; q < NP; ++q) {
-          const uint64_t d1 = f2_sub(X1[q], Lx);
-          const uint64_t d2 = f2_sub(X2[q], Ly);
-          const uint64_t r2 = f2_fma(d2, d2, f2_mul(d1, d1));
-          float ra, rb;
-          f2_unpack(r2, ra, rb);
-          uint64_t w = f2_pack(rcp_approx(ra), rcp_approx(rb));
-          if (MASS) w = f2_mul(w, Lm);
-          P1[q] = f2_fma(w, d1, P1[q]);
-          P2[q] = f2_fma(w, d2, P2[q]);
-        }
+#pragma unroll 1
+      for (int p4 = 0; p4 < kGroup / 8; ++p4) {  // blocks of four lens pairs: fixed reciprocal pattern
+        const int l = g + p4 * 8;
+        lens_pair_all<NP, mont_pair<MASS>(0), MASS, ROW>(lbase, mbase, l + 0, X1, X2, X2D, P1, P2);
+        lens_pair_all<NP, mont_pair<MASS>(1), MASS, ROW>(lbase, mbase, l + 2, X1, X2, X2D, P1, P2);
+        lens_pair_all<NP, mont_pair<MASS>(2), MASS, ROW>(lbase, mbase, l + 4, X1, X2, X2D, P1, P2);
+        lens_pair_all<NP, mont_pair<MASS>(3), MASS, ROW>(lbase, mbase, l + 6, X1, X2, X2D, P1, P2);
       }
 #pragma unroll
       for (int q = 0; q < NP; ++q) {
@@ -290,25 +381,24 @@ __device__ __forceinline__ bool deflect(const FieldDev& f, const float (&x1)[RPT
         twosum_accumulate(H2[q], L2[q], P2[q]);
       }
     }
-    if (g < cnt) {  // last, partial group of the field
+    if (g < cnt) {  // last, partial group of the field: same pattern by pair index, odd lens direct
       uint64_t P1[NP], P2[NP];
 #pragma unroll
       for (int q = 0; q < NP; ++q) P1[q] = P2[q] = 0ull;
-      for (int l = g; l < cnt; ++l) {
-        uint64_t Lx, Ly, Lm = 0;
-        lds_pair2(lbase + (uint32_t)l * 16u, Lx, Ly);
-        if (MASS) Lm = lds_pair(mbase + (uint32_t)l * 8u);
+      int p = 0;
+      for (; g + 2 * p + 1 < cnt; ++p) {
+        if (mont_pair<MASS>(p))
+          lens_pair_all<NP, true, MASS, ROW>(lbase, mbase, g + 2 * p, X1, X2, X2D, P1, P2);
+        else
+          lens_pair_all<NP, false, MASS, ROW>(lbase, mbase, g + 2 * p, X1, X2, X2D, P1, P2);
+      }
+      if (g + 2 * p < cnt) {
+        uint64_t Lx, Ly, M;
+        load_lens<MASS>(lbase, mbase, g + 2 * p, Lx, Ly, M);
 #pragma unroll
         for (int q = 0; q < NP; ++q) {
-          const uint64_t d1 = f2_sub(X1[q], Lx);
-          const uint64_t d2 = f2_sub(X2[q], Ly);
-          const uint64_t r2 = f2_fma(d2, d2, f2_mul(d1, d1));
-          float ra, rb;
-          f2_unpack(r2, ra, rb);
-          uint64_t w = f2_pack(rcp_approx(ra), rcp_approx(rb));
-          if (MASS) w = f2_mul(w, Lm);
-          P1[q] = f2_fma(w, d1, P1[q]);
-          P2[q] = f2_fma(w, d2, P2[q]);
+          const uint64_t D2 = f2_sub(ROW ? X2D : X2[q], Ly);
+          lens_single_step<MASS>(X1[q], Lx, D2, f2_mul(D2, D2), M, P1[q], P2[q]);
         }
       }
 #pragma unroll
@@ -344,25 +434,38 @@ __device__ __forceinline__ bool deflect(const FieldDev& f, const float (&x1)[RPT
 }
 
 // ----------------------------------------------------------------------------------------------
-// One ray tile of a shoot call: rays ray_base + k*BLOCK + tid (k < RPT) of the call's rays.
+// Ray tiles of a shoot call.  A CTA of WARPS warps covers WARPS consecutive grid rows (one per
+// warp) by 32 * RPT consecutive columns; lane l of a warp holds columns c0 + l + 32 k, k < RPT.
 // ----------------------------------------------------------------------------------------------
-template <int BLOCK, int RPT, int TILE, bool MASS>
-__device__ __forceinline__ bool shoot_tile(const ShootDesc& d, int64_t ray_base, LensSmem<TILE>& sm,
-                                           PipeState& ps) {
+template <int WARPS, int RPT>
+__host__ __device__ __forceinline__ int64_t shoot_tiles(int64_t n_rows, int64_t n0) {
+  const int64_t seg = 32 * RPT;
+  return ((n_rows + WARPS - 1) / WARPS) * ((n0 + seg - 1) / seg);
+}
+
+template <int WARPS, int RPT, int TILE, bool MASS>
+__device__ __forceinline__ bool shoot_tile(const ShootDesc& d, int64_t tile, LensSmem<TILE>& sm, PipeState& ps) {
+  constexpr int SEG = 32 * RPT;
+  const int64_t ncol = (d.n0 + SEG - 1) / SEG;
+  const int64_t trow = tile / ncol;
+  const int64_t tcol = tile - trow * ncol;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t jrel = trow * WARPS + warp;
+  const bool row_ok = jrel < d.n_rows;
+  const int64_t j = d.j_begin + (row_ok ? jrel : d.n_rows - 1);
+  const float x2r = ray_coord(j, d.sp1, d.or1);
   float x1[RPT], x2[RPT];
   bool valid[RPT];
 #pragma unroll
   for (int k = 0; k < RPT; ++k) {
-    int64_t r = ray_base + (int64_t)k * BLOCK + threadIdx.x;
-    valid[k] = r < d.n_rays;
-    if (!valid[k]) r = d.n_rays - 1;
-    const int64_t j = d.j_begin + r / d.n0;
-    const int64_t i = r - (r / d.n0) * d.n0;
+    int64_t i = tcol * SEG + lane + 32 * k;
+    valid[k] = row_ok && i < d.n0;
+    if (i >= d.n0) i = d.n0 - 1;
     x1[k] = ray_coord(i, d.sp0, d.or0);
-    x2[k] = ray_coord(j, d.sp1, d.or1);
+    x2[k] = x2r;
   }
   double a1[RPT], a2[RPT];
-  if (!deflect<BLOCK, RPT, TILE, MASS>(d.f, x1, x2, a1, a2, sm, ps)) return false;
+  if (!deflect<RPT, TILE, MASS, true>(d.f, x1, x2, a1, a2, sm, ps)) return false;
   unsigned oow_lane = 0;
 #pragma unroll
   for (int k = 0; k < RPT; ++k) {
@@ -380,8 +483,7 @@ __device__ __forceinline__ bool shoot_tile(const ShootDesc& d, int64_t ray_base,
     const unsigned miss = __ballot_sync(0xffffffffu, valid[k] && !inwin);
     oow_lane += __popc(miss);
   }
-  if (d.oow != nullptr && (threadIdx.x & 31) == 0 && oow_lane != 0)
-    atomicAdd(d.oow, (unsigned long long)oow_lane);
+  if (d.oow != nullptr && lane == 0 && oow_lane != 0) atomicAdd(d.oow, (unsigned long long)oow_lane);
   return true;
 }
 

@@ -13,8 +13,9 @@ namespace rsint {
 constexpr int kTile = 512;
 
 // Launch shapes compiled into the library; the per-ray arithmetic is identical for all.
+// A CTA of block / 32 warps covers block / 32 grid rows by 32 * rpt columns.
 struct KernelCfg {
-  int block;  // threads per CTA
+  int block;  // threads per CTA (a multiple of 32)
   int rpt;    // rays per thread (even: packed pairs)
 };
 constexpr int kNumCfg = 6;

@@ -5,12 +5,12 @@ namespace {
 
 using namespace rsdev;
 
-template <int BLOCK, int RPT, int TILE, bool MASS>
-__global__ void __launch_bounds__(BLOCK) shoot_kernel(const ShootDesc d) {
+template <int WARPS, int RPT, int TILE, bool MASS>
+__global__ void __launch_bounds__(WARPS * 32) shoot_kernel(const ShootDesc d) {
   __shared__ LensSmem<TILE> sm;
   PipeState ps;
   pipe_init(sm.bar, ps);
-  (void)shoot_tile<BLOCK, RPT, TILE, MASS>(d, (int64_t)blockIdx.x * (BLOCK * RPT), sm, ps);
+  (void)shoot_tile<WARPS, RPT, TILE, MASS>(d, (int64_t)blockIdx.x, sm, ps);
 }
 
 template <int BLOCK, int RPT, int TILE, bool MASS>
@@ -32,7 +32,7 @@ __global__ void __launch_bounds__(BLOCK)
     x2[q] = ray_coord(ij[2 * r + 1], sp1, or1);
   }
   double a1[RPT], a2[RPT];
-  if (!deflect<BLOCK, RPT, TILE, MASS>(f, x1, x2, a1, a2, sm, ps)) return;
+  if (!deflect<RPT, TILE, MASS, false>(f, x1, x2, a1, a2, sm, ps)) return;
 #pragma unroll
   for (int q = 0; q < RPT; ++q) {
     if (!valid[q]) continue;
@@ -46,15 +46,15 @@ __global__ void __launch_bounds__(BLOCK)
   }
 }
 
-template <int BLOCK, int RPT>
+template <int WARPS, int RPT>
 cudaError_t launch_shoot_t(const ShootDesc& d, cudaStream_t s) {
-  const int64_t per = (int64_t)BLOCK * RPT;
-  const int64_t grid = (d.n_rays + per - 1) / per;
+  const int64_t grid = shoot_tiles<WARPS, RPT>(d.n_rows, d.n0);
   if (grid <= 0) return cudaSuccess;
+  if (grid >= ((int64_t)1 << 31)) return cudaErrorInvalidValue;
   if (d.f.has_mass)
-    shoot_kernel<BLOCK, RPT, rsint::kTile, true><<<(unsigned)grid, BLOCK, 0, s>>>(d);
+    shoot_kernel<WARPS, RPT, rsint::kTile, true><<<(unsigned)grid, WARPS * 32, 0, s>>>(d);
   else
-    shoot_kernel<BLOCK, RPT, rsint::kTile, false><<<(unsigned)grid, BLOCK, 0, s>>>(d);
+    shoot_kernel<WARPS, RPT, rsint::kTile, false><<<(unsigned)grid, WARPS * 32, 0, s>>>(d);
   return cudaGetLastError();
 }
 
@@ -64,12 +64,12 @@ namespace rsint {
 
 cudaError_t launch_shoot(int cfg, const rsdev::ShootDesc& d, cudaStream_t s) {
   switch (cfg) {
-    case 0: return launch_shoot_t<128, 4>(d, s);
-    case 1: return launch_shoot_t<128, 8>(d, s);
-    case 2: return launch_shoot_t<256, 4>(d, s);
-    case 3: return launch_shoot_t<256, 8>(d, s);
-    case 4: return launch_shoot_t<512, 4>(d, s);
-    case 5: return launch_shoot_t<256, 12>(d, s);
+    case 0: return launch_shoot_t<4, 4>(d, s);
+    case 1: return launch_shoot_t<4, 8>(d, s);
+    case 2: return launch_shoot_t<8, 4>(d, s);
+    case 3: return launch_shoot_t<8, 8>(d, s);
+    case 4: return launch_shoot_t<16, 4>(d, s);
+    case 5: return launch_shoot_t<8, 12>(d, s);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -95,3 +95,31 @@ def error_stats(y_gpu, y_ref, window):
         "p99": float(np.quantile(err, 0.99)) if err.size else 0.0,
         "frac_gt_1e-5": float((err > 1e-5).mean()) if err.size else 0.0,
     }
+
+
+def abs_term_sum(field_spec, x):
+    """sum_i m_i / |x - x_i| per ray (float64), the scale of a rigorous FP32 error bound."""
+    L = field_spec.lens_xy.astype(np.float64)
+    m = None if field_spec.masses is None else field_spec.masses.astype(np.float64)
+    out = np.zeros(x.shape[0])
+    for s in range(0, L.shape[0], 4096):
+        d = x[:, None, :] - L[None, s:s + 4096, :]
+        r = np.sqrt((d ** 2).sum(-1))
+        t = 1.0 / r if m is None else m[None, s:s + 4096] / r
+        out += t.sum(1)
+    return out
+
+
+U32 = 2.0 ** -24
+# Worst-case relative error constants of the float32 body (units of u = 2^-24):
+#   per term: d1/d2 rounding (1), d^2 and the fma forming r^2 (2), rcp.approx (<= 1 ulp: 2),
+#   shared-reciprocal product and back-multiply (2), mass multiply (1)          -> 8
+#   accumulation of a 32-lens group in float32: gamma_32 ~ 32                   -> 32
+# The (hi, lo) TwoSum fold across groups is error-free; the float64 epilogue adds ~1e-16.
+K_TERM, K_GROUP = 8.0, 32.0
+
+
+def per_ray_bound(field_spec, x, y_ref):
+    """Rigorous bound on |y_gpu - y_exact| per ray for the float32 path."""
+    B = abs_term_sum(field_spec, x)
+    return (K_TERM + K_GROUP) * U32 * B + 1e-15 * (np.abs(y_ref).max(1) + np.abs(x).max(1))

