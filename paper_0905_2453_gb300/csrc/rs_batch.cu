@@ -13,7 +13,7 @@ using namespace rsdev;
 template <int WARPS, int RPT, int TILE>
 __global__ void __launch_bounds__(WARPS * 32)
     batch_kernel(const ShootDesc* __restrict__ descs, const int2* __restrict__ items, int n_items, int* counter) {
-  __shared__ LensSmem<TILE> sm;
+  __shared__ LensSmem<TILE, WARPS> sm;
   __shared__ int s_item;
   PipeState ps;
   pipe_init(sm.bar, ps);
@@ -51,24 +51,24 @@ namespace rsint {
 cudaError_t launch_batch(int cfg, const rsdev::ShootDesc* descs, const int2* items, int n_items, int* counter,
                          int grid, cudaStream_t s) {
   switch (cfg) {
-    case 0: return launch_batch_t<4, 4>(descs, items, n_items, counter, grid, s);
-    case 1: return launch_batch_t<4, 8>(descs, items, n_items, counter, grid, s);
-    case 2: return launch_batch_t<8, 4>(descs, items, n_items, counter, grid, s);
-    case 3: return launch_batch_t<8, 8>(descs, items, n_items, counter, grid, s);
-    case 4: return launch_batch_t<16, 4>(descs, items, n_items, counter, grid, s);
-    case 5: return launch_batch_t<8, 12>(descs, items, n_items, counter, grid, s);
+    case 0: return launch_batch_t<2, 8>(descs, items, n_items, counter, grid, s);
+    case 1: return launch_batch_t<4, 4>(descs, items, n_items, counter, grid, s);
+    case 2: return launch_batch_t<4, 8>(descs, items, n_items, counter, grid, s);
+    case 3: return launch_batch_t<8, 4>(descs, items, n_items, counter, grid, s);
+    case 4: return launch_batch_t<8, 8>(descs, items, n_items, counter, grid, s);
+    case 5: return launch_batch_t<8, 6>(descs, items, n_items, counter, grid, s);
     default: return cudaErrorInvalidValue;
   }
 }
 
 cudaError_t batch_blocks_per_sm(int cfg, int* blocks) {
   switch (cfg) {
-    case 0: return occ_t<4, 4>(blocks);
-    case 1: return occ_t<4, 8>(blocks);
-    case 2: return occ_t<8, 4>(blocks);
-    case 3: return occ_t<8, 8>(blocks);
-    case 4: return occ_t<16, 4>(blocks);
-    case 5: return occ_t<8, 12>(blocks);
+    case 0: return occ_t<2, 8>(blocks);
+    case 1: return occ_t<4, 4>(blocks);
+    case 2: return occ_t<4, 8>(blocks);
+    case 3: return occ_t<8, 4>(blocks);
+    case 4: return occ_t<8, 8>(blocks);
+    case 5: return occ_t<8, 6>(blocks);
     default: return cudaErrorInvalidValue;
   }
 }

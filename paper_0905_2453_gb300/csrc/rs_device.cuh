@@ -182,10 +182,12 @@ struct ShootDesc {
   unsigned long long* oow;    // out-of-window counter or nullptr
 };
 
-template <int TILE>
+template <int TILE, int ROWS = 1>
 struct __align__(16) LensSmem {
-  float4 lens4[2][TILE];
-  float2 mass2[2][TILE];
+  float4 lens4[2][TILE];     // double-buffered lens tiles {x1, x1, x2, x2}
+  float2 mass2[2][TILE];     // {m, m}
+  float4 rowtab[ROWS][TILE]; // per CTA row r and lens l of the current tile: {d2, d2, d2^2, d2^2}
+  float x2row[ROWS];         // x2 of the CTA's rows
   uint64_t bar[2];
 };
 
@@ -205,8 +207,8 @@ __device__ __forceinline__ void pipe_init(uint64_t* bar, PipeState& ps) {
   __syncthreads();
 }
 
-template <int TILE, bool MASS>
-__device__ __forceinline__ void issue_lens_tile(const FieldDev& f, LensSmem<TILE>& sm, int tile, int buf) {
+template <int TILE, bool MASS, int ROWS>
+__device__ __forceinline__ void issue_lens_tile(const FieldDev& f, LensSmem<TILE, ROWS>& sm, int tile, int buf) {
   // called by one thread; full tiles are always in bounds thanks to the kLensPad padding
   const uint32_t b4 = TILE * sizeof(float4);
   const uint32_t b2 = MASS ? TILE * sizeof(float2) : 0u;
@@ -299,20 +301,27 @@ __device__ __forceinline__ void load_lens(uint32_t lbase, uint32_t mbase, int l,
 }
 
 // One lens pair (lenses l, l + 1) against all ray pairs of the thread.
-// ROW: all rays of the thread share x2 (one grid row): d2 and d2^2 are formed once per lens.
+// ROW: all rays of the thread share x2 (one grid row); d2 and d2^2 of the row come from the
+// shared-memory row table built once per lens tile (rt = that row's table).  Otherwise each ray
+// pair forms them itself.  Either way every ray gets exactly the same operations.
 template <int NP, bool MONT, bool MASS, bool ROW>
-__device__ __forceinline__ void lens_pair_all(uint32_t lbase, uint32_t mbase, int l, const uint64_t (&X1)[NP],
-                                              const uint64_t (&X2)[NP], uint64_t X2D, uint64_t (&P1)[NP],
+__device__ __forceinline__ void lens_pair_all(uint32_t lbase, uint32_t mbase, uint32_t rt, int l,
+                                              const uint64_t (&X1)[NP], const uint64_t (&X2)[NP], uint64_t (&P1)[NP],
                                               uint64_t (&P2)[NP]) {
   uint64_t Lxa, Lya, Ma, Lxb, Lyb, Mb;
-  load_lens<MASS>(lbase, mbase, l, Lxa, Lya, Ma);
-  load_lens<MASS>(lbase, mbase, l + 1, Lxb, Lyb, Mb);
   if (ROW) {
-    const uint64_t D2a = f2_sub(X2D, Lya), D2b = f2_sub(X2D, Lyb);
-    const uint64_t S2a = f2_mul(D2a, D2a), S2b = f2_mul(D2b, D2b);
+    Lxa = lds_pair(lbase + (uint32_t)l * 16u);
+    Lxb = lds_pair(lbase + (uint32_t)(l + 1) * 16u);
+    Ma = MASS ? lds_pair(mbase + (uint32_t)l * 8u) : 0ull;
+    Mb = MASS ? lds_pair(mbase + (uint32_t)(l + 1) * 8u) : 0ull;
+    uint64_t D2a, S2a, D2b, S2b;
+    lds_pair2(rt + (uint32_t)l * 16u, D2a, S2a);
+    lds_pair2(rt + (uint32_t)(l + 1) * 16u, D2b, S2b);
 #pragma unroll
     for (int q = 0; q < NP; ++q) lens_pair_step<MONT, MASS>(X1[q], Lxa, Lxb, D2a, S2a, D2b, S2b, Ma, Mb, P1[q], P2[q]);
   } else {
+    load_lens<MASS>(lbase, mbase, l, Lxa, Lya, Ma);
+    load_lens<MASS>(lbase, mbase, l + 1, Lxb, Lyb, Mb);
 #pragma unroll
     for (int q = 0; q < NP; ++q) {
       const uint64_t D2a = f2_sub(X2[q], Lya), D2b = f2_sub(X2[q], Lyb);
@@ -322,15 +331,35 @@ __device__ __forceinline__ void lens_pair_all(uint32_t lbase, uint32_t mbase, in
   }
 }
 
+// Row table for the current lens tile: entry (r, l) = {d2, d2, d2^2, d2^2} with d2 = x2(row r) - x2(lens l),
+// the same float32 operations a thread would otherwise repeat for every lens.
+template <int TILE, int ROWS>
+__device__ __forceinline__ void build_row_table(LensSmem<TILE, ROWS>& sm, int b) {
+  constexpr int BLOCK = ROWS * 32;
+#pragma unroll 4
+  for (int e = threadIdx.x; e < ROWS * TILE; e += BLOCK) {
+    const int r = e / TILE, l = e - (e / TILE) * TILE;
+    const uint64_t X2D = f2_pack(sm.x2row[r], sm.x2row[r]);
+    const float y = sm.lens4[b][l].z;
+    const uint64_t D2 = f2_sub(X2D, f2_pack(y, y));
+    const uint64_t S2 = f2_mul(D2, D2);
+    float d0, d1, s0, s1;
+    f2_unpack(D2, d0, d1);
+    f2_unpack(S2, s0, s1);
+    sm.rowtab[r][l] = make_float4(d0, d1, s0, s1);
+  }
+}
+
 // ----------------------------------------------------------------------------------------------
 // Deflection of RPT rays per thread by all lenses of the field (Eq. 2).
-// X1/X2: packed ray coordinates (pairs of rays); X2D = {x2, x2} when ROW (all rays share x2).
-// alpha1/alpha2 (double) out.  Returns false if a bounded wait gave up (the CTA must then stop;
-// the status word has been set).  The arithmetic per ray depends only on the ray and the field.
+// x1/x2: ray coordinates (ROW: all rays of a warp share x2, recorded in sm.x2row[warp] by the
+// caller).  alpha1/alpha2 (double) out.  Returns false if a bounded wait gave up (the CTA must
+// then stop; the status word has been set).  The arithmetic per ray depends only on the ray and
+// the field.
 // ----------------------------------------------------------------------------------------------
-template <int RPT, int TILE, bool MASS, bool ROW>
+template <int RPT, int TILE, bool MASS, bool ROW, int ROWS>
 __device__ __forceinline__ bool deflect(const FieldDev& f, const float (&x1)[RPT], const float (&x2)[RPT],
-                                        double (&a1)[RPT], double (&a2)[RPT], LensSmem<TILE>& sm,
+                                        double (&a1)[RPT], double (&a2)[RPT], LensSmem<TILE, ROWS>& sm,
                                         PipeState& ps) {
   static_assert(RPT % 2 == 0, "rays per thread must be even (packed pairs)");
   static_assert(TILE % kGroup == 0 && kGroup % 8 == 0, "lens tile must hold whole lens groups");
@@ -342,9 +371,9 @@ __device__ __forceinline__ bool deflect(const FieldDev& f, const float (&x1)[RPT
     X2[q] = f2_pack(x2[2 * q], x2[2 * q + 1]);
     H1[q] = L1[q] = H2[q] = L2[q] = 0ull;
   }
-  const uint64_t X2D = f2_pack(x2[0], x2[0]);
   const int n = f.n_lens;
   const int ntiles = (n + TILE - 1) / TILE;
+  const uint32_t rt = smem_u32(&sm.rowtab[ROW ? (threadIdx.x >> 5) : 0][0]);
   bool ok = true;
   if (threadIdx.x == 0) {
     if (ntiles > 0) issue_lens_tile<TILE, MASS>(f, sm, 0, 0);
@@ -359,6 +388,10 @@ __device__ __forceinline__ bool deflect(const FieldDev& f, const float (&x1)[RPT
       ok = false;
       break;
     }
+    if (ROW) {
+      build_row_table<TILE, ROWS>(sm, b);
+      __syncthreads();
+    }
     const uint32_t lbase = smem_u32(&sm.lens4[b][0]);
     const uint32_t mbase = smem_u32(&sm.mass2[b][0]);
     const int cnt = min(TILE, n - t * TILE);
@@ -367,13 +400,13 @@ __device__ __forceinline__ bool deflect(const FieldDev& f, const float (&x1)[RPT
       uint64_t P1[NP], P2[NP];
 #pragma unroll
       for (int q = 0; q < NP; ++q) P1[q] = P2[q] = 0ull;
-#pragma unroll 1
+#pragma unroll
       for (int p4 = 0; p4 < kGroup / 8; ++p4) {  // blocks of four lens pairs: fixed reciprocal pattern
         const int l = g + p4 * 8;
-        lens_pair_all<NP, mont_pair<MASS>(0), MASS, ROW>(lbase, mbase, l + 0, X1, X2, X2D, P1, P2);
-        lens_pair_all<NP, mont_pair<MASS>(1), MASS, ROW>(lbase, mbase, l + 2, X1, X2, X2D, P1, P2);
-        lens_pair_all<NP, mont_pair<MASS>(2), MASS, ROW>(lbase, mbase, l + 4, X1, X2, X2D, P1, P2);
-        lens_pair_all<NP, mont_pair<MASS>(3), MASS, ROW>(lbase, mbase, l + 6, X1, X2, X2D, P1, P2);
+        lens_pair_all<NP, mont_pair<MASS>(0), MASS, ROW>(lbase, mbase, rt, l + 0, X1, X2, P1, P2);
+        lens_pair_all<NP, mont_pair<MASS>(1), MASS, ROW>(lbase, mbase, rt, l + 2, X1, X2, P1, P2);
+        lens_pair_all<NP, mont_pair<MASS>(2), MASS, ROW>(lbase, mbase, rt, l + 4, X1, X2, P1, P2);
+        lens_pair_all<NP, mont_pair<MASS>(3), MASS, ROW>(lbase, mbase, rt, l + 6, X1, X2, P1, P2);
       }
 #pragma unroll
       for (int q = 0; q < NP; ++q) {
@@ -388,17 +421,25 @@ __device__ __forceinline__ bool deflect(const FieldDev& f, const float (&x1)[RPT
       int p = 0;
       for (; g + 2 * p + 1 < cnt; ++p) {
         if (mont_pair<MASS>(p))
-          lens_pair_all<NP, true, MASS, ROW>(lbase, mbase, g + 2 * p, X1, X2, X2D, P1, P2);
+          lens_pair_all<NP, true, MASS, ROW>(lbase, mbase, rt, g + 2 * p, X1, X2, P1, P2);
         else
-          lens_pair_all<NP, false, MASS, ROW>(lbase, mbase, g + 2 * p, X1, X2, X2D, P1, P2);
+          lens_pair_all<NP, false, MASS, ROW>(lbase, mbase, rt, g + 2 * p, X1, X2, P1, P2);
       }
       if (g + 2 * p < cnt) {
+        const int l = g + 2 * p;
         uint64_t Lx, Ly, M;
-        load_lens<MASS>(lbase, mbase, g + 2 * p, Lx, Ly, M);
+        load_lens<MASS>(lbase, mbase, l, Lx, Ly, M);
+        if (ROW) {
+          uint64_t D2, S2;
+          lds_pair2(rt + (uint32_t)l * 16u, D2, S2);
 #pragma unroll
-        for (int q = 0; q < NP; ++q) {
-          const uint64_t D2 = f2_sub(ROW ? X2D : X2[q], Ly);
-          lens_single_step<MASS>(X1[q], Lx, D2, f2_mul(D2, D2), M, P1[q], P2[q]);
+          for (int q = 0; q < NP; ++q) lens_single_step<MASS>(X1[q], Lx, D2, S2, M, P1[q], P2[q]);
+        } else {
+#pragma unroll
+          for (int q = 0; q < NP; ++q) {
+            const uint64_t D2 = f2_sub(X2[q], Ly);
+            lens_single_step<MASS>(X1[q], Lx, D2, f2_mul(D2, D2), M, P1[q], P2[q]);
+          }
         }
       }
 #pragma unroll
@@ -407,7 +448,7 @@ __device__ __forceinline__ bool deflect(const FieldDev& f, const float (&x1)[RPT
         twosum_accumulate(H2[q], L2[q], P2[q]);
       }
     }
-    __syncthreads();  // every thread is done with buffer b
+    __syncthreads();  // every thread is done with buffer b and the row table
     if (threadIdx.x == 0 && t + 2 < ntiles) issue_lens_tile<TILE, MASS>(f, sm, t + 2, b);
   }
   if (!ok) {
@@ -444,7 +485,8 @@ __host__ __device__ __forceinline__ int64_t shoot_tiles(int64_t n_rows, int64_t 
 }
 
 template <int WARPS, int RPT, int TILE, bool MASS>
-__device__ __forceinline__ bool shoot_tile(const ShootDesc& d, int64_t tile, LensSmem<TILE>& sm, PipeState& ps) {
+__device__ __forceinline__ bool shoot_tile(const ShootDesc& d, int64_t tile, LensSmem<TILE, WARPS>& sm,
+                                           PipeState& ps) {
   constexpr int SEG = 32 * RPT;
   const int64_t ncol = (d.n0 + SEG - 1) / SEG;
   const int64_t trow = tile / ncol;
@@ -464,8 +506,9 @@ __device__ __forceinline__ bool shoot_tile(const ShootDesc& d, int64_t tile, Len
     x1[k] = ray_coord(i, d.sp0, d.or0);
     x2[k] = x2r;
   }
+  if (lane == 0) sm.x2row[warp] = x2r;  // read by build_row_table after the first tile barrier
   double a1[RPT], a2[RPT];
-  if (!deflect<RPT, TILE, MASS, true>(d.f, x1, x2, a1, a2, sm, ps)) return false;
+  if (!deflect<RPT, TILE, MASS, true, WARPS>(d.f, x1, x2, a1, a2, sm, ps)) return false;
   unsigned oow_lane = 0;
 #pragma unroll
   for (int k = 0; k < RPT; ++k) {

@@ -10,7 +10,7 @@
 namespace rsint {
 
 // Lenses per shared-memory stage (a multiple of rsdev::kGroup, a divisor of rsdev::kLensPad).
-constexpr int kTile = 512;
+constexpr int kTile = 256;
 
 // Launch shapes compiled into the library; the per-ray arithmetic is identical for all.
 // A CTA of block / 32 warps covers block / 32 grid rows by 32 * rpt columns.
@@ -19,8 +19,8 @@ struct KernelCfg {
   int rpt;    // rays per thread (even: packed pairs)
 };
 constexpr int kNumCfg = 6;
-constexpr KernelCfg kCfgs[kNumCfg] = {{128, 4}, {128, 8}, {256, 4}, {256, 8}, {512, 4}, {256, 12}};
-constexpr int kDefaultCfg = 3;
+constexpr KernelCfg kCfgs[kNumCfg] = {{64, 8}, {128, 4}, {128, 8}, {256, 4}, {256, 8}, {256, 6}};
+constexpr int kDefaultCfg = 4;
 
 inline int find_cfg(int block, int rpt) {
   for (int i = 0; i < kNumCfg; ++i)

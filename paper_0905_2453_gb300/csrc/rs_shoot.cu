@@ -7,7 +7,7 @@ using namespace rsdev;
 
 template <int WARPS, int RPT, int TILE, bool MASS>
 __global__ void __launch_bounds__(WARPS * 32) shoot_kernel(const ShootDesc d) {
-  __shared__ LensSmem<TILE> sm;
+  __shared__ LensSmem<TILE, WARPS> sm;
   PipeState ps;
   pipe_init(sm.bar, ps);
   (void)shoot_tile<WARPS, RPT, TILE, MASS>(d, (int64_t)blockIdx.x, sm, ps);
@@ -32,7 +32,7 @@ __global__ void __launch_bounds__(BLOCK)
     x2[q] = ray_coord(ij[2 * r + 1], sp1, or1);
   }
   double a1[RPT], a2[RPT];
-  if (!deflect<RPT, TILE, MASS, false>(f, x1, x2, a1, a2, sm, ps)) return;
+  if (!deflect<RPT, TILE, MASS, false, 1>(f, x1, x2, a1, a2, sm, ps)) return;
 #pragma unroll
   for (int q = 0; q < RPT; ++q) {
     if (!valid[q]) continue;
@@ -64,12 +64,12 @@ namespace rsint {
 
 cudaError_t launch_shoot(int cfg, const rsdev::ShootDesc& d, cudaStream_t s) {
   switch (cfg) {
-    case 0: return launch_shoot_t<4, 4>(d, s);
-    case 1: return launch_shoot_t<4, 8>(d, s);
-    case 2: return launch_shoot_t<8, 4>(d, s);
-    case 3: return launch_shoot_t<8, 8>(d, s);
-    case 4: return launch_shoot_t<16, 4>(d, s);
-    case 5: return launch_shoot_t<8, 12>(d, s);
+    case 0: return launch_shoot_t<2, 8>(d, s);
+    case 1: return launch_shoot_t<4, 4>(d, s);
+    case 2: return launch_shoot_t<4, 8>(d, s);
+    case 3: return launch_shoot_t<8, 4>(d, s);
+    case 4: return launch_shoot_t<8, 8>(d, s);
+    case 5: return launch_shoot_t<8, 6>(d, s);
     default: return cudaErrorInvalidValue;
   }
 }
