@@ -265,6 +265,8 @@ def run_ours(args):
     spec = workload(args.workload, seed=rank)
     stream = torch.cuda.current_stream(device)
     field = rs.Field.from_spec(spec, stream)
+    from paper_0905_2453_gb300 import tune
+    shape = tune.autotune(field, spec.grid, spec.window, stream=stream)
     npix = (int(spec.window.npix[1]), int(spec.window.npix[0]))
     counts = torch.zeros(npix, dtype=torch.int32, device=device)
     oow = torch.zeros(1, dtype=torch.int64, device=device)
@@ -364,22 +366,26 @@ def run_ours(args):
     peak = fp32_peak_tflops(sms, max_mhz)
     achieved = inter_step * FLOPS_PER_INTERACTION / shoot_avg_s / 1e12
     med = clk.get("sm_mhz")
+    cfg = workload_config(spec, args.workload)
+    cfg["launch_shape"] = f"{shape[0]} threads x {shape[1]} rays/thread (autotuned)"
+    cfg["certified_binning"] = rs.rs_get_certified_binning()
     line = {
         "metric": METRIC, "value": value, "unit": "interactions/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_s / args.steps * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": workload_config(spec, args.workload),
+        "config": cfg,
         "pct_fp32_peak": 100.0 * achieved / peak,
         "pct_fp32_peak_at_measured_clock": (100.0 * achieved / fp32_peak_tflops(sms, med)) if med else None,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": profiled_traffic(args.workload),
-                     "kernel": "shoot_kernel", "kernel_ms": shoot_avg_s * 1e3,
+                     "kernel": "shoot_kernel (span of rs_shoot: list reset, shoot, certified re-evaluation)",
+                     "kernel_ms": shoot_avg_s * 1e3,
                      "peak_basis": f"FP32 FMA: {sms} SMs x 128 lanes x 2 flops x {max_mhz:.0f} MHz (max clock); "
                                    f"10 flops per interaction (paper App. A)"},
         "clocks": {"sm_mhz": med, "sm_max_mhz": clk.get("sm_max_mhz"), "reasons": clk.get("reasons"),
                    "samples": clk.get("samples")},
         "e2e": e2e,
-        "gpu_launches": 2 * args.steps,
+        "gpu_launches": (3 if rs.rs_get_certified_binning() else 2) * args.steps,
         "cpu_baseline": cpu,
         "batched": batched,
         "wall_s_timed_region": wall,
@@ -390,8 +396,11 @@ def run_ours(args):
 
 
 def run_batched(rs, torch, device, stream, reps=3):
+    from paper_0905_2453_gb300 import tune
     specs = ri.batch_fields(64)
     fields = [rs.Field.from_spec(s, stream) for s in specs]
+    big = max(range(len(specs)), key=lambda k: specs[k].interactions)
+    tune.autotune(fields[big], specs[big].grid, specs[big].window, stream=stream)
     grids = [s.grid for s in specs]
     wins = [s.window for s in specs]
     b = rs.Batch(fields, grids, wins)

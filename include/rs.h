@@ -127,14 +127,39 @@ int rs_shoot_rows(rs_field_t f, const rs_ray_grid* g, int64_t row_begin, int64_t
                   const rs_window* w, uint32_t* d_counts, uint64_t* d_out_of_window, void* stream);
 
 /*
- * rs_trace -- source positions of listed rays, for checks against a reference.
+ * rs_trace -- source positions of listed rays through the float32 path, for checks.
  *   d_ray_ij : int64[2*k] device, (i, j) per ray (each within the grid).
  *   d_y      : double[2*k] device, receives (y1, y2) per ray (Eq. 6).
  *   d_alpha  : double[2*k] device or NULL, receives (alpha1, alpha2) per ray (Eq. 2).
+ *   d_err    : double[2*k] device or NULL, receives per axis the half-width of the band
+ *              around y inside which the float32 result cannot decide a pixel (see
+ *              certified binning below).
  * The per-ray arithmetic is the one rs_shoot uses, bit for bit.
  */
 int rs_trace(rs_field_t f, const rs_ray_grid* g, const int64_t* d_ray_ij, int64_t k, double* d_y,
-             double* d_alpha, void* stream);
+             double* d_alpha, double* d_err, void* stream);
+
+/*
+ * rs_trace_certified -- source positions of listed rays with the deflection (Eq. 2) summed in
+ * float-float arithmetic (~2^-44 relative per term): the evaluation certified binning uses.
+ * Arguments as rs_trace (no d_err).
+ */
+int rs_trace_certified(rs_field_t f, const rs_ray_grid* g, const int64_t* d_ray_ij, int64_t k,
+                       double* d_y, double* d_alpha, void* stream);
+
+/*
+ * Certified binning (on by default).  The float32 shoot attaches to every ray an error
+ * estimate sigma = 6 u sqrt(32 sum_g (P1_g^2 + P2_g^2)) (u = 2^-24, P_g the float32 partial
+ * sums of its 32-lens groups).  A ray whose source position lies within that band of a pixel
+ * or window edge is not binned by the float32 result but re-evaluated with
+ * rs_trace_certified's arithmetic and binned from that; the maps then agree with a float64
+ * evaluation except for rays within ~1e-12 of an edge.  rs_shoot allocates the list of such
+ * rays stream-ordered (cudaMallocAsync, capacity max(4096, rays/32), at most 2^24 entries);
+ * rays beyond the capacity keep their float32 decision.  Batches own their list.
+ * rs_set_certified_binning(0) turns it off for calls (and batches planned) afterwards.
+ */
+int rs_set_certified_binning(int enabled);
+int rs_get_certified_binning(int* enabled);
 
 /*
  * rs_magnification -- Eq. 4: d_mu[p] = d_counts[p] / N_av (float, device), with
@@ -190,6 +215,14 @@ int rs_field_status(rs_field_t f, int clear, int* status);
 int rs_set_launch_config(int has_masses, int block, int rays_per_thread);
 int rs_get_launch_config(int has_masses, int* block, int* rays_per_thread);
 int rs_launch_configs(int* pairs, int cap, int* count);
+
+/*
+ * rs_selftest_bounded_wait -- run one CTA that waits on an mbarrier phase nothing completes,
+ * bounded by limit_ns (0 .. 2e9) of the device's global timer, the same bounded wait the
+ * kernels use for lens-tile copies.  *status = RS_ETIMEOUT when the wait gave up (the expected
+ * outcome), RS_OK otherwise.  Synchronous.  No paper counterpart: failure-detection support.
+ */
+int rs_selftest_bounded_wait(int64_t limit_ns, int* status);
 
 /* Thread-local message for the last nonzero status returned on this thread. */
 const char* rs_last_error(void);

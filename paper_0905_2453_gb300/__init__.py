@@ -28,7 +28,8 @@ __all__ = [
     "rs_create_field", "rs_destroy_field", "rs_field_info", "rs_shoot", "rs_shoot_rows", "rs_trace",
     "rs_magnification", "rs_batch_create", "rs_batch_launch", "rs_batch_destroy", "rs_shoot_batch",
     "rs_field_status", "rs_last_error", "rs_version", "rs_set_launch_config", "rs_get_launch_config",
-    "rs_launch_configs", "EXPORTED_SYMBOLS",
+    "rs_launch_configs", "rs_trace_certified", "rs_set_certified_binning", "rs_get_certified_binning",
+    "rs_selftest_bounded_wait", "EXPORTED_SYMBOLS",
 ]
 
 RS_OK, RS_EINVAL, RS_ENOMEM, RS_ECUDA, RS_EOVERFLOW, RS_ETIMEOUT = 0, 1, 2, 3, 4, 5
@@ -38,7 +39,8 @@ EXPORTED_SYMBOLS = (
     "rs_create_field", "rs_destroy_field", "rs_field_info", "rs_shoot", "rs_shoot_rows", "rs_trace",
     "rs_magnification", "rs_batch_create", "rs_batch_launch", "rs_batch_destroy", "rs_shoot_batch",
     "rs_field_status", "rs_last_error", "rs_version", "rs_set_launch_config", "rs_get_launch_config",
-    "rs_launch_configs",
+    "rs_launch_configs", "rs_trace_certified", "rs_set_certified_binning", "rs_get_certified_binning",
+    "rs_selftest_bounded_wait",
 )
 
 
@@ -100,7 +102,11 @@ def load():
         "rs_field_info": ([vp, ctypes.POINTER(i64), ctypes.POINTER(i32)], i32),
         "rs_shoot": ([vp, gp, wp, vp, vp, vp], i32),
         "rs_shoot_rows": ([vp, gp, i64, i64, wp, vp, vp, vp], i32),
-        "rs_trace": ([vp, gp, vp, i64, vp, vp, vp], i32),
+        "rs_trace": ([vp, gp, vp, i64, vp, vp, vp, vp], i32),
+        "rs_trace_certified": ([vp, gp, vp, i64, vp, vp, vp], i32),
+        "rs_set_certified_binning": ([i32], i32),
+        "rs_get_certified_binning": ([ctypes.POINTER(i32)], i32),
+        "rs_selftest_bounded_wait": ([i64, ctypes.POINTER(i32)], i32),
         "rs_magnification": ([vp, gp, wp, vp, vp], i32),
         "rs_batch_create": ([i32, vp, vp, vp, vp, vp, ctypes.POINTER(vp)], i32),
         "rs_batch_launch": ([vp, vp], i32),
@@ -245,14 +251,46 @@ def rs_shoot_rows(handle: int, grid, row_begin: int, row_end: int, window, count
                                 _stream(stream)), "rs_shoot_rows")
 
 
-def rs_trace(handle: int, grid, ray_ij: torch.Tensor, y: torch.Tensor, alpha: torch.Tensor = None, stream=None):
-    """Source positions (float64 [k, 2]) of listed rays (int64 [k, 2]) into ``y`` (and ``alpha``)."""
+def rs_trace(handle: int, grid, ray_ij: torch.Tensor, y: torch.Tensor, alpha: torch.Tensor = None,
+             err: torch.Tensor = None, stream=None):
+    """Source positions (float64 [k, 2]) of listed rays (int64 [k, 2]) into ``y`` (and ``alpha``,
+    and ``err``: the per-axis band half-width of the float32 result)."""
     k = ray_ij.numel() // 2
     pij = _dptr(ray_ij, torch.int64, "ray_ij")
     py = _dptr(y, torch.float64, "y", 2 * k)
-    pa = _dptr(alpha, torch.float64, "alpha", 2 * k) if alpha is not None else None
+    pa = _dptr(alpha, torch.float64, "alpha", 2 * k)
+    pe = _dptr(err, torch.float64, "err", 2 * k)
     g = _cgrid(grid)
-    _check(load().rs_trace(handle, ctypes.byref(g), pij, k, py, pa, _stream(stream)), "rs_trace")
+    _check(load().rs_trace(handle, ctypes.byref(g), pij, k, py, pa, pe, _stream(stream)), "rs_trace")
+
+
+def rs_trace_certified(handle: int, grid, ray_ij: torch.Tensor, y: torch.Tensor, alpha: torch.Tensor = None,
+                       stream=None):
+    """Source positions of listed rays with the float-float deflection sum (certified binning's evaluation)."""
+    k = ray_ij.numel() // 2
+    pij = _dptr(ray_ij, torch.int64, "ray_ij")
+    py = _dptr(y, torch.float64, "y", 2 * k)
+    pa = _dptr(alpha, torch.float64, "alpha", 2 * k)
+    g = _cgrid(grid)
+    _check(load().rs_trace_certified(handle, ctypes.byref(g), pij, k, py, pa, _stream(stream)),
+           "rs_trace_certified")
+
+
+def rs_selftest_bounded_wait(limit_ns: int) -> int:
+    """Run the bounded-wait self-test kernel; returns RS_ETIMEOUT when the wait gave up as designed."""
+    st = ctypes.c_int()
+    _check(load().rs_selftest_bounded_wait(int(limit_ns), ctypes.byref(st)), "rs_selftest_bounded_wait")
+    return int(st.value)
+
+
+def rs_set_certified_binning(enabled: bool) -> None:
+    _check(load().rs_set_certified_binning(1 if enabled else 0), "rs_set_certified_binning")
+
+
+def rs_get_certified_binning() -> bool:
+    v = ctypes.c_int()
+    _check(load().rs_get_certified_binning(ctypes.byref(v)), "rs_get_certified_binning")
+    return bool(v.value)
 
 
 def rs_magnification(counts: torch.Tensor, grid, window, mu: torch.Tensor, stream=None):
@@ -349,13 +387,19 @@ class Field:
             rs_shoot_rows(self.handle, grid, rows[0], rows[1], window, counts, out_of_window, stream)
         return counts
 
-    def trace(self, grid, ray_ij, with_alpha=False, stream=None):
+    def trace(self, grid, ray_ij, with_alpha=False, with_err=False, certified=False, stream=None):
+        """Source positions of listed rays: float32 path (default) or float-float (certified=True)."""
         dev = torch.device("cuda", torch.cuda.current_device())
         ij = torch.as_tensor(ray_ij, dtype=torch.int64).reshape(-1, 2).to(dev).contiguous()
         y = torch.empty((ij.shape[0], 2), dtype=torch.float64, device=dev)
         a = torch.empty_like(y) if with_alpha else None
-        rs_trace(self.handle, grid, ij, y, a, stream)
-        return (y, a) if with_alpha else y
+        e = torch.empty_like(y) if (with_err and not certified) else None
+        if certified:
+            rs_trace_certified(self.handle, grid, ij, y, a, stream)
+        else:
+            rs_trace(self.handle, grid, ij, y, a, e, stream)
+        out = (y,) + ((a,) if with_alpha else ()) + ((e,) if (with_err and not certified) else ())
+        return out if len(out) > 1 else y
 
     def status(self, clear=False) -> int:
         return rs_field_status(self.handle, clear)

@@ -29,12 +29,18 @@ struct rs_field {
 struct rs_batch {
   int device;
   int n_fields;
-  int n_items;
-  int cfg;
-  int grid;
+  // work items of fields without (group 0) and with (group 1) per-lens masses: one persistent
+  // kernel per group, each with its own launch shape
+  int n_items[2];
+  int item_offset[2];
+  int cfg[2];
+  int grid[2];
   ShootDesc* d_descs;
   int2* d_items;
   int* d_counter;
+  uint2* d_rc_list;
+  unsigned int* d_rc_count;
+  unsigned int rc_cap;
   cudaGraph_t graph;
   cudaGraphExec_t exec;
 };
@@ -44,6 +50,14 @@ namespace {
 thread_local std::string g_err;
 // Launch shape per mass mode (index 0: unit masses, 1: per-lens masses).
 int g_cfg[2] = {rsint::kDefaultCfg, rsint::kDefaultCfg};
+// Certified binning (float-float re-evaluation of rays inside their error band of a pixel edge).
+int g_certify = 1;
+
+int recheck_grid(int device) {
+  int v = 0;
+  if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, device) != cudaSuccess || v < 1) v = 1;
+  return v * 8;
+}
 
 int fail(int code, const char* fmt, ...) {
   char buf[512];
@@ -146,6 +160,20 @@ __global__ void magnification_kernel(const uint32_t* __restrict__ c, float* __re
     done = nv * 4;
   }
   for (int64_t i = done + t0; i < n; i += stride) mu[i] = (float)c[i] * inv_nav;
+}
+
+// Waits on an mbarrier phase that nothing completes, with the given limit: exercises the bounded
+// wait and its error status without hanging or faulting the device.
+__global__ void selftest_wait_kernel(uint64_t limit_ns, unsigned int* out) {
+  __shared__ uint64_t bar;
+  if (threadIdx.x == 0) {
+    rsdev::mbar_init(&bar, 1);
+    rsdev::mbar_fence_init();
+  }
+  __syncthreads();
+  const bool ok = rsdev::mbar_wait_bounded(&bar, 0u, limit_ns);
+  __syncthreads();
+  if (threadIdx.x == 0) *out = ok ? 0u : rsdev::kStatusTimeout;
 }
 
 int num_sms(int device) {
@@ -365,8 +393,25 @@ int rs_shoot_rows(rs_field_t f, const rs_ray_grid* g, int64_t row_begin, int64_t
   ShootDesc d;
   if ((rc = fill_desc(f, g, row_begin, row_end, w, d_counts, d_out_of_window, &d)) != RS_OK) return rc;
   if (d.n_rows == 0 || d.n0 == 0) return RS_OK;
-  cudaError_t e = rsint::launch_shoot(g_cfg[f->dev.has_mass ? 1 : 0], d, reinterpret_cast<cudaStream_t>(stream));
-  if (e != cudaSuccess) return cuda_fail(e, "shoot kernel launch");
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  void* ws = nullptr;
+  cudaError_t e = cudaSuccess;
+  if (g_certify) {
+    // stream-ordered workspace: [count | pad | list of {field, ray}]
+    d.rc_cap = rsint::recheck_capacity(d.n_rows * d.n0);
+    if ((e = cudaMallocAsync(&ws, 16 + sizeof(uint2) * (size_t)d.rc_cap, s)) != cudaSuccess)
+      return cuda_fail(e, "cudaMallocAsync (re-evaluation list)");
+    d.rc_count = reinterpret_cast<unsigned int*>(ws);
+    d.rc_list = reinterpret_cast<uint2*>(reinterpret_cast<char*>(ws) + 16);
+    e = cudaMemsetAsync(d.rc_count, 0, sizeof(unsigned int), s);
+  }
+  if (e == cudaSuccess) e = rsint::launch_shoot(g_cfg[f->dev.has_mass ? 1 : 0], d, s);
+  if (e == cudaSuccess && ws) e = rsint::launch_recheck(&d, nullptr, d.rc_list, d.rc_count, d.rc_cap, recheck_grid(f->device), s);
+  if (ws) {
+    cudaError_t e2 = cudaFreeAsync(ws, s);
+    if (e == cudaSuccess) e = e2;
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "shoot launch");
   return RS_OK;
 }
 
@@ -377,7 +422,7 @@ int rs_shoot(rs_field_t f, const rs_ray_grid* g, const rs_window* w, uint32_t* d
 }
 
 int rs_trace(rs_field_t f, const rs_ray_grid* g, const int64_t* d_ray_ij, int64_t k, double* d_y, double* d_alpha,
-             void* stream) {
+             double* d_err, void* stream) {
   if (!f) return fail(RS_EINVAL, "field is NULL");
   int rc;
   if ((rc = check_grid(g)) != RS_OK) return rc;
@@ -387,8 +432,51 @@ int rs_trace(rs_field_t f, const rs_ray_grid* g, const int64_t* d_ray_ij, int64_
   if (k >= ((int64_t)1 << 31)) return fail(RS_EOVERFLOW, "k must be < 2^31");
   if ((rc = check_field_device(f)) != RS_OK) return rc;
   cudaError_t e = rsint::launch_trace(f->dev, g->origin[0], g->origin[1], g->spacing[0], g->spacing[1], d_ray_ij, k,
-                                      d_y, d_alpha, reinterpret_cast<cudaStream_t>(stream));
+                                      d_y, d_alpha, d_err, reinterpret_cast<cudaStream_t>(stream));
   if (e != cudaSuccess) return cuda_fail(e, "trace kernel launch");
+  return RS_OK;
+}
+
+int rs_trace_certified(rs_field_t f, const rs_ray_grid* g, const int64_t* d_ray_ij, int64_t k, double* d_y,
+                       double* d_alpha, void* stream) {
+  if (!f) return fail(RS_EINVAL, "field is NULL");
+  int rc;
+  if ((rc = check_grid(g)) != RS_OK) return rc;
+  if (k < 0) return fail(RS_EINVAL, "k < 0");
+  if (k == 0) return RS_OK;
+  if (!d_ray_ij || !d_y) return fail(RS_EINVAL, "d_ray_ij / d_y is NULL");
+  if (k >= ((int64_t)1 << 31)) return fail(RS_EOVERFLOW, "k must be < 2^31");
+  if ((rc = check_field_device(f)) != RS_OK) return rc;
+  cudaError_t e = rsint::launch_trace_ff(f->dev, g->origin[0], g->origin[1], g->spacing[0], g->spacing[1], d_ray_ij,
+                                         k, d_y, d_alpha, reinterpret_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(e, "certified trace kernel launch");
+  return RS_OK;
+}
+
+int rs_selftest_bounded_wait(int64_t limit_ns, int* status) {
+  if (!status) return fail(RS_EINVAL, "status is NULL");
+  if (limit_ns < 0 || limit_ns > 2000000000LL) return fail(RS_EINVAL, "limit_ns must be in [0, 2e9]");
+  unsigned int* d = nullptr;
+  cudaError_t e = cudaMalloc(&d, sizeof(unsigned int));
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc (self-test)");
+  selftest_wait_kernel<<<1, 32>>>((uint64_t)limit_ns, d);
+  e = cudaGetLastError();
+  unsigned int v = 0;
+  if (e == cudaSuccess) e = cudaMemcpy(&v, d, sizeof(v), cudaMemcpyDeviceToHost);
+  cudaFree(d);
+  if (e != cudaSuccess) return cuda_fail(e, "self-test kernel");
+  *status = v == 0 ? RS_OK : (int)v;
+  return RS_OK;
+}
+
+int rs_set_certified_binning(int enabled) {
+  g_certify = enabled ? 1 : 0;
+  return RS_OK;
+}
+
+int rs_get_certified_binning(int* enabled) {
+  if (!enabled) return fail(RS_EINVAL, "enabled is NULL");
+  *enabled = g_certify;
   return RS_OK;
 }
 
@@ -426,16 +514,13 @@ int rs_batch_create(int n_fields, const rs_field_t* fields, const rs_ray_grid* g
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
   int rc;
-  const int cfg = g_cfg[1];
-  const int warps = rsint::kCfgs[cfg].block / 32;
-  const int64_t seg = 32 * (int64_t)rsint::kCfgs[cfg].rpt;
   std::vector<ShootDesc> descs(n_fields);
   struct Item {
     double cost;
     int field;
     int tile;
   };
-  std::vector<Item> items;
+  std::vector<Item> items[2];
   for (int k = 0; k < n_fields; ++k) {
     if (!fields[k]) return fail(RS_EINVAL, "fields[%d] is NULL", k);
     if (fields[k]->device != dev) return fail(RS_EINVAL, "fields[%d] lives on another device", k);
@@ -445,47 +530,69 @@ int rs_batch_create(int n_fields, const rs_field_t* fields, const rs_ray_grid* g
     if ((rc = fill_desc(fields[k], &grids[k], 0, grids[k].n[1], &windows[k], d_counts[k],
                         d_out_of_window ? d_out_of_window + k : nullptr, &descs[k])) != RS_OK)
       return rc;
+    const int grp = fields[k]->dev.has_mass ? 1 : 0;
+    const int warps = rsint::kCfgs[g_cfg[grp]].block / 32;
+    const int64_t seg = 32 * (int64_t)rsint::kCfgs[g_cfg[grp]].rpt;
     const int64_t n0 = descs[k].n0, nr = descs[k].n_rows;
     if (n0 == 0 || nr == 0) continue;
     const int64_t ncol = (n0 + seg - 1) / seg;
     const int64_t nt = ((nr + warps - 1) / warps) * ncol;
-    if ((int64_t)items.size() + nt >= ((int64_t)1 << 31)) return fail(RS_EOVERFLOW, "too many work items");
+    if ((int64_t)(items[0].size() + items[1].size()) + nt >= ((int64_t)1 << 31))
+      return fail(RS_EOVERFLOW, "too many work items");
     for (int64_t t = 0; t < nt; ++t) {
       const int64_t trow = t / ncol, tcol = t - trow * ncol;
       const int64_t rows = std::min<int64_t>(warps, nr - trow * warps);
       const int64_t cols = std::min<int64_t>(seg, n0 - tcol * seg);
       // per-ray cost: one interaction per lens plus a fixed epilogue (~ 64 interactions)
       const double cost = (double)(rows * cols) * ((double)fields[k]->n_lens + 64.0);
-      items.push_back({cost, k, (int)t});
+      items[grp].push_back({cost, k, (int)t});
     }
   }
-  std::stable_sort(items.begin(), items.end(), [](const Item& a, const Item& b) { return a.cost > b.cost; });
-  std::vector<int2> h_items(items.size());
-  for (size_t i = 0; i < items.size(); ++i) h_items[i] = make_int2(items[i].field, items[i].tile);
-
+  std::vector<int2> h_items;
   rs_batch* b = new (std::nothrow) rs_batch();
   if (!b) return fail(RS_ENOMEM, "host allocation failed");
   b->device = dev;
   b->n_fields = n_fields;
-  b->n_items = (int)h_items.size();
-  b->cfg = cfg;
-  int bps = 0;
-  if ((e = rsint::batch_blocks_per_sm(cfg, &bps)) != cudaSuccess || bps < 1) bps = 1;
-  b->grid = num_sms(dev) * bps;
+  for (int grp = 0; grp < 2; ++grp) {
+    std::stable_sort(items[grp].begin(), items[grp].end(),
+                     [](const Item& x, const Item& y) { return x.cost > y.cost; });
+    b->item_offset[grp] = (int)h_items.size();
+    b->n_items[grp] = (int)items[grp].size();
+    for (const Item& it : items[grp]) h_items.push_back(make_int2(it.field, it.tile));
+    b->cfg[grp] = g_cfg[grp];
+    int bps = 0;
+    if (rsint::batch_blocks_per_sm(b->cfg[grp], grp == 1, &bps) != cudaSuccess || bps < 1) bps = 1;
+    b->grid[grp] = num_sms(dev) * bps;
+  }
   auto cleanup = [&]() {
     if (b->exec) cudaGraphExecDestroy(b->exec);
     if (b->graph) cudaGraphDestroy(b->graph);
     cudaFree(b->d_descs);
     cudaFree(b->d_items);
     cudaFree(b->d_counter);
+    cudaFree(b->d_rc_list);
+    cudaFree(b->d_rc_count);
     delete b;
   };
+  if (g_certify) {
+    int64_t total = 0;
+    for (int k = 0; k < n_fields; ++k) total += descs[k].n_rows * descs[k].n0;
+    b->rc_cap = rsint::recheck_capacity(total);
+  }
   if ((e = cudaMalloc(&b->d_descs, sizeof(ShootDesc) * n_fields)) != cudaSuccess ||
       (e = cudaMalloc(&b->d_items, sizeof(int2) * std::max<size_t>(1, h_items.size()))) != cudaSuccess ||
-      (e = cudaMalloc(&b->d_counter, sizeof(int))) != cudaSuccess) {
+      (e = cudaMalloc(&b->d_counter, 2 * sizeof(int))) != cudaSuccess ||
+      (b->rc_cap > 0 && (e = cudaMalloc(&b->d_rc_list, sizeof(uint2) * (size_t)b->rc_cap)) != cudaSuccess) ||
+      (b->rc_cap > 0 && (e = cudaMalloc(&b->d_rc_count, sizeof(unsigned int))) != cudaSuccess)) {
     rc = cuda_fail(e, "cudaMalloc (batch)");
     cleanup();
     return rc;
+  }
+  for (int k = 0; k < n_fields; ++k) {
+    descs[k].field_id = k;
+    descs[k].rc_list = b->d_rc_list;
+    descs[k].rc_count = b->d_rc_count;
+    descs[k].rc_cap = b->rc_cap;
   }
   if ((e = cudaMemcpy(b->d_descs, descs.data(), sizeof(ShootDesc) * n_fields, cudaMemcpyHostToDevice)) != cudaSuccess ||
       (!h_items.empty() &&
@@ -506,9 +613,14 @@ int rs_batch_create(int n_fields, const rs_field_t* fields, const rs_ray_grid* g
     for (int k = 0; k < n_fields && e == cudaSuccess; ++k)
       e = cudaMemsetAsync(d_counts[k], 0, sizeof(uint32_t) * (size_t)windows[k].npix[0] * (size_t)windows[k].npix[1], cs);
     if (e == cudaSuccess && d_out_of_window) e = cudaMemsetAsync(d_out_of_window, 0, sizeof(uint64_t) * n_fields, cs);
-    if (e == cudaSuccess) e = cudaMemsetAsync(b->d_counter, 0, sizeof(int), cs);
-    if (e == cudaSuccess && b->n_items > 0)
-      e = rsint::launch_batch(cfg, b->d_descs, b->d_items, b->n_items, b->d_counter, b->grid, cs);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->d_counter, 0, 2 * sizeof(int), cs);
+    if (e == cudaSuccess && b->rc_cap > 0) e = cudaMemsetAsync(b->d_rc_count, 0, sizeof(unsigned int), cs);
+    for (int grp = 1; grp >= 0 && e == cudaSuccess; --grp)
+      if (b->n_items[grp] > 0)
+        e = rsint::launch_batch(b->cfg[grp], grp == 1, b->d_descs, b->d_items + b->item_offset[grp], b->n_items[grp],
+                                b->d_counter + grp, b->grid[grp], cs);
+    if (e == cudaSuccess && b->rc_cap > 0)
+      e = rsint::launch_recheck(nullptr, b->d_descs, b->d_rc_list, b->d_rc_count, b->rc_cap, recheck_grid(dev), cs);
     cudaError_t e2 = cudaStreamEndCapture(cs, &b->graph);
     if (e == cudaSuccess) e = e2;
   }
@@ -542,6 +654,8 @@ int rs_batch_destroy(rs_batch_t b) {
   cudaFree(b->d_descs);
   cudaFree(b->d_items);
   cudaFree(b->d_counter);
+  cudaFree(b->d_rc_list);
+  cudaFree(b->d_rc_count);
   delete b;
   return RS_OK;
 }

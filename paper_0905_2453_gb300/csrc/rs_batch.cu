@@ -10,7 +10,7 @@ namespace {
 
 using namespace rsdev;
 
-template <int WARPS, int RPT, int TILE>
+template <int WARPS, int RPT, int TILE, bool MASS>
 __global__ void __launch_bounds__(WARPS * 32)
     batch_kernel(const ShootDesc* __restrict__ descs, const int2* __restrict__ items, int n_items, int* counter) {
   __shared__ LensSmem<TILE, WARPS> sm;
@@ -25,50 +25,55 @@ __global__ void __launch_bounds__(WARPS * 32)
     if (it >= n_items) break;
     const int2 w = items[it];
     const ShootDesc& d = descs[w.x];
-    const bool ok = d.f.has_mass ? shoot_tile<WARPS, RPT, TILE, true>(d, (int64_t)w.y, sm, ps)
-                                 : shoot_tile<WARPS, RPT, TILE, false>(d, (int64_t)w.y, sm, ps);
+    const bool ok = shoot_tile<WARPS, RPT, TILE, MASS>(d, (int64_t)w.y, sm, ps);
     if (!ok) break;
   }
 }
 
 template <int WARPS, int RPT>
-cudaError_t launch_batch_t(const ShootDesc* descs, const int2* items, int n_items, int* counter, int grid,
+cudaError_t launch_batch_t(bool mass, const ShootDesc* descs, const int2* items, int n_items, int* counter, int grid,
                            cudaStream_t s) {
-  batch_kernel<WARPS, RPT, rsint::kTile><<<grid, WARPS * 32, 0, s>>>(descs, items, n_items, counter);
+  if (mass)
+    batch_kernel<WARPS, RPT, rsint::kTile, true><<<grid, WARPS * 32, 0, s>>>(descs, items, n_items, counter);
+  else
+    batch_kernel<WARPS, RPT, rsint::kTile, false><<<grid, WARPS * 32, 0, s>>>(descs, items, n_items, counter);
   return cudaGetLastError();
 }
 
 template <int WARPS, int RPT>
-cudaError_t occ_t(int* blocks) {
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, batch_kernel<WARPS, RPT, rsint::kTile>, WARPS * 32,
-                                                       0);
+cudaError_t occ_t(bool mass, int* blocks) {
+  if (mass)
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, batch_kernel<WARPS, RPT, rsint::kTile, true>,
+                                                         WARPS * 32, 0);
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, batch_kernel<WARPS, RPT, rsint::kTile, false>,
+                                                       WARPS * 32, 0);
 }
 
 }  // namespace
 
 namespace rsint {
 
-cudaError_t launch_batch(int cfg, const rsdev::ShootDesc* descs, const int2* items, int n_items, int* counter,
-                         int grid, cudaStream_t s) {
+cudaError_t launch_batch(int cfg, bool mass, const rsdev::ShootDesc* descs, const int2* items, int n_items,
+                         int* counter, int grid, cudaStream_t s) {
   switch (cfg) {
-    case 0: return launch_batch_t<2, 8>(descs, items, n_items, counter, grid, s);
-    case 1: return launch_batch_t<4, 4>(descs, items, n_items, counter, grid, s);
-    case 2: return launch_batch_t<4, 8>(descs, items, n_items, counter, grid, s);
-    case 3: return launch_batch_t<8, 4>(descs, items, n_items, counter, grid, s);
-    case 4: return launch_batch_t<8, 8>(descs, items, n_items, counter, grid, s);
-    case 5: return launch_batch_t<8, 6>(descs, items, n_items, counter, grid, s);
+    case 0: return launch_batch_t<2, 8>(mass, descs, items, n_items, counter, grid, s);
+    case 1: return launch_batch_t<4, 4>(mass, descs, items, n_items, counter, grid, s);
+    case 2: return launch_batch_t<4, 8>(mass, descs, items, n_items, counter, grid, s);
+    case 3: return launch_batch_t<8, 4>(mass, descs, items, n_items, counter, grid, s);
+    case 4: return launch_batch_t<8, 8>(mass, descs, items, n_items, counter, grid, s);
+    case 5: return launch_batch_t<8, 6>(mass, descs, items, n_items, counter, grid, s);
     default: return cudaErrorInvalidValue;
   }
 }
 
-cudaError_t batch_blocks_per_sm(int cfg, int* blocks) {
+cudaError_t batch_blocks_per_sm(int cfg, bool mass, int* blocks) {
   switch (cfg) {
-    case 0: return occ_t<2, 8>(blocks);
-    case 1: return occ_t<4, 4>(blocks);
-    case 2: return occ_t<4, 8>(blocks);
-    case 3: return occ_t<8, 4>(blocks);
-    case 4: return occ_t<8, 8>(blocks);
-    case 5: return occ_t<8, 6>(blocks);
+    case 0: return occ_t<2, 8>(mass, blocks);
+    case 1: return occ_t<4, 4>(mass, blocks);
+    case 2: return occ_t<4, 8>(mass, blocks);
+    case 3: return occ_t<8, 4>(mass, blocks);
+    case 4: return occ_t<8, 8>(mass, blocks);
+    case 5: return occ_t<8, 6>(mass, blocks);
     default: return cudaErrorInvalidValue;
   }
 }

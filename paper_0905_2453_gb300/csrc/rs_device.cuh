@@ -147,13 +147,13 @@ __device__ __forceinline__ uint64_t globaltimer_ns() {
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
   return t;
 }
-// Bounded wait for the phase with the given parity to complete.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+// Bounded wait for the phase with the given parity to complete (limit in ns of globaltimer).
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, uint64_t limit_ns = kWaitLimitNs) {
   if (mbar_try_wait(bar, parity)) return true;
   const uint64_t t0 = globaltimer_ns();
   for (uint32_t it = 1; it < (1u << 30); ++it) {
     if (mbar_try_wait(bar, parity)) return true;
-    if ((it & 255u) == 0u && globaltimer_ns() - t0 > kWaitLimitNs) return false;
+    if ((it & 255u) == 0u && globaltimer_ns() - t0 > limit_ns) return false;
   }
   return false;
 }
@@ -180,7 +180,19 @@ struct ShootDesc {
   int32_t np0, np1;           // pixels per axis
   uint32_t* counts;           // [np1][np0]
   unsigned long long* oow;    // out-of-window counter or nullptr
+  uint2* rc_list;             // certified binning: rays to re-evaluate {field_id, ray index}, or nullptr
+  unsigned int* rc_count;     // entries requested so far (may exceed rc_cap)
+  unsigned int rc_cap;        // capacity of rc_list
+  int32_t field_id;           // index of this field in its batch (0 for a single-field call)
 };
+
+// Certified binning: a ray whose float32 source position lies within kSigmaSafety * sigma of a
+// pixel edge (sigma: the per-ray error estimate below) is re-evaluated in float-float arithmetic
+// before it is counted.
+constexpr float kSigmaSafety = 6.0f;
+// sigma = u sqrt(32 sum_g (P1_g^2 + P2_g^2)): the rounding of a 32-lens float32 group partial is a
+// random walk of at most 32 steps of ~u |P_g|; u = 2^-24.
+constexpr float kSigmaScale = 5.9604645e-08f * 5.656854249f * kSigmaSafety;
 
 template <int TILE, int ROWS = 1>
 struct __align__(16) LensSmem {
@@ -359,17 +371,17 @@ __device__ __forceinline__ void build_row_table(LensSmem<TILE, ROWS>& sm, int b)
 // ----------------------------------------------------------------------------------------------
 template <int RPT, int TILE, bool MASS, bool ROW, int ROWS>
 __device__ __forceinline__ bool deflect(const FieldDev& f, const float (&x1)[RPT], const float (&x2)[RPT],
-                                        double (&a1)[RPT], double (&a2)[RPT], LensSmem<TILE, ROWS>& sm,
-                                        PipeState& ps) {
+                                        double (&a1)[RPT], double (&a2)[RPT], float (&sig)[RPT],
+                                        LensSmem<TILE, ROWS>& sm, PipeState& ps) {
   static_assert(RPT % 2 == 0, "rays per thread must be even (packed pairs)");
   static_assert(TILE % kGroup == 0 && kGroup % 8 == 0, "lens tile must hold whole lens groups");
   constexpr int NP = RPT / 2;
-  uint64_t X1[NP], X2[NP], H1[NP], L1[NP], H2[NP], L2[NP];
+  uint64_t X1[NP], X2[NP], H1[NP], L1[NP], H2[NP], L2[NP], SS[NP];
 #pragma unroll
   for (int q = 0; q < NP; ++q) {
     X1[q] = f2_pack(x1[2 * q], x1[2 * q + 1]);
     X2[q] = f2_pack(x2[2 * q], x2[2 * q + 1]);
-    H1[q] = L1[q] = H2[q] = L2[q] = 0ull;
+    H1[q] = L1[q] = H2[q] = L2[q] = SS[q] = 0ull;
   }
   const int n = f.n_lens;
   const int ntiles = (n + TILE - 1) / TILE;
@@ -412,6 +424,8 @@ __device__ __forceinline__ bool deflect(const FieldDev& f, const float (&x1)[RPT
       for (int q = 0; q < NP; ++q) {
         twosum_accumulate(H1[q], L1[q], P1[q]);
         twosum_accumulate(H2[q], L2[q], P2[q]);
+        SS[q] = f2_fma(P1[q], P1[q], SS[q]);
+        SS[q] = f2_fma(P2[q], P2[q], SS[q]);
       }
     }
     if (g < cnt) {  // last, partial group of the field: same pattern by pair index, odd lens direct
@@ -446,6 +460,8 @@ __device__ __forceinline__ bool deflect(const FieldDev& f, const float (&x1)[RPT
       for (int q = 0; q < NP; ++q) {
         twosum_accumulate(H1[q], L1[q], P1[q]);
         twosum_accumulate(H2[q], L2[q], P2[q]);
+        SS[q] = f2_fma(P1[q], P1[q], SS[q]);
+        SS[q] = f2_fma(P2[q], P2[q], SS[q]);
       }
     }
     __syncthreads();  // every thread is done with buffer b and the row table
@@ -470,8 +486,17 @@ __device__ __forceinline__ bool deflect(const FieldDev& f, const float (&x1)[RPT
     f2_unpack(L2[q], l, lB);
     a2[2 * q] = (double)h + (double)l;
     a2[2 * q + 1] = (double)hB + (double)lB;
+    f2_unpack(SS[q], h, hB);
+    sig[2 * q] = kSigmaScale * sqrtf(h);
+    sig[2 * q + 1] = kSigmaScale * sqrtf(hB);
   }
   return true;
+}
+
+// Half-width of the band around y within which the float32 path cannot decide the pixel:
+// the safety-scaled sigma plus the float64 epilogue and (hi, lo) representation error.
+__device__ __forceinline__ double band_halfwidth(float sig, double y, double a) {
+  return (double)sig + 4e-15 * (fabs(y) + fabs(a));
 }
 
 // ----------------------------------------------------------------------------------------------
@@ -508,7 +533,8 @@ __device__ __forceinline__ bool shoot_tile(const ShootDesc& d, int64_t tile, Len
   }
   if (lane == 0) sm.x2row[warp] = x2r;  // read by build_row_table after the first tile barrier
   double a1[RPT], a2[RPT];
-  if (!deflect<RPT, TILE, MASS, true, WARPS>(d.f, x1, x2, a1, a2, sm, ps)) return false;
+  float sig[RPT];
+  if (!deflect<RPT, TILE, MASS, true, WARPS>(d.f, x1, x2, a1, a2, sig, sm, ps)) return false;
   unsigned oow_lane = 0;
 #pragma unroll
   for (int k = 0; k < RPT; ++k) {
@@ -518,12 +544,39 @@ __device__ __forceinline__ bool shoot_tile(const ShootDesc& d, int64_t tile, Len
     const double u1 = __dmul_rn(__dsub_rn(y1, d.lo0), d.sc0);
     const double u2 = __dmul_rn(__dsub_rn(y2, d.lo1), d.sc1);
     const bool inwin = (u1 >= 0.0) && (u1 < (double)d.np0) && (u2 >= 0.0) && (u2 < (double)d.np1);
-    if (valid[k] && inwin) {
+    bool bin_now = valid[k];
+    if (d.rc_list != nullptr) {
+      // certain: the whole band [u - du, u + du] on both axes is out of the window, or inside one pixel
+      const double du1 = band_halfwidth(sig[k], y1, a1[k]) * d.sc0;
+      const double du2 = band_halfwidth(sig[k], y2, a2[k]) * d.sc1;
+      const bool out_sure = !((u1 >= -du1) && (u1 < d.np0 + du1) && (u2 >= -du2) && (u2 < d.np1 + du2));
+      const double f1 = u1 - floor(u1), f2 = u2 - floor(u2);
+      const bool in_sure = (u1 >= du1) && (u1 < d.np0 - du1) && (u2 >= du2) && (u2 < d.np1 - du2) &&
+                           (f1 >= du1) && (f1 <= 1.0 - du1) && (f2 >= du2) && (f2 <= 1.0 - du2);
+      const bool need = valid[k] && !out_sure && !in_sure;
+      const unsigned mask = __ballot_sync(0xffffffffu, need);
+      if (mask != 0u) {
+        const int leader = __ffs(mask) - 1;
+        unsigned base = 0;
+        if (lane == leader) base = atomicAdd(d.rc_count, (unsigned)__popc(mask));
+        base = __shfl_sync(0xffffffffu, base, leader);
+        if (need) {
+          const unsigned slot = base + (unsigned)__popc(mask & ((1u << lane) - 1u));
+          if (slot < d.rc_cap) {
+            const int64_t i = tcol * SEG + lane + 32 * k;
+            d.rc_list[slot] = make_uint2((unsigned)d.field_id, (unsigned)(jrel * d.n0 + i));
+            bin_now = false;  // counted by the float-float re-evaluation
+          }
+          // list full: the ray keeps its float32 decision
+        }
+      }
+    }
+    if (bin_now && inwin) {
       const int p1 = (int)floor(u1);
       const int p2 = (int)floor(u2);
       atomicAdd(d.counts + (size_t)p2 * (size_t)d.np0 + (size_t)p1, 1u);
     }
-    const unsigned miss = __ballot_sync(0xffffffffu, valid[k] && !inwin);
+    const unsigned miss = __ballot_sync(0xffffffffu, bin_now && !inwin);
     oow_lane += __popc(miss);
   }
   if (d.oow != nullptr && lane == 0 && oow_lane != 0) atomicAdd(d.oow, (unsigned long long)oow_lane);

@@ -20,7 +20,7 @@ struct KernelCfg {
 };
 constexpr int kNumCfg = 6;
 constexpr KernelCfg kCfgs[kNumCfg] = {{64, 8}, {128, 4}, {128, 8}, {256, 4}, {256, 8}, {256, 6}};
-constexpr int kDefaultCfg = 4;
+constexpr int kDefaultCfg = 3;
 
 inline int find_cfg(int block, int rpt) {
   for (int i = 0; i < kNumCfg; ++i)
@@ -31,13 +31,30 @@ inline int find_cfg(int block, int rpt) {
 // Plain launch: one CTA per ray tile of block * rpt rays.
 cudaError_t launch_shoot(int cfg, const rsdev::ShootDesc& d, cudaStream_t s);
 
-// Listed rays -> source positions (and deflections).
+// Listed rays -> source positions (and deflections, and band half-widths), float32 path.
 cudaError_t launch_trace(const rsdev::FieldDev& f, double or0, double or1, double sp0, double sp1,
-                         const int64_t* ij, int64_t k, double* y, double* alpha, cudaStream_t s);
+                         const int64_t* ij, int64_t k, double* y, double* alpha, double* err, cudaStream_t s);
+
+// Listed rays -> source positions in float-float (the certified re-evaluation).
+cudaError_t launch_trace_ff(const rsdev::FieldDev& f, double or0, double or1, double sp0, double sp1,
+                            const int64_t* ij, int64_t k, double* y, double* alpha, cudaStream_t s);
+
+// Re-evaluate and bin the listed rays (single: one field, descriptor by value; else descs[field]).
+cudaError_t launch_recheck(const rsdev::ShootDesc* single, const rsdev::ShootDesc* descs, const uint2* list,
+                           const unsigned int* count, unsigned int cap, int grid, cudaStream_t s);
+
+// Capacity of the re-evaluation list for a call of n_rays rays.
+inline unsigned int recheck_capacity(int64_t n_rays) {
+  int64_t c = n_rays / 32;
+  if (c < 4096) c = n_rays < 4096 ? n_rays : 4096;
+  if (c > ((int64_t)1 << 24)) c = (int64_t)1 << 24;
+  return (unsigned int)c;
+}
 
 // Persistent batched launch over LPT-ordered (field, ray tile) items.
-cudaError_t launch_batch(int cfg, const rsdev::ShootDesc* descs, const int2* items, int n_items,
+// mass: the items all belong to fields with (true) or without (false) per-lens masses.
+cudaError_t launch_batch(int cfg, bool mass, const rsdev::ShootDesc* descs, const int2* items, int n_items,
                          int* counter, int grid, cudaStream_t s);
-cudaError_t batch_blocks_per_sm(int cfg, int* blocks);
+cudaError_t batch_blocks_per_sm(int cfg, bool mass, int* blocks);
 
 }  // namespace rsint

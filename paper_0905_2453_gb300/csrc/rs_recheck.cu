@@ -1,0 +1,161 @@
+// Certified binning: float-float re-evaluation of the rays the float32 shoot could not bin with
+// certainty (source position within its error band of a pixel or window edge).
+//
+// Each listed ray's deflection (Eq. 2) is summed again over all lenses of its field in
+// float-float ("double-float") arithmetic on the FP32 pipe -- about 2^-44 relative per term,
+// eighty times cheaper on GB300 than float64 -- then mapped (Eq. 6) and binned exactly as in the
+// shoot epilogue.  One thread per listed ray; the lens loop reads the field's device arrays
+// directly (all threads of a warp usually walk the same field in step, so loads broadcast).
+#include "rs_internal.h"
+
+namespace {
+
+using namespace rsdev;
+
+// s + e = a + b exactly (Knuth).
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+// s + e = a + b exactly when |a| >= |b| (Dekker).
+__device__ __forceinline__ void fast_two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  e = __fsub_rn(b, __fsub_rn(s, a));
+}
+// (ah, al) += (bh, bl)
+__device__ __forceinline__ void ff_add(float& ah, float& al, float bh, float bl) {
+  float s, e;
+  two_sum(ah, bh, s, e);
+  e = __fadd_rn(e, __fadd_rn(al, bl));
+  fast_two_sum(s, e, ah, al);
+}
+
+// Deflection of one ray by lenses [0, n) in float-float; returns alpha as doubles.
+template <bool MASS>
+__device__ void deflect_ff(const FieldDev& f, float x1, float x2, double& a1, double& a2) {
+  float A1h = 0.f, A1l = 0.f, A2h = 0.f, A2l = 0.f;
+  const int n = f.n_lens;
+  for (int l = 0; l < n; ++l) {
+    const float4 L = __ldg(f.lens4 + l);
+    // exact differences x - x_l as float pairs
+    float ah, al, bh, bl;
+    two_sum(x1, -L.x, ah, al);
+    two_sum(x2, -L.z, bh, bl);
+    // r^2 = (ah + al)^2 + (bh + bl)^2 to ~2^-46 relative (al^2, bl^2 dropped)
+    const float p = __fmul_rn(ah, ah);
+    float pe = __fmaf_rn(ah, ah, -p);
+    pe = __fmaf_rn(__fmul_rn(2.f, ah), al, pe);
+    const float q = __fmul_rn(bh, bh);
+    float qe = __fmaf_rn(bh, bh, -q);
+    qe = __fmaf_rn(__fmul_rn(2.f, bh), bl, qe);
+    float s, se;
+    two_sum(p, q, s, se);
+    se = __fadd_rn(se, __fadd_rn(pe, qe));
+    float rh, rl;
+    fast_two_sum(s, se, rh, rl);
+    // w = 1 / r^2: approximate reciprocal plus one Newton correction from the exact residual
+    const float w0 = rcp_approx(rh);
+    float e = __fmaf_rn(-rh, w0, 1.f);
+    e = __fmaf_rn(-rl, w0, e);
+    float wh, wl;
+    fast_two_sum(w0, __fmul_rn(w0, e), wh, wl);
+    if (MASS) {
+      const float m = __ldg(f.mass2 + l).x;
+      const float mh = __fmul_rn(wh, m);
+      float ml = __fmaf_rn(wh, m, -mh);
+      ml = __fmaf_rn(wl, m, ml);
+      fast_two_sum(mh, ml, wh, wl);
+    }
+    // terms w * d, accumulated in float-float
+    const float t1h = __fmul_rn(wh, ah);
+    float t1l = __fmaf_rn(wh, ah, -t1h);
+    t1l = __fmaf_rn(wh, al, t1l);
+    t1l = __fmaf_rn(wl, ah, t1l);
+    const float t2h = __fmul_rn(wh, bh);
+    float t2l = __fmaf_rn(wh, bh, -t2h);
+    t2l = __fmaf_rn(wh, bl, t2l);
+    t2l = __fmaf_rn(wl, bh, t2l);
+    ff_add(A1h, A1l, t1h, t1l);
+    ff_add(A2h, A2l, t2h, t2l);
+  }
+  a1 = (double)A1h + (double)A1l;
+  a2 = (double)A2h + (double)A2l;
+}
+
+template <bool SINGLE>
+__global__ void __launch_bounds__(128) recheck_kernel(const ShootDesc one, const ShootDesc* __restrict__ descs,
+                                                      const uint2* __restrict__ list,
+                                                      const unsigned int* __restrict__ count, unsigned int cap) {
+  const unsigned int n = min(*count, cap);
+  for (unsigned int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
+    const uint2 it = list[e];
+    const ShootDesc& d = SINGLE ? one : descs[it.x];
+    const int64_t r = (int64_t)it.y;
+    const int64_t jrel = r / d.n0;
+    const int64_t i = r - jrel * d.n0;
+    const float x1 = ray_coord(i, d.sp0, d.or0);
+    const float x2 = ray_coord(d.j_begin + jrel, d.sp1, d.or1);
+    double a1, a2;
+    if (d.f.has_mass)
+      deflect_ff<true>(d.f, x1, x2, a1, a2);
+    else
+      deflect_ff<false>(d.f, x1, x2, a1, a2);
+    const double y1 = __dsub_rn(__dmul_rn(d.f.lam1, (double)x1), a1);
+    const double y2 = __dsub_rn(__dmul_rn(d.f.lam2, (double)x2), a2);
+    const double u1 = __dmul_rn(__dsub_rn(y1, d.lo0), d.sc0);
+    const double u2 = __dmul_rn(__dsub_rn(y2, d.lo1), d.sc1);
+    const bool inwin = (u1 >= 0.0) && (u1 < (double)d.np0) && (u2 >= 0.0) && (u2 < (double)d.np1);
+    if (inwin) {
+      const int p1 = (int)floor(u1);
+      const int p2 = (int)floor(u2);
+      atomicAdd(d.counts + (size_t)p2 * (size_t)d.np0 + (size_t)p1, 1u);
+    } else if (d.oow != nullptr) {
+      atomicAdd(d.oow, 1ull);
+    }
+  }
+}
+
+__global__ void __launch_bounds__(128) trace_ff_kernel(const FieldDev f, double or0, double or1, double sp0,
+                                                       double sp1, const int64_t* __restrict__ ij, int64_t k,
+                                                       double* __restrict__ y, double* __restrict__ alpha) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= k) return;
+  const float x1 = ray_coord(ij[2 * r], sp0, or0);
+  const float x2 = ray_coord(ij[2 * r + 1], sp1, or1);
+  double a1, a2;
+  if (f.has_mass)
+    deflect_ff<true>(f, x1, x2, a1, a2);
+  else
+    deflect_ff<false>(f, x1, x2, a1, a2);
+  y[2 * r] = __dsub_rn(__dmul_rn(f.lam1, (double)x1), a1);
+  y[2 * r + 1] = __dsub_rn(__dmul_rn(f.lam2, (double)x2), a2);
+  if (alpha != nullptr) {
+    alpha[2 * r] = a1;
+    alpha[2 * r + 1] = a2;
+  }
+}
+
+}  // namespace
+
+namespace rsint {
+
+cudaError_t launch_recheck(const rsdev::ShootDesc* single, const rsdev::ShootDesc* descs, const uint2* list,
+                           const unsigned int* count, unsigned int cap, int grid, cudaStream_t s) {
+  if (cap == 0) return cudaSuccess;
+  if (single != nullptr)
+    recheck_kernel<true><<<grid, 128, 0, s>>>(*single, nullptr, list, count, cap);
+  else
+    recheck_kernel<false><<<grid, 128, 0, s>>>(rsdev::ShootDesc{}, descs, list, count, cap);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_trace_ff(const rsdev::FieldDev& f, double or0, double or1, double sp0, double sp1,
+                            const int64_t* ij, int64_t k, double* y, double* alpha, cudaStream_t s) {
+  if (k <= 0) return cudaSuccess;
+  const int64_t grid = (k + 127) / 128;
+  trace_ff_kernel<<<(unsigned)grid, 128, 0, s>>>(f, or0, or1, sp0, sp1, ij, k, y, alpha);
+  return cudaGetLastError();
+}
+
+}  // namespace rsint

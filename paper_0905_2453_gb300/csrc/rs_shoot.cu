@@ -16,7 +16,7 @@ __global__ void __launch_bounds__(WARPS * 32) shoot_kernel(const ShootDesc d) {
 template <int BLOCK, int RPT, int TILE, bool MASS>
 __global__ void __launch_bounds__(BLOCK)
     trace_kernel(const FieldDev f, double or0, double or1, double sp0, double sp1, const int64_t* __restrict__ ij,
-                 int64_t k, double* __restrict__ y, double* __restrict__ alpha) {
+                 int64_t k, double* __restrict__ y, double* __restrict__ alpha, double* __restrict__ err) {
   __shared__ LensSmem<TILE> sm;
   PipeState ps;
   pipe_init(sm.bar, ps);
@@ -32,16 +32,23 @@ __global__ void __launch_bounds__(BLOCK)
     x2[q] = ray_coord(ij[2 * r + 1], sp1, or1);
   }
   double a1[RPT], a2[RPT];
-  if (!deflect<RPT, TILE, MASS, false, 1>(f, x1, x2, a1, a2, sm, ps)) return;
+  float sig[RPT];
+  if (!deflect<RPT, TILE, MASS, false, 1>(f, x1, x2, a1, a2, sig, sm, ps)) return;
 #pragma unroll
   for (int q = 0; q < RPT; ++q) {
     if (!valid[q]) continue;
     const int64_t r = base + (int64_t)q * BLOCK + threadIdx.x;
-    y[2 * r] = __dsub_rn(__dmul_rn(f.lam1, (double)x1[q]), a1[q]);
-    y[2 * r + 1] = __dsub_rn(__dmul_rn(f.lam2, (double)x2[q]), a2[q]);
+    const double y1 = __dsub_rn(__dmul_rn(f.lam1, (double)x1[q]), a1[q]);
+    const double y2 = __dsub_rn(__dmul_rn(f.lam2, (double)x2[q]), a2[q]);
+    y[2 * r] = y1;
+    y[2 * r + 1] = y2;
     if (alpha != nullptr) {
       alpha[2 * r] = a1[q];
       alpha[2 * r + 1] = a2[q];
+    }
+    if (err != nullptr) {
+      err[2 * r] = band_halfwidth(sig[q], y1, a1[q]);
+      err[2 * r + 1] = band_halfwidth(sig[q], y2, a2[q]);
     }
   }
 }
@@ -75,14 +82,14 @@ cudaError_t launch_shoot(int cfg, const rsdev::ShootDesc& d, cudaStream_t s) {
 }
 
 cudaError_t launch_trace(const rsdev::FieldDev& f, double or0, double or1, double sp0, double sp1,
-                         const int64_t* ij, int64_t k, double* y, double* alpha, cudaStream_t s) {
+                         const int64_t* ij, int64_t k, double* y, double* alpha, double* err, cudaStream_t s) {
   constexpr int B = 128, R = 4;
   if (k <= 0) return cudaSuccess;
   const int64_t grid = (k + B * R - 1) / (B * R);
   if (f.has_mass)
-    trace_kernel<B, R, kTile, true><<<(unsigned)grid, B, 0, s>>>(f, or0, or1, sp0, sp1, ij, k, y, alpha);
+    trace_kernel<B, R, kTile, true><<<(unsigned)grid, B, 0, s>>>(f, or0, or1, sp0, sp1, ij, k, y, alpha, err);
   else
-    trace_kernel<B, R, kTile, false><<<(unsigned)grid, B, 0, s>>>(f, or0, or1, sp0, sp1, ij, k, y, alpha);
+    trace_kernel<B, R, kTile, false><<<(unsigned)grid, B, 0, s>>>(f, or0, or1, sp0, sp1, ij, k, y, alpha, err);
   return cudaGetLastError();
 }
 

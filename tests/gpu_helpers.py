@@ -42,21 +42,26 @@ def shoot_gpu(field_spec, grid=None, window=None, rows=None, counts=None, oow=No
     return counts.cpu().numpy().view(np.uint32), int(oow.item())
 
 
-def trace_gpu(field_spec, ray_ij, grid=None, chunk=1 << 22):
+def trace_gpu(field_spec, ray_ij, grid=None, chunk=1 << 22, certified=False):
+    """float32-path source positions and band half-widths (or float-float positions if certified)."""
     m = rs()
     grid = grid or field_spec.grid
     f = m.Field.from_spec(field_spec)
     try:
         ij = np.asarray(ray_ij, np.int64).reshape(-1, 2)
-        ys, als = [], []
+        ys, es = [], []
         for s in range(0, ij.shape[0], chunk):
-            y, a = f.trace(grid, torch.from_numpy(ij[s:s + chunk]), with_alpha=True)
-            ys.append(y.cpu().numpy())
-            als.append(a.cpu().numpy())
+            t = torch.from_numpy(ij[s:s + chunk])
+            if certified:
+                ys.append(f.trace(grid, t, certified=True).cpu().numpy())
+            else:
+                y, e = f.trace(grid, t, with_err=True)
+                ys.append(y.cpu().numpy())
+                es.append(e.cpu().numpy())
         torch.cuda.synchronize()
     finally:
         f.close()
-    return np.concatenate(ys), np.concatenate(als)
+    return np.concatenate(ys), (np.concatenate(es) if es else None)
 
 
 def all_rays(grid, rows=None):

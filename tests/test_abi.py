@@ -75,7 +75,8 @@ def test_validation_codes(rs):
     g = rs._cgrid(rs.RayGrid((0.0, 0.0), (1.0, 1.0), (4, 4)))
     w = rs._cwin(rs.Window((-1.0, -1.0), (1.0, 1.0), (4, 4)))
     assert lib.rs_shoot(None, ctypes.byref(g), ctypes.byref(w), None, None, None) == rs.RS_EINVAL
-    assert lib.rs_trace(None, ctypes.byref(g), None, 1, None, None, None) == rs.RS_EINVAL
+    assert lib.rs_trace(None, ctypes.byref(g), None, 1, None, None, None, None) == rs.RS_EINVAL
+    assert lib.rs_trace_certified(None, ctypes.byref(g), None, 1, None, None, None) == rs.RS_EINVAL
     assert lib.rs_batch_create(0, None, None, None, None, None, ctypes.byref(h)) == rs.RS_EINVAL
     assert lib.rs_destroy_field(None) == rs.RS_OK
     assert lib.rs_batch_destroy(None) == rs.RS_OK

@@ -55,38 +55,53 @@ def test_nonsquare_grid_window_layout():
 
 
 def _check_per_ray(spec, ij, label):
-    """Per-ray source positions: rigorous float32 bound for every ray, and the measured
-    distribution against the 1e-5-pixel target (reported; below the float32 floor at small N)."""
-    y_gpu, _ = trace_gpu(spec, ij)
+    """Per-ray source positions.
+
+    float32 path: within the rigorous operation-count bound for every ray, and within its own
+    band half-width (the estimate certified binning relies on) for every ray.
+    float-float path (certified re-evaluation): within the 1e-5-pixel per-ray tolerance.
+    """
+    y_gpu, band = trace_gpu(spec, ij)
+    y_ff, _ = trace_gpu(spec, ij, certified=True)
     y_ref, _, x = oracle.trace_field(spec, ij)
     fin = np.isfinite(y_ref).all(1)
     assert np.array_equal(fin, np.isfinite(y_gpu).all(1))
+    assert np.array_equal(fin, np.isfinite(y_ff).all(1))
     bound = per_ray_bound(spec, x[fin], y_ref[fin])
-    err = np.abs(y_gpu[fin] - y_ref[fin]).max(1)
-    assert np.all(err <= bound), (label, float((err / bound).max()))
+    err = np.abs(y_gpu[fin] - y_ref[fin])
+    assert np.all(err.max(1) <= bound), (label, float((err.max(1) / bound).max()))
+    assert np.all(err <= band[fin]), (label, float((err / band[fin]).max()))
     st = error_stats(y_gpu, y_ref, spec.window)
-    print(f"{label} per-ray error (pixels): {st}")
+    st_ff = error_stats(y_ff, y_ref, spec.window)
+    print(f"{label} float32 per-ray error (pixels): {st}; worst error / band = "
+          f"{float((err / band[fin]).max()):.3f}")
+    print(f"{label} float-float per-ray error (pixels): {st_ff}")
+    assert st_ff["max"] <= PER_RAY_TOL_PIX
     return y_gpu, y_ref, st
 
 
 def test_tiny_field_full_map_and_every_ray():
-    """100 lenses, 1000^2 rays, 256^2 map: every ray traced against the oracle; the shot map is
-    the binning of the traced rays; map-level agreement with the oracle."""
+    """100 lenses, 1000^2 rays, 256^2 map: every ray traced against the oracle; the certified
+    map equals the oracle's map; without certification the map is the binning of the traced rays."""
     f = ri.tiny_field()
     counts, oow = shoot_gpu(f)
     assert int(counts.sum()) + oow == f.grid.n_rays
     y_gpu, y_ref, st = _check_per_ray(f, all_rays(f.grid), "tiny field")
     assert st["p50"] <= 3e-5 and st["p99"] <= 2e-4
-    # the traced rays bin exactly into the shot map (same arithmetic)
+    ref, oow_ref = oracle.shoot_field(f)
+    assert np.array_equal(counts, ref) and oow == oow_ref
+    m = rs()
+    m.rs_set_certified_binning(False)
+    try:
+        fast, _ = shoot_gpu(f)
+    finally:
+        m.rs_set_certified_binning(True)
     p = pixel_index(y_gpu, f.window)
     rebinned = np.bincount(p[p >= 0], minlength=f.window.n_pix).reshape(counts.shape)
-    assert np.array_equal(rebinned, counts)
+    assert np.array_equal(rebinned, fast)
     flips = int((p != pixel_index(y_ref, f.window)).sum())
-    print("tiny field flips:", flips, "of", p.size)
+    print("tiny field float32 flips (uncertified):", flips, "of", p.size)
     assert flips / p.size <= FLIP_FRAC_TOL
-    ref, oow_ref = oracle.shoot_field(f)
-    d = np.abs(counts.astype(np.int64) - ref.astype(np.int64))
-    assert np.all(d <= np.maximum(1, 1e-3 * ref))
 
 
 def test_point_lens_map():
@@ -193,8 +208,6 @@ def test_n1e4_full_size_sampled_rays():
     ij = ri.sample_rays(f.grid, 20000, seed=123)
     y_gpu, y_ref, st = _check_per_ray(f, ij, "N=1e4")
     assert st["p50"] <= 3e-5 and st["p99"] <= 2e-4
-    flips = int((pixel_index(y_gpu, f.window) != pixel_index(y_ref, f.window)).sum())
-    assert flips <= 2
     counts, oow = shoot_gpu(f)
     assert int(counts.sum()) + oow == f.grid.n_rays
 
@@ -212,25 +225,48 @@ def test_n1e4_full_map_vs_oracle():
 
 
 def test_map_of_1e8_rays_flips_and_pixels():
-    """1.05e8 rays (10240^2 over [-10, 10]^2) through the 100-lens field: per-ray pixel flips
-    <= 1e-5 of rays and per-pixel |N - N_oracle| <= max(1, 1e-3 N_oracle)."""
+    """1.05e8 rays (10240^2 over [-10, 10]^2) through the 100-lens field: the certified map
+    against the oracle's map -- per-pixel |N - N_oracle| <= max(1, 1e-3 N_oracle) and at most
+    1e-5 of the rays moved; and the float32 path alone (uncertified) measured per ray."""
     base = ri.tiny_field()
     g = ri.cell_centred_grid(-10.0, 10.0, 10240)
     f = ri.Field("tiny-1e8", base.lens_xy, base.masses, 0.0, 0.0, g, base.window)
     counts, oow = shoot_gpu(f)
-    ref = np.zeros_like(counts)
-    flips = 0
-    step = 512
-    for jb in range(0, 10240, step):
-        ij = all_rays(g, rows=(jb, jb + step))
+    ref, oow_ref = oracle.shoot_field(f)
+    assert int(counts.sum()) + oow == g.n_rays
+    d = counts.astype(np.int64) - ref.astype(np.int64)
+    moved = int(np.abs(d).sum()) // 2 + abs(oow - oow_ref)
+    print("1e8-ray certified map: rays moved", moved, "of", g.n_rays)
+    assert moved <= FLIP_FRAC_TOL * g.n_rays
+    assert np.all(np.abs(d) <= np.maximum(1, 1e-3 * ref))
+    # float32 decisions alone: per-ray flips, every 4th row block
+    flips, n = 0, 0
+    for jb in range(0, 10240, 2048):
+        ij = all_rays(g, rows=(jb, jb + 512))
         y_gpu, _ = trace_gpu(f, ij)
         y_ref, _, _ = oracle.trace_field(f, ij)
-        p_gpu = pixel_index(y_gpu, f.window)
-        p_ref = pixel_index(y_ref, f.window)
-        flips += int((p_gpu != p_ref).sum())
-        ref += np.bincount(p_ref[p_ref >= 0], minlength=f.window.n_pix).reshape(ref.shape).astype(np.uint32)
-    print("1e8-ray map flips:", flips, "of", g.n_rays)
-    assert flips <= FLIP_FRAC_TOL * g.n_rays
-    assert int(counts.sum()) + oow == g.n_rays
-    d = np.abs(counts.astype(np.int64) - ref.astype(np.int64))
-    assert np.all(d <= np.maximum(1, 1e-3 * ref))
+        flips += int((pixel_index(y_gpu, f.window) != pixel_index(y_ref, f.window)).sum())
+        n += ij.shape[0]
+    print("float32-only flips:", flips, "of", n)
+    assert flips <= FLIP_FRAC_TOL * n
+
+
+def test_bounded_wait_reports_timeout_and_device_stays_usable():
+    """A wait that nothing completes gives up after its limit with RS_ETIMEOUT (no hang, no fault),
+    and the device keeps working afterwards."""
+    m = rs()
+    assert m.rs_selftest_bounded_wait(10_000_000) == m.RS_ETIMEOUT
+    f = ri.tiny_field()
+    counts, oow = shoot_gpu(f)
+    assert int(counts.sum()) + oow == f.grid.n_rays
+
+
+def test_certified_trace_matches_oracle_large_fields():
+    """Float-float re-evaluation on the 1e6-lens Salpeter field: sampled rays within 1e-5 pixel."""
+    f = ri.n1e6_salpeter_field()
+    ij = ri.sample_rays(f.grid, 512, seed=9)
+    y_ff, _ = trace_gpu(f, ij, certified=True)
+    y_ref, _, _ = oracle.trace_field(f, ij)
+    st = error_stats(y_ff, y_ref, f.window)
+    print("N=1e6 float-float per-ray error (pixels):", st)
+    assert st["max"] <= PER_RAY_TOL_PIX
