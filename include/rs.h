@@ -149,7 +149,7 @@ int rs_trace_certified(rs_field_t f, const rs_ray_grid* g, const int64_t* d_ray_
 
 /*
  * Certified binning (on by default).  The float32 shoot attaches to every ray an error
- * estimate sigma = 6 u sqrt(32 sum_g (P1_g^2 + P2_g^2)) (u = 2^-24, P_g the float32 partial
+ * estimate sigma = 10 u sqrt(32 sum_g (P1_g^2 + P2_g^2)) (u = 2^-24, P_g the float32 partial
  * sums of its 32-lens groups).  A ray whose source position lies within that band of a pixel
  * or window edge is not binned by the float32 result but re-evaluated with
  * rs_trace_certified's arithmetic and binned from that; the maps then agree with a float64

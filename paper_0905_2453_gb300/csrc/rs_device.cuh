@@ -189,7 +189,7 @@ struct ShootDesc {
 // Certified binning: a ray whose float32 source position lies within kSigmaSafety * sigma of a
 // pixel edge (sigma: the per-ray error estimate below) is re-evaluated in float-float arithmetic
 // before it is counted.
-constexpr float kSigmaSafety = 6.0f;
+constexpr float kSigmaSafety = 10.0f;
 // sigma = u sqrt(32 sum_g (P1_g^2 + P2_g^2)): the rounding of a 32-lens float32 group partial is a
 // random walk of at most 32 steps of ~u |P_g|; u = 2^-24.
 constexpr float kSigmaScale = 5.9604645e-08f * 5.656854249f * kSigmaSafety;
