@@ -217,6 +217,29 @@ int rs_get_launch_config(int has_masses, int* block, int* rays_per_thread);
 int rs_launch_configs(int* pairs, int cap, int* count);
 
 /*
+ * rs_shoot_rows_noalloc -- rs_shoot_rows with certified binning, allocating nothing.
+ * The paper has no counterpart: this entry point serves callers that cannot allocate device
+ * memory while they run (work replayed in a CUDA graph whose capture must not contain
+ * allocation nodes; applications whose allocator reserved the device memory at start-up;
+ * latency-critical loops that cannot wait on an allocator).
+ * Identical results to rs_shoot_rows with certified binning on (the global switch
+ * rs_set_certified_binning does not apply: this variant always certifies).  Its list of rays to
+ * re-evaluate lives in a static device array of 2^19 entries (4 MiB + 256 B, resident on every
+ * device that loads the library until the process exits) instead of a per-call allocation:
+ *   - at most 2^24 rays per call (one list entry per 32 rays); larger row ranges return
+ *     RS_EOVERFLOW without launching anything -- split them over several calls;
+ *   - the first call on a device looks up the array's device address (cudaGetSymbolAddress,
+ *     with that device current); make that first call before any stream capture;
+ *   - every call shares the array and the array keeps the last call's contents; each call
+ *     clears the entry counter on its stream.  Calls that overlap on the GPU (different
+ *     streams, or different host threads, without ordering between them) race on the array:
+ *     order them on one stream or with events.
+ * Arguments and accumulation semantics as rs_shoot_rows.
+ */
+int rs_shoot_rows_noalloc(rs_field_t f, const rs_ray_grid* g, int64_t row_begin, int64_t row_end,
+                          const rs_window* w, uint32_t* d_counts, uint64_t* d_out_of_window, void* stream);
+
+/*
  * rs_selftest_bounded_wait -- run one CTA that waits on an mbarrier phase nothing completes,
  * bounded by limit_ns (0 .. 2e9) of the device's global timer, the same bounded wait the
  * kernels use for lens-tile copies.  *status = RS_ETIMEOUT when the wait gave up (the expected

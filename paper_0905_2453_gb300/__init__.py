@@ -29,7 +29,7 @@ __all__ = [
     "rs_magnification", "rs_batch_create", "rs_batch_launch", "rs_batch_destroy", "rs_shoot_batch",
     "rs_field_status", "rs_last_error", "rs_version", "rs_set_launch_config", "rs_get_launch_config",
     "rs_launch_configs", "rs_trace_certified", "rs_set_certified_binning", "rs_get_certified_binning",
-    "rs_selftest_bounded_wait", "EXPORTED_SYMBOLS",
+    "rs_selftest_bounded_wait", "rs_shoot_rows_noalloc", "EXPORTED_SYMBOLS",
 ]
 
 RS_OK, RS_EINVAL, RS_ENOMEM, RS_ECUDA, RS_EOVERFLOW, RS_ETIMEOUT = 0, 1, 2, 3, 4, 5
@@ -40,7 +40,7 @@ EXPORTED_SYMBOLS = (
     "rs_magnification", "rs_batch_create", "rs_batch_launch", "rs_batch_destroy", "rs_shoot_batch",
     "rs_field_status", "rs_last_error", "rs_version", "rs_set_launch_config", "rs_get_launch_config",
     "rs_launch_configs", "rs_trace_certified", "rs_set_certified_binning", "rs_get_certified_binning",
-    "rs_selftest_bounded_wait",
+    "rs_selftest_bounded_wait", "rs_shoot_rows_noalloc",
 )
 
 
@@ -107,6 +107,7 @@ def load():
         "rs_set_certified_binning": ([i32], i32),
         "rs_get_certified_binning": ([ctypes.POINTER(i32)], i32),
         "rs_selftest_bounded_wait": ([i64, ctypes.POINTER(i32)], i32),
+        "rs_shoot_rows_noalloc": ([vp, gp, i64, i64, wp, vp, vp, vp], i32),
         "rs_magnification": ([vp, gp, wp, vp, vp], i32),
         "rs_batch_create": ([i32, vp, vp, vp, vp, vp, ctypes.POINTER(vp)], i32),
         "rs_batch_launch": ([vp, vp], i32),
@@ -249,6 +250,18 @@ def rs_shoot_rows(handle: int, grid, row_begin: int, row_end: int, window, count
     g, w = _cgrid(grid), _cwin(window)
     _check(load().rs_shoot_rows(handle, ctypes.byref(g), int(row_begin), int(row_end), ctypes.byref(w), pc, po,
                                 _stream(stream)), "rs_shoot_rows")
+
+
+def rs_shoot_rows_noalloc(handle: int, grid, row_begin: int, row_end: int, window, counts, out_of_window=None,
+                          stream=None):
+    """rs_shoot_rows with certified binning that allocates no device memory (for callers that
+    cannot allocate while they run); at most 2^24 rays per call, see include/rs.h."""
+    npx = int(window.npix[0]) * int(window.npix[1])
+    pc = _dptr(counts, _COUNT_DTYPES, "counts", npx)
+    po = _dptr(out_of_window, _OOW_DTYPES, "out_of_window", 1)
+    g, w = _cgrid(grid), _cwin(window)
+    _check(load().rs_shoot_rows_noalloc(handle, ctypes.byref(g), int(row_begin), int(row_end), ctypes.byref(w), pc,
+                                        po, _stream(stream)), "rs_shoot_rows_noalloc")
 
 
 def rs_trace(handle: int, grid, ray_ij: torch.Tensor, y: torch.Tensor, alpha: torch.Tensor = None,

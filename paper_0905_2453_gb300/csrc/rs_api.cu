@@ -6,6 +6,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -674,3 +675,76 @@ int rs_shoot_batch(int n_fields, const rs_field_t* fields, const rs_ray_grid* gr
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------------------------------------------------ no allocation
+//
+// rs_shoot_rows_noalloc: rs_shoot_rows with certified binning whose re-evaluation list lives in
+// this file's static device array instead of memory allocated per call.  For callers that must
+// not allocate device memory once they run: code replayed inside a CUDA graph whose capture
+// forbids allocation nodes, applications whose own allocator has reserved the device memory up
+// front, and latency-critical loops that cannot afford an allocator call.
+
+// Re-evaluation list shared by every rs_shoot_rows_noalloc call: a 256-byte header (the entry
+// counter) followed by up to kStaticRecheckEntries {field, ray} entries.  4 MiB + 256 B on each
+// device that loads the library, held until the process exits.
+constexpr unsigned int kStaticRecheckEntries = 1u << 19;
+static __device__ __align__(256) unsigned char g_static_recheck[256 + sizeof(uint2) * kStaticRecheckEntries];
+
+namespace {
+
+constexpr int kMaxDevices = 64;
+std::mutex g_static_mutex;
+void* g_static_ptr[kMaxDevices] = {};
+
+// Device address of g_static_recheck on the current device, looked up once per device.  In host
+// code the array's name only stands in for the device symbol; its address must come from
+// cudaGetSymbolAddress with the device current.
+int static_recheck_ptr(int device, void** out) {
+  if (device < 0 || device >= kMaxDevices) return fail(RS_EINVAL, "device index %d beyond %d", device, kMaxDevices);
+  std::lock_guard<std::mutex> lock(g_static_mutex);
+  if (!g_static_ptr[device]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_static_recheck);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress (static re-evaluation list)");
+    g_static_ptr[device] = p;
+  }
+  *out = g_static_ptr[device];
+  return RS_OK;
+}
+
+}  // namespace
+
+extern "C" int rs_shoot_rows_noalloc(rs_field_t f, const rs_ray_grid* g, int64_t row_begin, int64_t row_end,
+                                     const rs_window* w, uint32_t* d_counts, uint64_t* d_out_of_window,
+                                     void* stream) {
+  if (!f) return fail(RS_EINVAL, "field is NULL");
+  int rc;
+  if ((rc = check_grid(g)) != RS_OK) return rc;
+  if ((rc = check_window(w)) != RS_OK) return rc;
+  if (!d_counts) return fail(RS_EINVAL, "d_counts is NULL");
+  if (row_begin < 0 || row_end < row_begin || row_end > g->n[1])
+    return fail(RS_EINVAL, "row range [%lld, %lld) outside [0, %lld]", (long long)row_begin, (long long)row_end,
+                (long long)g->n[1]);
+  if ((rc = check_field_device(f)) != RS_OK) return rc;
+  ShootDesc d;
+  if ((rc = fill_desc(f, g, row_begin, row_end, w, d_counts, d_out_of_window, &d)) != RS_OK) return rc;
+  if (d.n_rows == 0 || d.n0 == 0) return RS_OK;
+  const unsigned int cap = rsint::recheck_capacity(d.n_rows * d.n0);
+  if (cap > kStaticRecheckEntries)
+    return fail(RS_EOVERFLOW,
+                "rs_shoot_rows_noalloc shoots at most 2^24 rays per call (its static re-evaluation list holds %u "
+                "entries, one per 32 rays); got %lld rays: split the rows over several calls",
+                kStaticRecheckEntries, (long long)(d.n_rows * d.n0));
+  void* base = nullptr;
+  if ((rc = static_recheck_ptr(f->device, &base)) != RS_OK) return rc;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  d.rc_count = reinterpret_cast<unsigned int*>(base);
+  d.rc_list = reinterpret_cast<uint2*>(reinterpret_cast<char*>(base) + 256);
+  d.rc_cap = cap;
+  // the array keeps the previous call's contents: only the counter must start at zero
+  cudaError_t e = cudaMemsetAsync(d.rc_count, 0, sizeof(unsigned int), s);
+  if (e == cudaSuccess) e = rsint::launch_shoot(g_cfg[f->dev.has_mass ? 1 : 0], d, s);
+  if (e == cudaSuccess) e = rsint::launch_recheck(&d, nullptr, d.rc_list, d.rc_count, d.rc_cap, recheck_grid(f->device), s);
+  if (e != cudaSuccess) return cuda_fail(e, "shoot launch (no-allocation variant)");
+  return RS_OK;
+}
