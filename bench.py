@@ -266,7 +266,12 @@ def run_ours(args):
     stream = torch.cuda.current_stream(device)
     field = rs.Field.from_spec(spec, stream)
     from paper_0905_2453_gb300 import tune
-    shape = tune.autotune(field, spec.grid, spec.window, stream=stream)
+    if args.launch_shape:
+        b_, r_ = (int(v) for v in args.launch_shape.split("x"))
+        rs.rs_set_launch_config(spec.masses is not None, b_, r_)
+        shape = (b_, r_, {})
+    else:
+        shape = tune.autotune(field, spec.grid, spec.window, stream=stream)
     npix = (int(spec.window.npix[1]), int(spec.window.npix[0]))
     counts = torch.zeros(npix, dtype=torch.int32, device=device)
     oow = torch.zeros(1, dtype=torch.int64, device=device)
@@ -367,7 +372,7 @@ def run_ours(args):
     achieved = inter_step * FLOPS_PER_INTERACTION / shoot_avg_s / 1e12
     med = clk.get("sm_mhz")
     cfg = workload_config(spec, args.workload)
-    cfg["launch_shape"] = f"{shape[0]} threads x {shape[1]} rays/thread (autotuned)"
+    cfg["launch_shape"] = f"{shape[0]} threads x {shape[1]} rays/thread" + ("" if args.launch_shape else " (autotuned)")
     cfg["certified_binning"] = rs.rs_get_certified_binning()
     line = {
         "metric": METRIC, "value": value, "unit": "interactions/s", "n_gpus": world, "steps": args.steps,
@@ -454,6 +459,7 @@ def main():
     ap.add_argument("--batch-reps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--launch-shape", default=None, help="fix the launch shape, e.g. 128x8 (skips the autotuner)")
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")

@@ -3,9 +3,9 @@
 //
 // Each listed ray's deflection (Eq. 2) is summed again over all lenses of its field in
 // float-float ("double-float") arithmetic on the FP32 pipe -- about 2^-44 relative per term,
-// eighty times cheaper on GB300 than float64 -- then mapped (Eq. 6) and binned exactly as in the
-// shoot epilogue.  One thread per listed ray; the lens loop reads the field's device arrays
-// directly (all threads of a warp usually walk the same field in step, so loads broadcast).
+// far cheaper on GB300 than float64 -- then mapped (Eq. 6) and binned exactly as in the shoot
+// epilogue.  One warp per listed ray: the lanes split the lens loop (coalesced lens loads) and a
+// fixed reduction tree combines them, so the result is deterministic.
 #include "rs_internal.h"
 
 namespace {
@@ -31,64 +31,85 @@ __device__ __forceinline__ void ff_add(float& ah, float& al, float bh, float bl)
   fast_two_sum(s, e, ah, al);
 }
 
-// Deflection of one ray by lenses [0, n) in float-float; returns alpha as doubles.
+// One lens term of Eq. 2 for ray (x1, x2) in float-float, added to (A1h, A1l), (A2h, A2l).
 template <bool MASS>
-__device__ void deflect_ff(const FieldDev& f, float x1, float x2, double& a1, double& a2) {
+__device__ __forceinline__ void lens_term_ff(const FieldDev& f, int l, float x1, float x2, float& A1h, float& A1l,
+                                             float& A2h, float& A2l) {
+  const float4 L = __ldg(f.lens4 + l);
+  // exact differences x - x_l as float pairs
+  float ah, al, bh, bl;
+  two_sum(x1, -L.x, ah, al);
+  two_sum(x2, -L.z, bh, bl);
+  // r^2 = (ah + al)^2 + (bh + bl)^2 to ~2^-46 relative (al^2, bl^2 dropped)
+  const float p = __fmul_rn(ah, ah);
+  float pe = __fmaf_rn(ah, ah, -p);
+  pe = __fmaf_rn(__fmul_rn(2.f, ah), al, pe);
+  const float q = __fmul_rn(bh, bh);
+  float qe = __fmaf_rn(bh, bh, -q);
+  qe = __fmaf_rn(__fmul_rn(2.f, bh), bl, qe);
+  float s, se;
+  two_sum(p, q, s, se);
+  se = __fadd_rn(se, __fadd_rn(pe, qe));
+  float rh, rl;
+  fast_two_sum(s, se, rh, rl);
+  // w = 1 / r^2: approximate reciprocal plus one Newton correction from the exact residual
+  const float w0 = rcp_approx(rh);
+  float e = __fmaf_rn(-rh, w0, 1.f);
+  e = __fmaf_rn(-rl, w0, e);
+  float wh, wl;
+  fast_two_sum(w0, __fmul_rn(w0, e), wh, wl);
+  if (MASS) {
+    const float m = __ldg(f.mass2 + l).x;
+    const float mh = __fmul_rn(wh, m);
+    float ml = __fmaf_rn(wh, m, -mh);
+    ml = __fmaf_rn(wl, m, ml);
+    fast_two_sum(mh, ml, wh, wl);
+  }
+  // terms w * d, accumulated in float-float
+  const float t1h = __fmul_rn(wh, ah);
+  float t1l = __fmaf_rn(wh, ah, -t1h);
+  t1l = __fmaf_rn(wh, al, t1l);
+  t1l = __fmaf_rn(wl, ah, t1l);
+  const float t2h = __fmul_rn(wh, bh);
+  float t2l = __fmaf_rn(wh, bh, -t2h);
+  t2l = __fmaf_rn(wh, bl, t2l);
+  t2l = __fmaf_rn(wl, bh, t2l);
+  ff_add(A1h, A1l, t1h, t1l);
+  ff_add(A2h, A2l, t2h, t2l);
+}
+
+// Deflection of one ray by all lenses of the field in float-float, spread over the 32 lanes of
+// a warp: lane k sums lenses k, k + 32, ... in order; the 32 partial sums are combined by a fixed
+// tree (shuffle-down by 16, 8, 4, 2, 1).  Every lane must call it with the same ray; lane 0
+// returns alpha (the other lanes' values are partial).
+template <bool MASS>
+__device__ void deflect_ff_warp(const FieldDev& f, float x1, float x2, double& a1, double& a2) {
+  const int lane = threadIdx.x & 31;
   float A1h = 0.f, A1l = 0.f, A2h = 0.f, A2l = 0.f;
   const int n = f.n_lens;
-  for (int l = 0; l < n; ++l) {
-    const float4 L = __ldg(f.lens4 + l);
-    // exact differences x - x_l as float pairs
-    float ah, al, bh, bl;
-    two_sum(x1, -L.x, ah, al);
-    two_sum(x2, -L.z, bh, bl);
-    // r^2 = (ah + al)^2 + (bh + bl)^2 to ~2^-46 relative (al^2, bl^2 dropped)
-    const float p = __fmul_rn(ah, ah);
-    float pe = __fmaf_rn(ah, ah, -p);
-    pe = __fmaf_rn(__fmul_rn(2.f, ah), al, pe);
-    const float q = __fmul_rn(bh, bh);
-    float qe = __fmaf_rn(bh, bh, -q);
-    qe = __fmaf_rn(__fmul_rn(2.f, bh), bl, qe);
-    float s, se;
-    two_sum(p, q, s, se);
-    se = __fadd_rn(se, __fadd_rn(pe, qe));
-    float rh, rl;
-    fast_two_sum(s, se, rh, rl);
-    // w = 1 / r^2: approximate reciprocal plus one Newton correction from the exact residual
-    const float w0 = rcp_approx(rh);
-    float e = __fmaf_rn(-rh, w0, 1.f);
-    e = __fmaf_rn(-rl, w0, e);
-    float wh, wl;
-    fast_two_sum(w0, __fmul_rn(w0, e), wh, wl);
-    if (MASS) {
-      const float m = __ldg(f.mass2 + l).x;
-      const float mh = __fmul_rn(wh, m);
-      float ml = __fmaf_rn(wh, m, -mh);
-      ml = __fmaf_rn(wl, m, ml);
-      fast_two_sum(mh, ml, wh, wl);
-    }
-    // terms w * d, accumulated in float-float
-    const float t1h = __fmul_rn(wh, ah);
-    float t1l = __fmaf_rn(wh, ah, -t1h);
-    t1l = __fmaf_rn(wh, al, t1l);
-    t1l = __fmaf_rn(wl, ah, t1l);
-    const float t2h = __fmul_rn(wh, bh);
-    float t2l = __fmaf_rn(wh, bh, -t2h);
-    t2l = __fmaf_rn(wh, bl, t2l);
-    t2l = __fmaf_rn(wl, bh, t2l);
-    ff_add(A1h, A1l, t1h, t1l);
-    ff_add(A2h, A2l, t2h, t2l);
+  for (int l = lane; l < n; l += 32) lens_term_ff<MASS>(f, l, x1, x2, A1h, A1l, A2h, A2l);
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    const float b1h = __shfl_down_sync(0xffffffffu, A1h, off);
+    const float b1l = __shfl_down_sync(0xffffffffu, A1l, off);
+    const float b2h = __shfl_down_sync(0xffffffffu, A2h, off);
+    const float b2l = __shfl_down_sync(0xffffffffu, A2l, off);
+    ff_add(A1h, A1l, b1h, b1l);
+    ff_add(A2h, A2l, b2h, b2l);
   }
   a1 = (double)A1h + (double)A1l;
   a2 = (double)A2h + (double)A2l;
 }
 
+// One warp per listed ray.
 template <bool SINGLE>
 __global__ void __launch_bounds__(128) recheck_kernel(const ShootDesc one, const ShootDesc* __restrict__ descs,
                                                       const uint2* __restrict__ list,
                                                       const unsigned int* __restrict__ count, unsigned int cap) {
   const unsigned int n = min(*count, cap);
-  for (unsigned int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
+  const unsigned int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const unsigned int nwarps = (gridDim.x * blockDim.x) >> 5;
+  for (unsigned int e = warp; e < n; e += nwarps) {
     const uint2 it = list[e];
     const ShootDesc& d = SINGLE ? one : descs[it.x];
     const int64_t r = (int64_t)it.y;
@@ -98,9 +119,10 @@ __global__ void __launch_bounds__(128) recheck_kernel(const ShootDesc one, const
     const float x2 = ray_coord(d.j_begin + jrel, d.sp1, d.or1);
     double a1, a2;
     if (d.f.has_mass)
-      deflect_ff<true>(d.f, x1, x2, a1, a2);
+      deflect_ff_warp<true>(d.f, x1, x2, a1, a2);
     else
-      deflect_ff<false>(d.f, x1, x2, a1, a2);
+      deflect_ff_warp<false>(d.f, x1, x2, a1, a2);
+    if ((threadIdx.x & 31) != 0) continue;
     const double y1 = __dsub_rn(__dmul_rn(d.f.lam1, (double)x1), a1);
     const double y2 = __dsub_rn(__dmul_rn(d.f.lam2, (double)x2), a2);
     const double u1 = __dmul_rn(__dsub_rn(y1, d.lo0), d.sc0);
@@ -116,18 +138,20 @@ __global__ void __launch_bounds__(128) recheck_kernel(const ShootDesc one, const
   }
 }
 
+// One warp per listed ray, same evaluation as the re-evaluation above.
 __global__ void __launch_bounds__(128) trace_ff_kernel(const FieldDev f, double or0, double or1, double sp0,
                                                        double sp1, const int64_t* __restrict__ ij, int64_t k,
                                                        double* __restrict__ y, double* __restrict__ alpha) {
-  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (r >= k) return;
+  const int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (r >= k) return;  // whole warps leave together
   const float x1 = ray_coord(ij[2 * r], sp0, or0);
   const float x2 = ray_coord(ij[2 * r + 1], sp1, or1);
   double a1, a2;
   if (f.has_mass)
-    deflect_ff<true>(f, x1, x2, a1, a2);
+    deflect_ff_warp<true>(f, x1, x2, a1, a2);
   else
-    deflect_ff<false>(f, x1, x2, a1, a2);
+    deflect_ff_warp<false>(f, x1, x2, a1, a2);
+  if ((threadIdx.x & 31) != 0) return;
   y[2 * r] = __dsub_rn(__dmul_rn(f.lam1, (double)x1), a1);
   y[2 * r + 1] = __dsub_rn(__dmul_rn(f.lam2, (double)x2), a2);
   if (alpha != nullptr) {
@@ -153,7 +177,7 @@ cudaError_t launch_recheck(const rsdev::ShootDesc* single, const rsdev::ShootDes
 cudaError_t launch_trace_ff(const rsdev::FieldDev& f, double or0, double or1, double sp0, double sp1,
                             const int64_t* ij, int64_t k, double* y, double* alpha, cudaStream_t s) {
   if (k <= 0) return cudaSuccess;
-  const int64_t grid = (k + 127) / 128;
+  const int64_t grid = (k + 3) / 4;  // four warps (rays) per 128-thread CTA
   trace_ff_kernel<<<(unsigned)grid, 128, 0, s>>>(f, or0, or1, sp0, sp1, ij, k, y, alpha);
   return cudaGetLastError();
 }
