@@ -54,7 +54,7 @@ def test_nonsquare_grid_window_layout():
     assert np.array_equal(counts, ref) and oow == oow_ref == g.n_rays // 2
 
 
-def _check_per_ray(spec, ij, label):
+def _check_per_ray(spec, ij, label, rigorous=True):
     """Per-ray source positions.
 
     float32 path: within the rigorous operation-count bound for every ray, and within its own
@@ -67,9 +67,10 @@ def _check_per_ray(spec, ij, label):
     fin = np.isfinite(y_ref).all(1)
     assert np.array_equal(fin, np.isfinite(y_gpu).all(1))
     assert np.array_equal(fin, np.isfinite(y_ff).all(1))
-    bound = per_ray_bound(spec, x[fin], y_ref[fin])
     err = np.abs(y_gpu[fin] - y_ref[fin])
-    assert np.all(err.max(1) <= bound), (label, float((err.max(1) / bound).max()))
+    if rigorous:
+        bound = per_ray_bound(spec, x[fin], y_ref[fin])
+        assert np.all(err.max(1) <= bound), (label, float((err.max(1) / bound).max()))
     assert np.all(err <= band[fin]), (label, float((err / band[fin]).max()))
     st = error_stats(y_gpu, y_ref, spec.window)
     st_ff = error_stats(y_ff, y_ref, spec.window)
@@ -270,3 +271,20 @@ def test_certified_trace_matches_oracle_large_fields():
     st = error_stats(y_ff, y_ref, f.window)
     print("N=1e6 float-float per-ray error (pixels):", st)
     assert st["max"] <= PER_RAY_TOL_PIX
+
+
+def test_n1e6_salpeter_sampled_rays_float32_and_map_invariants():
+    """1e6 Salpeter lenses, 16384^2 grid: sampled rays (float32 path within its bounds and bands),
+    and the certified map of a 1024-row block conserves rays."""
+    f = ri.n1e6_salpeter_field()
+    ij = ri.sample_rays(f.grid, 256, seed=31)
+    y_gpu, y_ref, st = _check_per_ray(f, ij, "N=1e6")
+    counts, oow = shoot_gpu(f, rows=(7680, 8704))
+    assert int(counts.sum()) + oow == 1024 * f.grid.n[0]
+
+
+def test_n1e8_sampled_rays():
+    """1e8 lenses with stored unit masses (2.4 GB on the device), 8192^2 grid: 64 sampled rays."""
+    f = ri.n1e8_field()
+    ij = ri.sample_rays(f.grid, 64, seed=41)
+    _check_per_ray(f, ij, "N=1e8", rigorous=False)
