@@ -37,7 +37,7 @@
  *     distances serves both lenses (Montgomery's simultaneous inversion).
  *     Per ray, partial sums over consecutive groups of 32 lenses (in lens index
  *     order) are folded into a two-float (hi, lo) accumulator with an
- *     error-free TwoSum.  The deflection alpha = hi + lo, Eq. 6 and the pixel
+ *     error-free TwoSum; (hi, lo) is renormalised after every 256 lenses.  The deflection alpha = hi + lo, Eq. 6 and the pixel
  *     index are then evaluated in double precision.
  *   - The per-ray arithmetic does not depend on launch configuration, so
  *     counts are bitwise reproducible and equal between rs_shoot,
@@ -148,14 +148,15 @@ int rs_trace_certified(rs_field_t f, const rs_ray_grid* g, const int64_t* d_ray_
                        double* d_y, double* d_alpha, void* stream);
 
 /*
- * Certified binning (on by default).  The float32 shoot attaches to every ray an error
- * estimate sigma = 10 u sqrt(32 sum_g (P1_g^2 + P2_g^2)) (u = 2^-24, P_g the float32 partial
- * sums of its 32-lens groups).  A ray whose source position lies within that band of a pixel
- * or window edge is not binned by the float32 result but re-evaluated with
- * rs_trace_certified's arithmetic and binned from that; the maps then agree with a float64
- * evaluation except for rays within ~1e-12 of an edge.  rs_shoot allocates the list of such
- * rays stream-ordered (cudaMallocAsync, capacity max(4096, rays/32), at most 2^24 entries);
- * rays beyond the capacity keep their float32 decision.  Batches own their list.
+ * Certified binning (on by default).  The float32 shoot attaches to every ray an error band:
+ * 10 u sqrt(32 sum_g (P1_g^2 + P2_g^2)) (u = 2^-24, P_g the float32 partial sums of its 32-lens
+ * groups: the random rounding) plus 2 u |alpha| per axis (a systematic bias of the approximate
+ * reciprocal).  A ray whose source position lies within that band of a pixel or window edge is
+ * not binned by the float32 result but re-evaluated with rs_trace_certified's arithmetic and
+ * binned from that; the maps then agree with a float64 evaluation except for rays within ~1e-12
+ * of an edge.  rs_shoot allocates the list of such rays stream-ordered (cudaMallocAsync,
+ * capacity max(4096, rays/32), at most 2^24 entries); rays beyond the capacity keep their
+ * float32 decision.  Batches own their list.
  * rs_set_certified_binning(0) turns it off for calls (and batches planned) afterwards.
  */
 int rs_set_certified_binning(int enabled);

@@ -15,17 +15,27 @@ __global__ void __launch_bounds__(WARPS * 32)
     batch_kernel(const ShootDesc* __restrict__ descs, const int2* __restrict__ items, int n_items, int* counter) {
   __shared__ LensSmem<TILE, WARPS> sm;
   __shared__ int s_item;
+  // the current item's field descriptor, staged in shared memory once per item so that the tile
+  // code reads it as cheaply as the plain kernel reads its kernel-parameter descriptor
+  __shared__ __align__(16) ShootDesc s_desc;
+  static_assert(sizeof(ShootDesc) % 4 == 0, "descriptor copied as 32-bit words");
   PipeState ps;
   pipe_init(sm.bar, ps);
+  int cur_field = -1;
   for (;;) {
     if (threadIdx.x == 0) s_item = atomicAdd(counter, 1);
     __syncthreads();
     const int it = s_item;
-    __syncthreads();
     if (it >= n_items) break;
     const int2 w = items[it];
-    const ShootDesc& d = descs[w.x];
-    const bool ok = shoot_tile<WARPS, RPT, TILE, MASS>(d, (int64_t)w.y, sm, ps);
+    if (w.x != cur_field) {  // CTA-uniform
+      const uint32_t* src = reinterpret_cast<const uint32_t*>(descs + w.x);
+      uint32_t* dst = reinterpret_cast<uint32_t*>(&s_desc);
+      for (int k = threadIdx.x; k < (int)(sizeof(ShootDesc) / 4); k += WARPS * 32) dst[k] = src[k];
+      cur_field = w.x;
+    }
+    __syncthreads();  // s_desc ready; every thread has read s_item
+    const bool ok = shoot_tile<WARPS, RPT, TILE, MASS>(s_desc, (int64_t)w.y, sm, ps);
     if (!ok) break;
   }
 }

@@ -37,6 +37,7 @@
 namespace rsdev {
 
 constexpr int kGroup = 32;                 // lenses per float32 partial sum (fixed: part of the arithmetic)
+constexpr int kRenorm = 256;               // (hi, lo) renormalised after every 256 lenses (fixed: arithmetic)
 constexpr int kLensPad = 1024;             // device lens arrays are padded to a multiple of this
 constexpr uint64_t kWaitLimitNs = 1000000000ull;  // bounded mbarrier wait: 1 s
 constexpr unsigned kStatusTimeout = 5u;    // == RS_ETIMEOUT
@@ -82,6 +83,15 @@ __device__ __forceinline__ float rcp_approx(float x) {
   float r;
   asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
   return r;
+}
+
+// (hi, lo) <- Fast2Sum(hi, lo): keeps |lo| <= ulp(hi)/2 so that the float32 sum of TwoSum residuals in
+// lo does not itself lose accuracy over millions of groups (|hi| >= |lo| holds: lo is a sum of at most
+// eight residuals, each <= ulp(hi)/2).
+__device__ __forceinline__ void renormalise(uint64_t& hi, uint64_t& lo) {
+  const uint64_t s = f2_add_x(hi, lo);
+  lo = f2_sub_x(lo, f2_sub_x(s, hi));
+  hi = s;
 }
 
 // Error-free transformation of hi + p into (s, e), s = fl(hi + p), s + e = hi + p exactly
@@ -375,6 +385,7 @@ __device__ __forceinline__ bool deflect(const FieldDev& f, const float (&x1)[RPT
                                         LensSmem<TILE, ROWS>& sm, PipeState& ps) {
   static_assert(RPT % 2 == 0, "rays per thread must be even (packed pairs)");
   static_assert(TILE % kGroup == 0 && kGroup % 8 == 0, "lens tile must hold whole lens groups");
+  static_assert(kRenorm % kGroup == 0, "renormalisation falls on group boundaries");
   constexpr int NP = RPT / 2;
   uint64_t X1[NP], X2[NP], H1[NP], L1[NP], H2[NP], L2[NP], SS[NP];
 #pragma unroll
@@ -426,6 +437,13 @@ __device__ __forceinline__ bool deflect(const FieldDev& f, const float (&x1)[RPT
         twosum_accumulate(H2[q], L2[q], P2[q]);
         SS[q] = f2_fma(P1[q], P1[q], SS[q]);
         SS[q] = f2_fma(P2[q], P2[q], SS[q]);
+      }
+      if ((t * TILE + g + kGroup) % kRenorm == 0) {  // CTA-uniform
+#pragma unroll
+        for (int q = 0; q < NP; ++q) {
+          renormalise(H1[q], L1[q]);
+          renormalise(H2[q], L2[q]);
+        }
       }
     }
     if (g < cnt) {  // last, partial group of the field: same pattern by pair index, odd lens direct
@@ -493,10 +511,13 @@ __device__ __forceinline__ bool deflect(const FieldDev& f, const float (&x1)[RPT
   return true;
 }
 
-// Half-width of the band around y within which the float32 path cannot decide the pixel:
-// the safety-scaled sigma plus the float64 epilogue and (hi, lo) representation error.
+// Half-width of the band around y within which the float32 path cannot decide the pixel: the
+// safety-scaled sigma (random rounding), a coherent term for a systematic bias of the approximate
+// reciprocal (every term of alpha scaled by the same 1 + b, |b| <= kRcpBias u, so the error is
+// b alpha), and the float64 epilogue and (hi, lo) representation error.
+constexpr double kRcpBias = 2.0 * 5.9604644775390625e-08;  // 2 u: the documented 1-ulp bound of rcp.approx
 __device__ __forceinline__ double band_halfwidth(float sig, double y, double a) {
-  return (double)sig + 4e-15 * (fabs(y) + fabs(a));
+  return (double)sig + kRcpBias * fabs(a) + 4e-15 * (fabs(y) + fabs(a));
 }
 
 // ----------------------------------------------------------------------------------------------
