@@ -149,9 +149,10 @@ int rs_trace_certified(rs_field_t f, const rs_ray_grid* g, const int64_t* d_ray_
 
 /*
  * Certified binning (on by default).  The float32 shoot attaches to every ray an error band:
- * 10 u sqrt(32 sum_g (P1_g^2 + P2_g^2)) (u = 2^-24, P_g the float32 partial sums of its 32-lens
- * groups: the random rounding) plus 2 u |alpha| per axis (a systematic bias of the approximate
- * reciprocal).  A ray whose source position lies within that band of a pixel or window edge is
+ * 10 u sqrt(32 sum_g (P1_g^2 + P2_g^2)) + 2 u sum_g (|P1_g| + |P2_g|) (u = 2^-24, P_g the float32
+ * partial sums of its 32-lens groups): the random rounding, plus coherent errors (the far field
+ * sees the ray's coordinate only to the precision of the lens-ray difference; a bias of the
+ * approximate reciprocal).  A ray whose source position lies within that band of a pixel or window edge is
  * not binned by the float32 result but re-evaluated with rs_trace_certified's arithmetic and
  * binned from that; the maps then agree with a float64 evaluation except for rays within ~1e-12
  * of an edge.  rs_shoot allocates the list of such rays stream-ordered (cudaMallocAsync,

@@ -79,6 +79,8 @@ __device__ __forceinline__ uint64_t f2_pack(float lo, float hi) {
 __device__ __forceinline__ void f2_unpack(uint64_t v, float& lo, float& hi) {
   asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
 }
+// |a| lane-wise (clears both sign bits).
+__device__ __forceinline__ uint64_t f2_abs(uint64_t a) { return a & 0x7fffffff7fffffffull; }
 __device__ __forceinline__ float rcp_approx(float x) {
   float r;
   asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
@@ -203,6 +205,12 @@ constexpr float kSigmaSafety = 10.0f;
 // sigma = u sqrt(32 sum_g (P1_g^2 + P2_g^2)): the rounding of a 32-lens float32 group partial is a
 // random walk of at most 32 steps of ~u |P_g|; u = 2^-24.
 constexpr float kSigmaScale = 5.9604645e-08f * 5.656854249f * kSigmaSafety;
+// Coherent errors: the rounding of d1 = x1 - x1_lens keeps the ray's x1 only to ulp(d1) for lenses
+// much farther away than |x1| -- the same shift for every lens of a binade, i.e. a systematic
+// displacement of the ray seen by the far field -- and a bias of the approximate reciprocal
+// scales every term alike.  Both are bounded by a few u times sum_g (|P1_g| + |P2_g|), which
+// upper-bounds |alpha| and tracks sum_i |t_i| for a far field of many lenses.
+constexpr float kSystematicScale = 2.0f * 5.9604645e-08f;
 
 template <int TILE, int ROWS = 1>
 struct __align__(16) LensSmem {
@@ -387,12 +395,12 @@ __device__ __forceinline__ bool deflect(const FieldDev& f, const float (&x1)[RPT
   static_assert(TILE % kGroup == 0 && kGroup % 8 == 0, "lens tile must hold whole lens groups");
   static_assert(kRenorm % kGroup == 0, "renormalisation falls on group boundaries");
   constexpr int NP = RPT / 2;
-  uint64_t X1[NP], X2[NP], H1[NP], L1[NP], H2[NP], L2[NP], SS[NP];
+  uint64_t X1[NP], X2[NP], H1[NP], L1[NP], H2[NP], L2[NP], SS[NP], AB[NP];
 #pragma unroll
   for (int q = 0; q < NP; ++q) {
     X1[q] = f2_pack(x1[2 * q], x1[2 * q + 1]);
     X2[q] = f2_pack(x2[2 * q], x2[2 * q + 1]);
-    H1[q] = L1[q] = H2[q] = L2[q] = SS[q] = 0ull;
+    H1[q] = L1[q] = H2[q] = L2[q] = SS[q] = AB[q] = 0ull;
   }
   const int n = f.n_lens;
   const int ntiles = (n + TILE - 1) / TILE;
@@ -437,6 +445,7 @@ __device__ __forceinline__ bool deflect(const FieldDev& f, const float (&x1)[RPT
         twosum_accumulate(H2[q], L2[q], P2[q]);
         SS[q] = f2_fma(P1[q], P1[q], SS[q]);
         SS[q] = f2_fma(P2[q], P2[q], SS[q]);
+        AB[q] = f2_add_x(AB[q], f2_add_x(f2_abs(P1[q]), f2_abs(P2[q])));
       }
       if ((t * TILE + g + kGroup) % kRenorm == 0) {  // CTA-uniform
 #pragma unroll
@@ -480,6 +489,7 @@ __device__ __forceinline__ bool deflect(const FieldDev& f, const float (&x1)[RPT
         twosum_accumulate(H2[q], L2[q], P2[q]);
         SS[q] = f2_fma(P1[q], P1[q], SS[q]);
         SS[q] = f2_fma(P2[q], P2[q], SS[q]);
+        AB[q] = f2_add_x(AB[q], f2_add_x(f2_abs(P1[q]), f2_abs(P2[q])));
       }
     }
     __syncthreads();  // every thread is done with buffer b and the row table
@@ -505,19 +515,18 @@ __device__ __forceinline__ bool deflect(const FieldDev& f, const float (&x1)[RPT
     a2[2 * q] = (double)h + (double)l;
     a2[2 * q + 1] = (double)hB + (double)lB;
     f2_unpack(SS[q], h, hB);
-    sig[2 * q] = kSigmaScale * sqrtf(h);
-    sig[2 * q + 1] = kSigmaScale * sqrtf(hB);
+    f2_unpack(AB[q], l, lB);
+    sig[2 * q] = kSigmaScale * sqrtf(h) + kSystematicScale * l;
+    sig[2 * q + 1] = kSigmaScale * sqrtf(hB) + kSystematicScale * lB;
   }
   return true;
 }
 
-// Half-width of the band around y within which the float32 path cannot decide the pixel: the
-// safety-scaled sigma (random rounding), a coherent term for a systematic bias of the approximate
-// reciprocal (every term of alpha scaled by the same 1 + b, |b| <= kRcpBias u, so the error is
-// b alpha), and the float64 epilogue and (hi, lo) representation error.
-constexpr double kRcpBias = 2.0 * 5.9604644775390625e-08;  // 2 u: the documented 1-ulp bound of rcp.approx
+// Half-width of the band around y within which the float32 path cannot decide the pixel: sig (the
+// safety-scaled random-rounding estimate plus the coherent term) and the float64 epilogue and
+// (hi, lo) representation error.
 __device__ __forceinline__ double band_halfwidth(float sig, double y, double a) {
-  return (double)sig + kRcpBias * fabs(a) + 4e-15 * (fabs(y) + fabs(a));
+  return (double)sig + 4e-15 * (fabs(y) + fabs(a));
 }
 
 // ----------------------------------------------------------------------------------------------
