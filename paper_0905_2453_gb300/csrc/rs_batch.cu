@@ -11,7 +11,7 @@ namespace {
 using namespace rsdev;
 
 template <int WARPS, int RPT, int TILE, bool MASS>
-__global__ void __launch_bounds__(WARPS * 32)
+__global__ void __launch_bounds__(WARPS * 32, 2)
     batch_kernel(const ShootDesc* __restrict__ descs, const int2* __restrict__ items, int n_items, int* counter) {
   __shared__ LensSmem<TILE, WARPS> sm;
   __shared__ int s_item;
