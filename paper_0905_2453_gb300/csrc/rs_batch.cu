@@ -10,8 +10,10 @@ namespace {
 
 using namespace rsdev;
 
+// Two CTAs per SM as the occupancy floor for small CTAs (more registers, as for the plain kernel);
+// eight-warp CTAs keep the default allocation (a two-CTA floor would force spills there).
 template <int WARPS, int RPT, int TILE, bool MASS>
-__global__ void __launch_bounds__(WARPS * 32, 2)
+__global__ void __launch_bounds__(WARPS * 32, WARPS <= 4 ? 2 : 1)
     batch_kernel(const ShootDesc* __restrict__ descs, const int2* __restrict__ items, int n_items, int* counter) {
   __shared__ LensSmem<TILE, WARPS> sm;
   __shared__ int s_item;

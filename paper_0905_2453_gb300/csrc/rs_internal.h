@@ -20,7 +20,7 @@ struct KernelCfg {
 };
 constexpr int kNumCfg = 6;
 constexpr KernelCfg kCfgs[kNumCfg] = {{64, 8}, {128, 4}, {128, 8}, {256, 4}, {256, 8}, {256, 6}};
-constexpr int kDefaultCfg = 3;
+constexpr int kDefaultCfg = 2;
 
 inline int find_cfg(int block, int rpt) {
   for (int i = 0; i < kNumCfg; ++i)

@@ -7,9 +7,9 @@ using namespace rsdev;
 
 // Two CTAs per SM as the occupancy floor: lets the compiler keep a small CTA's eight rays per thread,
 // their two-float accumulators and a deeper instruction window in registers (measured faster than the
-// default allocation, which spills).
+// default allocation, which spills); eight-warp CTAs keep the default allocation.
 template <int WARPS, int RPT, int TILE, bool MASS>
-__global__ void __launch_bounds__(WARPS * 32, 2) shoot_kernel(const ShootDesc d) {
+__global__ void __launch_bounds__(WARPS * 32, WARPS <= 4 ? 2 : 1) shoot_kernel(const ShootDesc d) {
   __shared__ LensSmem<TILE, WARPS> sm;
   PipeState ps;
   pipe_init(sm.bar, ps);
