@@ -203,6 +203,9 @@ int fill_desc(const rs_field* f, const rs_ray_grid* g, int64_t row_begin, int64_
   d->lo1 = w->lo[1];
   d->sc0 = (double)w->npix[0] / (w->hi[0] - w->lo[0]);
   d->sc1 = (double)w->npix[1] / (w->hi[1] - w->lo[1]);
+  // rounded up so that the float band in pixel units is never narrower than in float64
+  d->scf0 = std::nextafter((float)d->sc0, INFINITY);
+  d->scf1 = std::nextafter((float)d->sc1, INFINITY);
   d->np0 = w->npix[0];
   d->np1 = w->npix[1];
   d->counts = d_counts;
@@ -342,6 +345,7 @@ int rs_create_field(const float* lens_xy, const float* masses, int64_t n_lens, d
   f->dev.has_mass = has_mass ? 1 : 0;
   f->dev.lam1 = (1.0 - kappa_c) - gamma;
   f->dev.lam2 = (1.0 - kappa_c) + gamma;
+  f->dev.lamabs = std::nextafter((float)std::max(std::fabs(f->dev.lam1), std::fabs(f->dev.lam2)), INFINITY);
   f->dev.status = f->status;
   *out = f;
   return RS_OK;

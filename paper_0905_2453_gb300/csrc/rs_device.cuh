@@ -179,6 +179,7 @@ struct FieldDev {
   int32_t n_lens;
   int32_t has_mass;
   double lam1, lam2;    // (1 - kappa_c) - gamma, (1 - kappa_c) + gamma
+  float lamabs;         // max(|lam1|, |lam2|), for the float64-epilogue term of the error band
   unsigned int* status; // device status word (RS_OK / RS_ETIMEOUT)
 };
 
@@ -189,6 +190,7 @@ struct ShootDesc {
   int64_t j_begin;            // first grid row of this call
   int64_t n_rows;             // grid rows in this call (rows x n0 < 2^32 rays)
   double lo0, lo1, sc0, sc1;  // window lower corner and npix / (hi - lo)
+  float scf0, scf1;           // the scales as float (error-band arithmetic only)
   int32_t np0, np1;           // pixels per axis
   uint32_t* counts;           // [np1][np0]
   unsigned long long* oow;    // out-of-window counter or nullptr
@@ -514,19 +516,23 @@ __device__ __forceinline__ bool deflect(const FieldDev& f, const float (&x1)[RPT
     f2_unpack(L2[q], l, lB);
     a2[2 * q] = (double)h + (double)l;
     a2[2 * q + 1] = (double)hB + (double)lB;
+    // |alpha| enters through the float64 epilogue rounding (~1e-16 |alpha|): 8e-15 (|hi1| + |hi2|)
+    float h1a, h1b, h2a, h2b;
+    f2_unpack(H1[q], h1a, h1b);
+    f2_unpack(H2[q], h2a, h2b);
     f2_unpack(SS[q], h, hB);
     f2_unpack(AB[q], l, lB);
-    sig[2 * q] = kSigmaScale * sqrtf(h) + kSystematicScale * l;
-    sig[2 * q + 1] = kSigmaScale * sqrtf(hB) + kSystematicScale * lB;
+    sig[2 * q] = kSigmaScale * sqrtf(h) + kSystematicScale * l + 8e-15f * (fabsf(h1a) + fabsf(h2a));
+    sig[2 * q + 1] = kSigmaScale * sqrtf(hB) + kSystematicScale * lB + 8e-15f * (fabsf(h1b) + fabsf(h2b));
   }
   return true;
 }
 
 // Half-width of the band around y within which the float32 path cannot decide the pixel: sig (the
-// safety-scaled random-rounding estimate plus the coherent term) and the float64 epilogue and
-// (hi, lo) representation error.
-__device__ __forceinline__ double band_halfwidth(float sig, double y, double a) {
-  return (double)sig + 4e-15 * (fabs(y) + fabs(a));
+// safety-scaled random-rounding estimate, the coherent term and the alpha part of the float64
+// epilogue rounding) plus the lam x part of that rounding.
+__device__ __forceinline__ float band_halfwidth(float sig, float lamabs, float x1, float x2) {
+  return sig + 4e-15f * lamabs * (fabsf(x1) + fabsf(x2));
 }
 
 // ----------------------------------------------------------------------------------------------
@@ -573,16 +579,26 @@ __device__ __forceinline__ bool shoot_tile(const ShootDesc& d, int64_t tile, Len
     const double y2 = __dsub_rn(__dmul_rn(d.f.lam2, (double)x2[k]), a2[k]);
     const double u1 = __dmul_rn(__dsub_rn(y1, d.lo0), d.sc0);
     const double u2 = __dmul_rn(__dsub_rn(y2, d.lo1), d.sc1);
-    const bool inwin = (u1 >= 0.0) && (u1 < (double)d.np0) && (u2 >= 0.0) && (u2 < (double)d.np1);
+    // pixel index in float64 (as the definition); |u| >= 2^31 or NaN is out of any window
+    const bool fin = (fabs(u1) < 2147483648.0) && (fabs(u2) < 2147483648.0);
+    const double fl1 = floor(u1), fl2 = floor(u2);
+    const int p1 = fin ? (int)fl1 : -1;
+    const int p2 = fin ? (int)fl2 : -1;
+    const bool inwin = fin && (p1 >= 0) && (p1 < d.np0) && (p2 >= 0) && (p2 < d.np1);
     bool bin_now = valid[k];
     if (d.rc_list != nullptr) {
-      // certain: the whole band [u - du, u + du] on both axes is out of the window, or inside one pixel
-      const double du1 = band_halfwidth(sig[k], y1, a1[k]) * d.sc0;
-      const double du2 = band_halfwidth(sig[k], y2, a2[k]) * d.sc1;
-      const bool out_sure = !((u1 >= -du1) && (u1 < d.np0 + du1) && (u2 >= -du2) && (u2 < d.np1 + du2));
-      const double f1 = u1 - floor(u1), f2 = u2 - floor(u2);
-      const bool in_sure = (u1 >= du1) && (u1 < d.np0 - du1) && (u2 >= du2) && (u2 < d.np1 - du2) &&
-                           (f1 >= du1) && (f1 <= 1.0 - du1) && (f2 >= du2) && (f2 <= 1.0 - du2);
+      // Certain: the band [u - du, u + du] lies inside one pixel of the window, or outside the window
+      // on some axis.  Tested in float with margins for the float rounding of u (~|u| 2^-23) and of
+      // the exact fractional part f = u - floor(u).
+      const float band = band_halfwidth(sig[k], d.f.lamabs, x1[k], x2[k]);
+      const float du1 = band * d.scf0, du2 = band * d.scf1;
+      const float f1 = (float)(u1 - fl1), f2 = (float)(u2 - fl2);
+      const float uf1 = (float)p1 + f1, uf2 = (float)p2 + f2;
+      const float mo1 = du1 + 1.2e-7f * fabsf(uf1) + 1e-7f, mo2 = du2 + 1.2e-7f * fabsf(uf2) + 1e-7f;
+      const float mf1 = du1 + 1e-7f, mf2 = du2 + 1e-7f;
+      const bool out_sure = !fin || (uf1 + mo1 < 0.f) || (uf1 - mo1 >= (float)d.np0) || (uf2 + mo2 < 0.f) ||
+                            (uf2 - mo2 >= (float)d.np1);
+      const bool in_sure = inwin && (f1 >= mf1) && (f1 <= 1.f - mf1) && (f2 >= mf2) && (f2 <= 1.f - mf2);
       const bool need = valid[k] && !out_sure && !in_sure;
       const unsigned mask = __ballot_sync(0xffffffffu, need);
       if (mask != 0u) {
@@ -601,11 +617,7 @@ __device__ __forceinline__ bool shoot_tile(const ShootDesc& d, int64_t tile, Len
         }
       }
     }
-    if (bin_now && inwin) {
-      const int p1 = (int)floor(u1);
-      const int p2 = (int)floor(u2);
-      atomicAdd(d.counts + (size_t)p2 * (size_t)d.np0 + (size_t)p1, 1u);
-    }
+    if (bin_now && inwin) atomicAdd(d.counts + (size_t)p2 * (size_t)d.np0 + (size_t)p1, 1u);
     const unsigned miss = __ballot_sync(0xffffffffu, bin_now && !inwin);
     oow_lane += __popc(miss);
   }

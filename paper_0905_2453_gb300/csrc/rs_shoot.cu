@@ -50,8 +50,9 @@ __global__ void __launch_bounds__(BLOCK)
       alpha[2 * r + 1] = a2[q];
     }
     if (err != nullptr) {
-      err[2 * r] = band_halfwidth(sig[q], y1, a1[q]);
-      err[2 * r + 1] = band_halfwidth(sig[q], y2, a2[q]);
+      const double b = (double)band_halfwidth(sig[q], f.lamabs, x1[q], x2[q]);
+      err[2 * r] = b;
+      err[2 * r + 1] = b;
     }
   }
 }

@@ -40,8 +40,8 @@ def _load(path):
         return {}
 
 
-def autotune(field, grid, window, target_interactions: float = 2e10, reps: int = 3, cache_path: str = None,
-             force: bool = False, stream=None):
+def autotune(field, grid, window, min_rays: float = 8e6, max_interactions: float = 3e11, reps: int = 3,
+             cache_path: str = None, force: bool = False, stream=None):
     """Pick and set the fastest launch shape for this (field, grid); returns (block, rpt, timings_ms)."""
     cache_path = cache_path or os.environ.get("RS_TUNE_CACHE", DEFAULT_CACHE)
     n_lens, has_mass = field.info()
@@ -51,9 +51,12 @@ def autotune(field, grid, window, target_interactions: float = 2e10, reps: int =
         b, r = cache[key]["block"], cache[key]["rpt"]
         rs_set_launch_config(has_mass, b, r)
         return b, r, cache[key].get("ms", {})
+    # proxy: enough rays for several full waves of the largest CTA tile on every SM (a partial wave
+    # would favour shapes with more, smaller CTAs), capped in work
     n0, n1 = int(grid.n[0]), int(grid.n[1])
-    per_row = max(1, n0 * max(1, n_lens))
-    rows = int(min(n1, max(64, target_interactions // per_row)))
+    rows = max(64, int(min_rays // max(1, n0)))
+    rows = min(rows, max(64, int(max_interactions // max(1, n0 * max(1, n_lens)))))
+    rows = min(rows, n1)
     dev = torch.device("cuda", torch.cuda.current_device())
     counts = torch.zeros((int(window.npix[1]), int(window.npix[0])), dtype=torch.int32, device=dev)
     st = torch.cuda.current_stream(dev) if stream is None else stream
