@@ -9,12 +9,16 @@ over rays, no fused multiply-add, no fast-math); this module compiles it with
 gcc and exposes it through ctypes with numpy arrays.  What each function
 computes and which passage of the paper it follows is stated in the C file:
 Eq. 2 with the per-lens steps of Appendix A (deflection), Eq. 6 (lens map with
-kappa_c and gamma), Eq. 4 (mu = N / N_av) and Section 2.1 step 4 (binning).
+kappa_c and gamma), Eq. 4 (mu = N / N_av), Section 2.1 step 4 (binning) and
+the light curves of Section 1 (a source profile moved across the map).
 
 Parity status: every function here is pinned by ``tests/test_oracle_pins.py``
 (exact rational brute force, zero-lens and linear-map lattice counts, the
 single point-lens magnification law, mirror symmetry, conservation,
-superposition and the 2-D Gauss law of a uniform disc).
+superposition and the 2-D Gauss law of a uniform disc); ``light_curve`` by
+``tests/test_oracle_lightcurve.py`` (constant and linear maps, Gauss circle
+lattice counts of the disc profile, the magnitude scale, and a point lens seen
+through a Gaussian source against Gauss-Hermite quadrature of the analytic law).
 """
 from __future__ import annotations
 
@@ -77,6 +81,8 @@ def load_library(path: str):
     lib.oracle_num_threads.restype = ctypes.c_int
     lib.oracle_set_num_threads.argtypes = [ctypes.c_int]
     lib.oracle_set_num_threads.restype = None
+    lib.oracle_light_curve.argtypes = [vp, vp, vp, vp, ctypes.c_int, ctypes.c_double, vp, vp, ctypes.c_int64, vp, vp]
+    lib.oracle_light_curve.restype = None
     return lib
 
 
@@ -183,6 +189,27 @@ def magnification(counts, spacing, lo, hi, npix):
     s, l, h = _d2(spacing), _d2(lo), _d2(hi)
     lib.oracle_magnification(_ptr(c), _ptr(s), _ptr(l), _ptr(h), _ptr(npx), _ptr(mu))
     return mu
+
+
+PROFILE_GAUSSIAN = 0
+PROFILE_DISC = 1
+
+
+def light_curve(mu, lo, hi, profile, s, y0, step, n):
+    """Light curve of a magnification map (float64 [npix1, npix0]) along y_k = y0 + k step.
+
+    profile: PROFILE_GAUSSIAN (s = standard deviation, cut at 6 s) or PROFILE_DISC (s = radius).
+    Returns (mu_k, dm_k) as float64 arrays of length n.
+    """
+    lib = _load()
+    m = np.ascontiguousarray(np.asarray(mu, dtype=np.float64))
+    npx = np.ascontiguousarray(np.array([m.shape[1], m.shape[0]], dtype=np.int32))
+    out = np.empty(int(n), np.float64)
+    mag = np.empty(int(n), np.float64)
+    l, h, a, b = _d2(lo), _d2(hi), _d2(y0), _d2(step)
+    lib.oracle_light_curve(_ptr(m), _ptr(npx), _ptr(l), _ptr(h), int(profile), float(s), _ptr(a), _ptr(b),
+                           int(n), _ptr(out), _ptr(mag))
+    return out, mag
 
 
 # Convenience wrappers over rs_inputs.Field objects --------------------------------
