@@ -356,6 +356,11 @@ def run_ours(args):
     if not args.no_batch and world == 1:
         batched = run_batched(rs, torch, device, stream, reps=args.batch_reps)
 
+    # ---------------- light curves over many maps (one launch)
+    light = None
+    if not args.no_light_curves and world == 1:
+        light = run_light_curves(rs, torch, device, stream)
+
     # ---------------- CPU baseline (oracle, bounded sample)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -393,6 +398,7 @@ def run_ours(args):
         "gpu_launches": (3 if rs.rs_get_certified_binning() else 2) * args.steps,
         "cpu_baseline": cpu,
         "batched": batched,
+        "light_curves": light,
         "wall_s_timed_region": wall,
     }
     print(json.dumps(line), flush=True)
@@ -447,6 +453,83 @@ def run_batched(rs, torch, device, stream, reps=3):
             "reps": reps}
 
 
+def support_pixels(wins, tracks, R):
+    """Pixels whose centres lie within R of each sample, summed over all samples (the pixels the
+    definition averages over), counted row by row in float64."""
+    total = 0
+    for t in tracks:
+        w = wins[t.map]
+        pix = [(w.hi[a] - w.lo[a]) / w.npix[a] for a in range(2)]
+        k = np.arange(t.n, dtype=np.float64)
+        t0 = (t.y0[0] + k * t.step[0] - w.lo[0]) / pix[0] - 0.5
+        t1 = (t.y0[1] + k * t.step[1] - w.lo[1]) / pix[1] - 0.5
+        rp0, rp1 = R / pix[0], R / pix[1]
+        for dj in range(-int(rp1) - 1, int(rp1) + 2):
+            j = np.floor(t1) + dj
+            dy = j - t1
+            h2 = rp0 * rp0 * (1.0 - (dy / rp1) ** 2)
+            ok = (h2 >= 0) & (j >= 0) & (j < w.npix[1])
+            h = np.sqrt(np.where(ok, h2, 0.0))
+            lo = np.maximum(np.ceil(t0 - h), 0)
+            hi = np.minimum(np.floor(t0 + h), w.npix[0] - 1)
+            total += int(np.where(ok, np.maximum(hi - lo + 1, 0), 0).sum())
+    return total
+
+
+def run_light_curves(rs, torch, device, stream, reps=20, cpu_samples=4096):
+    """Light curves of 1024 tracks x 2048 samples over 64 synthetic caustic maps in one launch."""
+    maps, wins, tracks, s = ri.light_curve_workload()
+    tmaps = [torch.from_numpy(m).to(device) for m in maps]
+    rtr = [rs.Track(t.map, t.y0, t.step, t.n) for t in tracks]
+    total = sum(t.n for t in tracks)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=device)
+    support = support_pixels(wins, tracks, 6.0 * s)
+    plan = rs.LightCurvePlan(tmaps, wins, rtr, rs.RS_PROFILE_GAUSSIAN, s)
+    for _ in range(3):
+        plan.launch(stream)
+    torch.cuda.synchronize(device)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+    for k in range(reps):
+        flush.fill_(k)
+        ev[k][0].record(stream)
+        plan.launch(stream)
+        ev[k][1].record(stream)
+    torch.cuda.synchronize(device)
+    t = statistics.mean(a.elapsed_time(b) for a, b in ev) / 1e3
+    # one-shot call (validation, table upload, launch, release) from the host
+    mu = torch.empty(total, dtype=torch.float64, device=device)
+    dm = torch.empty_like(mu)
+    rs.rs_light_curves(tmaps, wins, rs.RS_PROFILE_GAUSSIAN, s, rtr, mu, dm, stream)
+    torch.cuda.synchronize(device)
+    same = bool(torch.equal(mu.view(torch.int64), plan.mu.view(torch.int64)))
+    t0 = time.perf_counter()
+    for _ in range(5):
+        rs.rs_light_curves(tmaps, wins, rs.RS_PROFILE_GAUSSIAN, s, rtr, mu, dm, stream)
+    torch.cuda.synchronize(device)
+    t_one = (time.perf_counter() - t0) / 5
+    plan.close()
+    # the oracle on a bounded sample: the first cpu_samples samples, in track order
+    import oracle
+    n_cpu, t_cpu, k = 0, 0.0, 0
+    while n_cpu < cpu_samples and k < len(tracks):
+        tr = tracks[k]
+        w = wins[tr.map]
+        m64 = maps[tr.map].astype(np.float64)
+        n = min(tr.n, cpu_samples - n_cpu)
+        t0 = time.perf_counter()
+        oracle.light_curve(m64, w.lo, w.hi, oracle.PROFILE_GAUSSIAN, s, tr.y0, tr.step, n)
+        t_cpu += time.perf_counter() - t0
+        n_cpu += n
+        k += 1
+    return {"workload": "64 caustic maps 512^2-1024^2, 1024 tracks x 2048 samples, Gaussian source 1-2 px",
+            "samples_per_s": total / t, "support_pixels_per_s": support / t, "kernel_ms": t * 1e3,
+            "support_pixels_per_launch": support, "samples_per_launch": total, "reps": reps,
+            "one_shot_ms": t_one * 1e3, "one_shot_equal_plan": same,
+            "l2": "flushed between launches",
+            "oracle": {"samples_per_s": n_cpu / t_cpu, "sample": f"{n_cpu} samples, full-map visit per sample",
+                       "cores": oracle.num_threads()}}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -456,6 +539,7 @@ def main():
     ap.add_argument("--workload", default="n1e4")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-light-curves", action="store_true")
     ap.add_argument("--batch-reps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)

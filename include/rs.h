@@ -219,6 +219,75 @@ int rs_get_launch_config(int has_masses, int* block, int* rays_per_thread);
 int rs_launch_configs(int* pairs, int cap, int* count);
 
 /*
+ * Light curves (Section 1: a source of finite size moves across the magnification map; the
+ * magnification it sees along its path, as a magnitude change, is the light curve that is
+ * compared with observations).  The paper states no formula; this library computes, for each
+ * sample position y of a straight track, the profile-weighted mean of the map
+ *     mu(y) = sum_p w(|c_p - y|) mu_p / sum_p w(|c_p - y|),   dm(y) = -2.5 log10 mu(y),
+ * over the pixels p of the map with centres c_p = (lo_k + (i_k + 0.5) pix_k)_k, pix_k = (hi_k - lo_k) / npix_k:
+ *   RS_PROFILE_GAUSSIAN: w = exp(-d^2 / (2 s^2)) for d^2 <= (6 s)^2, else 0 (s = standard deviation);
+ *   RS_PROFILE_DISC:     w = 1 for d^2 <= s^2, else 0 (s = radius).
+ * A sample whose profile covers no pixel gives NaN; a zero mean gives dm = +inf.
+ *
+ * rs_track: samples y_k = y0 + k * step, k = 0 .. n-1, over map number `map` of the call.
+ */
+#define RS_PROFILE_GAUSSIAN 0
+#define RS_PROFILE_DISC 1
+
+typedef struct {
+  int32_t map;     /* index into the call's maps, 0 <= map < n_maps                       */
+  int32_t reserved;
+  double y0[2];    /* first sample (finite, |y| <= 1e9)                                    */
+  double step[2];  /* sample spacing (finite; the last sample must also satisfy |y| <= 1e9) */
+  int64_t n;       /* number of samples, >= 0                                              */
+} rs_track;
+
+/*
+ * rs_light_curves -- light curves of many tracks over many maps in one launch (the batched maps
+ * of rs_batch_create feed it directly).
+ *   n_maps   : >= 1 when any track has samples.
+ *   d_mu     : host array of n_maps device pointers, map m = float[npix1][npix0] (row-major
+ *              [p2][p1], e.g. the output of rs_magnification).  Read only.
+ *   windows  : host array of n_maps source-plane windows, one per map.  Per axis npix <= 2^24
+ *              and max(|lo|, |hi|) / pix <= 2^30.
+ *   profile, s : RS_PROFILE_GAUSSIAN or RS_PROFILE_DISC and its size (finite, > 0; the profile's
+ *              support may span at most 2^22 pixels from its centre along either axis).
+ *   tracks   : host array of n_tracks tracks.  Track t's samples are written at consecutive
+ *              positions starting at sum_{u < t} tracks[u].n.
+ *   d_mu_out : double[sum n] device, receives mu(y_k).
+ *   d_dm_out : double[sum n] device or NULL, receives dm(y_k).
+ * Numerics: a pixel belongs to the profile exactly when the float64 test
+ * ((lo + (i + 0.5) pix) - y)^2 summed over both axes (no fused multiply-add) <= the cut says
+ * so; the kernel decides from a float32 estimate and repeats the float64 test for pixels within
+ * a guard band of the cut, so the set of pixels is that of a float64 evaluation.  Weights are
+ * float32 (expf of the float32 exponent), sums are compensated float32 pairs; mu(y) carries a
+ * relative error of a few 1e-7 (rows of the support are summed in float32, at most 2 R / pix + 3
+ * terms each, then folded into compensated pairs).  The descriptor table is allocated stream-ordered
+ * (cudaMallocAsync) and freed on the stream.
+ * Errors: RS_EINVAL (argument), RS_EOVERFLOW (more than 2^40 samples), RS_ENOMEM, RS_ECUDA.
+ */
+int rs_light_curves(int n_maps, const float* const* d_mu, const rs_window* windows, int profile, double s,
+                    int n_tracks, const rs_track* tracks, double* d_mu_out, double* d_dm_out, void* stream);
+
+/*
+ * Light-curve plans: the same computation with the track table validated and uploaded once, for
+ * repeated launches over the same map buffers (maps refreshed in place, e.g. by a batch) and for
+ * CUDA-graph capture (a launch allocates nothing).
+ * rs_light_curve_plan_create -- arguments as rs_light_curves; the map pointers are stored and read
+ *   at every launch, so the maps must outlive the plan.  Synchronous upload; the current device.
+ * rs_light_curve_plan_samples -- total number of samples (length of the outputs).
+ * rs_light_curve_plan_launch -- enqueue the light-curve kernel on `stream`.
+ * rs_light_curve_plan_destroy -- synchronise the plan's device and release it.  NULL is a no-op.
+ */
+typedef struct rs_lc_plan* rs_lc_plan_t;
+
+int rs_light_curve_plan_create(int n_maps, const float* const* d_mu, const rs_window* windows, int profile,
+                               double s, int n_tracks, const rs_track* tracks, rs_lc_plan_t* out);
+int rs_light_curve_plan_samples(rs_lc_plan_t p, int64_t* n_samples);
+int rs_light_curve_plan_launch(rs_lc_plan_t p, double* d_mu_out, double* d_dm_out, void* stream);
+int rs_light_curve_plan_destroy(rs_lc_plan_t p);
+
+/*
  * rs_shoot_rows_noalloc -- rs_shoot_rows with certified binning, allocating nothing.
  * The paper has no counterpart: this entry point serves callers that cannot allocate device
  * memory while they run (work replayed in a CUDA graph whose capture must not contain

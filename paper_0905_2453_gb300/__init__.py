@@ -40,7 +40,9 @@ EXPORTED_SYMBOLS = (
     "rs_magnification", "rs_batch_create", "rs_batch_launch", "rs_batch_destroy", "rs_shoot_batch",
     "rs_field_status", "rs_last_error", "rs_version", "rs_set_launch_config", "rs_get_launch_config",
     "rs_launch_configs", "rs_trace_certified", "rs_set_certified_binning", "rs_get_certified_binning",
-    "rs_selftest_bounded_wait", "rs_shoot_rows_noalloc",
+    "rs_selftest_bounded_wait", "rs_shoot_rows_noalloc", "rs_light_curves",
+    "rs_light_curve_plan_create", "rs_light_curve_plan_samples", "rs_light_curve_plan_launch",
+    "rs_light_curve_plan_destroy",
 )
 
 
@@ -56,6 +58,24 @@ class _Grid(ctypes.Structure):
 
 class _Window(ctypes.Structure):
     _fields_ = [("lo", ctypes.c_double * 2), ("hi", ctypes.c_double * 2), ("npix", ctypes.c_int32 * 2)]
+
+
+class _Track(ctypes.Structure):
+    _fields_ = [("map", ctypes.c_int32), ("reserved", ctypes.c_int32), ("y0", ctypes.c_double * 2),
+                ("step", ctypes.c_double * 2), ("n", ctypes.c_int64)]
+
+
+RS_PROFILE_GAUSSIAN = 0
+RS_PROFILE_DISC = 1
+
+
+@dataclass
+class Track:
+    """Straight source track: samples y_k = y0 + k step, k = 0 .. n-1, over map number ``map``."""
+    map: int
+    y0: tuple
+    step: tuple
+    n: int
 
 
 @dataclass
@@ -109,6 +129,11 @@ def load():
         "rs_selftest_bounded_wait": ([i64, ctypes.POINTER(i32)], i32),
         "rs_shoot_rows_noalloc": ([vp, gp, i64, i64, wp, vp, vp, vp], i32),
         "rs_magnification": ([vp, gp, wp, vp, vp], i32),
+        "rs_light_curves": ([i32, vp, vp, i32, dbl, i32, vp, vp, vp, vp], i32),
+        "rs_light_curve_plan_create": ([i32, vp, vp, i32, dbl, i32, vp, ctypes.POINTER(vp)], i32),
+        "rs_light_curve_plan_samples": ([vp, ctypes.POINTER(i64)], i32),
+        "rs_light_curve_plan_launch": ([vp, vp, vp, vp], i32),
+        "rs_light_curve_plan_destroy": ([vp], i32),
         "rs_batch_create": ([i32, vp, vp, vp, vp, vp, ctypes.POINTER(vp)], i32),
         "rs_batch_launch": ([vp, vp], i32),
         "rs_batch_destroy": ([vp], i32),
@@ -312,6 +337,97 @@ def rs_magnification(counts: torch.Tensor, grid, window, mu: torch.Tensor, strea
     pm = _dptr(mu, torch.float32, "mu", npx)
     g, w = _cgrid(grid), _cwin(window)
     _check(load().rs_magnification(pc, ctypes.byref(g), ctypes.byref(w), pm, _stream(stream)), "rs_magnification")
+
+
+def _lc_arrays(maps, windows, tracks):
+    n_maps = len(maps)
+    if len(windows) != n_maps:
+        raise ValueError("maps and windows must have the same length")
+    M = (ctypes.c_void_p * max(1, n_maps))(*[_dptr(m, torch.float32, f"maps[{k}]",
+                                                     int(windows[k].npix[0]) * int(windows[k].npix[1]))
+                                               for k, m in enumerate(maps)])
+    W = (_Window * max(1, n_maps))(*[_cwin(w) for w in windows])
+    T = (_Track * max(1, len(tracks)))()
+    for k, t in enumerate(tracks):
+        T[k].map = int(t.map)
+        T[k].n = int(t.n)
+        for a in range(2):
+            T[k].y0[a] = float(t.y0[a])
+            T[k].step[a] = float(t.step[a])
+    return n_maps, M, W, T
+
+
+def rs_light_curves(maps, windows, profile: int, s: float, tracks, mu_out: torch.Tensor, dm_out: torch.Tensor = None,
+                    stream=None):
+    """Light curves of ``tracks`` over ``maps`` (float32 CUDA tensors [npix1, npix0]) into float64 outputs."""
+    n_maps, M, W, T = _lc_arrays(maps, windows, tracks)
+    total = sum(int(t.n) for t in tracks)
+    pm = _dptr(mu_out, torch.float64, "mu_out", total)
+    pd = _dptr(dm_out, torch.float64, "dm_out", total)
+    _check(load().rs_light_curves(n_maps, M, W, int(profile), float(s), len(tracks), T, pm, pd, _stream(stream)),
+           "rs_light_curves")
+
+
+def rs_light_curve_plan_create(maps, windows, profile: int, s: float, tracks) -> int:
+    n_maps, M, W, T = _lc_arrays(maps, windows, tracks)
+    p = ctypes.c_void_p()
+    _check(load().rs_light_curve_plan_create(n_maps, M, W, int(profile), float(s), len(tracks), T, ctypes.byref(p)),
+           "rs_light_curve_plan_create")
+    return p.value
+
+
+def rs_light_curve_plan_samples(plan: int) -> int:
+    n = ctypes.c_int64()
+    _check(load().rs_light_curve_plan_samples(plan, ctypes.byref(n)), "rs_light_curve_plan_samples")
+    return int(n.value)
+
+
+def rs_light_curve_plan_launch(plan: int, mu_out: torch.Tensor, dm_out: torch.Tensor = None, stream=None):
+    n = rs_light_curve_plan_samples(plan)
+    pm = _dptr(mu_out, torch.float64, "mu_out", n)
+    pd = _dptr(dm_out, torch.float64, "dm_out", n)
+    _check(load().rs_light_curve_plan_launch(plan, pm, pd, _stream(stream)), "rs_light_curve_plan_launch")
+
+
+def rs_light_curve_plan_destroy(plan: int):
+    _check(load().rs_light_curve_plan_destroy(plan), "rs_light_curve_plan_destroy")
+
+
+class LightCurvePlan:
+    """Tracks over maps, validated and uploaded once; ``launch`` fills ``mu`` and ``dm`` (float64)."""
+
+    def __init__(self, maps, windows, tracks, profile: int = 0, s: float = 1.0):
+        self.maps = list(maps)      # the plan reads these buffers at every launch
+        self.handle = rs_light_curve_plan_create(self.maps, windows, profile, s, tracks)
+        n = rs_light_curve_plan_samples(self.handle)
+        dev = self.maps[0].device if self.maps else torch.device("cuda", torch.cuda.current_device())
+        self.mu = torch.empty(n, dtype=torch.float64, device=dev)
+        self.dm = torch.empty(n, dtype=torch.float64, device=dev)
+
+    def launch(self, stream=None):
+        rs_light_curve_plan_launch(self.handle, self.mu, self.dm, stream)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            rs_light_curve_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def light_curves(maps, windows, tracks, profile: int = RS_PROFILE_GAUSSIAN, s: float = 1.0, stream=None):
+    """Returns (mu, dm) as float64 CUDA tensors with the tracks' samples concatenated in order."""
+    total = sum(int(t.n) for t in tracks)
+    dev = maps[0].device if maps else torch.device("cuda", torch.cuda.current_device())
+    mu = torch.empty(max(total, 0), dtype=torch.float64, device=dev)
+    dm = torch.empty_like(mu)
+    if total:
+        rs_light_curves(maps, windows, profile, s, tracks, mu, dm, stream)
+    return mu, dm
 
 
 def _batch_arrays(handles, grids, windows, counts_list, oow):

@@ -57,4 +57,26 @@ cudaError_t launch_batch(int cfg, bool mass, const rsdev::ShootDesc* descs, cons
                          int* counter, int grid, cudaStream_t s);
 cudaError_t batch_blocks_per_sm(int cfg, bool mass, int* blocks);
 
+// Light curves (rs_lightcurve.cu): one descriptor per track with samples, in output order.
+struct LcTrack {
+  const float* mu;          // map, float[np1][np0]
+  int np0, np1;
+  double lo0, lo1;          // window lower edges
+  double pix0, pix1;        // pixel sizes (hi - lo) / npix
+  double y00, y01;          // first sample
+  double st0, st1;          // sample step
+  double t00, t01;          // first sample in pixel-index units: (y0 - lo) / pix - 0.5
+  double d0, d1;            // step in pixel-index units: step / pix
+  double rp0, rp1;          // support radius in pixels per axis (R / pix)
+  float a0, a1;             // exponent per squared pixel offset (Gaussian: log2(e) pix^2 / (2 s^2); disc: pix^2 / s^2)
+  float inv_a0;             // 1 / a0
+  float band;               // guard band of the float32 exponent around the cut
+  int64_t n;                // samples (> 0)
+  int64_t out_off;          // first output position
+};
+
+// profile: 0 Gaussian, 1 disc.  cut2: the float64 squared support radius; ecut: the cut in exponent units.
+cudaError_t launch_light_curves(int profile, const LcTrack* tracks, int n_tracks, int64_t n_samples, double cut2,
+                                float ecut, double* mu_out, double* dm_out, int grid, cudaStream_t s);
+
 }  // namespace rsint

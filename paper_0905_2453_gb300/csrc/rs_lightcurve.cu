@@ -1,0 +1,130 @@
+// Light curves of magnification maps (Section 1): the profile-weighted mean of a map around each
+// sample of a straight source track, and its magnitude change -2.5 log10 mu.
+//
+// One thread per sample; the 32 samples of a warp are consecutive samples of (mostly) one track,
+// so the warp's loads of neighbouring pixels fall in the same L1 lines and every per-sample
+// float64 step (position, box, quotient) is paid once per thread, not once per pixel.  A thread
+// walks the rows of the box that bounds its profile's support and, per row, the chord of the
+// support (one pixel of margin each side).  Membership is decided from a float32 exponent
+// E = (di)^2 a0 + (dj)^2 a1 of the pixel offset (di, dj) in pixel units; pixels whose E lies within
+// a guard band of the cut repeat the float64 test ((lo + (i + 0.5) pix) - y)^2 + (...)^2 <= cut^2
+// (no fused multiply-add), so the covered pixel set is exactly that of a float64 evaluation.
+// Gaussian weights are 2^-E with the exponent pre-scaled by log2(e) (one MUFU ex2).  Each row's
+// partial sums are plain float32 (at most 2 R / pix + 3 terms); the rows are folded into compensated
+// (TwoSum) float32 pairs and the mean is their float-float quotient.
+#include "rs_internal.h"
+
+namespace {
+
+using rsint::LcTrack;
+
+__device__ __forceinline__ void acc_two_sum(float& s, float& c, float x) {
+  const float t = __fadd_rn(s, x);
+  const float bp = __fsub_rn(t, s);
+  c = __fadd_rn(c, __fadd_rn(__fsub_rn(s, __fsub_rn(t, bp)), __fsub_rn(x, bp)));
+  s = t;
+}
+
+__device__ __forceinline__ float ex2_neg(float e) {
+  float r;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(-e));
+  return r;
+}
+
+// The float64 membership test, written as the definition states it.
+__device__ __noinline__ bool inside_f64(const LcTrack& T, int64_t k, int i, int j, double cut2) {
+  const double yx = __dadd_rn(T.y00, __dmul_rn((double)k, T.st0));
+  const double yy = __dadd_rn(T.y01, __dmul_rn((double)k, T.st1));
+  const double cx = __dadd_rn(T.lo0, __dmul_rn((double)i + 0.5, T.pix0));
+  const double cy = __dadd_rn(T.lo1, __dmul_rn((double)j + 0.5, T.pix1));
+  const double dx = __dsub_rn(cx, yx);
+  const double dy = __dsub_rn(cy, yy);
+  return __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)) <= cut2;
+}
+
+template <int PROFILE>
+__global__ void __launch_bounds__(256) light_curve_kernel(const LcTrack* __restrict__ tracks, int n_tracks,
+                                                          int64_t n_samples, double cut2, float ecut,
+                                                          double* __restrict__ mu_out,
+                                                          double* __restrict__ dm_out) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < n_samples; g += stride) {
+    // the track holding sample g: the last one whose first output position is <= g
+    int lo = 0, hi = n_tracks - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (tracks[mid].out_off <= g) lo = mid; else hi = mid - 1;
+    }
+    const LcTrack& T = tracks[lo];
+    const int64_t k = g - T.out_off;
+    // sample position in pixel-index units (pixel i has its centre at t = i)
+    const double t0 = fma((double)k, T.d0, T.t00);
+    const double t1 = fma((double)k, T.d1, T.t01);
+    float sw = 0.f, cw = 0.f, sm = 0.f, cm = 0.f;
+    if (t0 > -T.rp0 - 2.0 && t0 < (double)T.np0 + T.rp0 + 1.0 && t1 > -T.rp1 - 2.0 &&
+        t1 < (double)T.np1 + T.rp1 + 1.0) {
+      const double ti = floor(t0), tj = floor(t1);
+      const int it = (int)ti, jt = (int)tj;
+      const float fx = (float)(t0 - ti), fy = (float)(t1 - tj);
+      const float rpx = (float)T.rp0, rpy = (float)T.rp1;
+      const int i_lo = max(it + (int)ceilf(fx - rpx) - 1, 0), i_hi = min(it + (int)floorf(fx + rpx) + 1, T.np0 - 1);
+      const int j_lo = max(jt + (int)ceilf(fy - rpy) - 1, 0), j_hi = min(jt + (int)floorf(fy + rpy) + 1, T.np1 - 1);
+      const float a0 = T.a0, a1 = T.a1, band = T.band, lim = ecut + T.band;
+      for (int j = j_lo; j <= j_hi; ++j) {
+        const float dyp = __fsub_rn((float)(j - jt), fy);
+        const float ey = __fmul_rn(__fmul_rn(dyp, dyp), a1);
+        const float rem = lim - ey;
+        if (!(rem >= 0.f)) continue;
+        // chord of the support on this row, one pixel of margin each side
+        const float half = sqrtf(rem * T.inv_a0) + 1.f;
+        const int c_lo = max(it + (int)ceilf(fx - half), i_lo);
+        const int c_hi = min(it + (int)floorf(fx + half), i_hi);
+        const float* __restrict__ row = T.mu + (int64_t)j * T.np0;
+        float kx = (float)(c_lo - it);
+        float rw = 0.f, rm = 0.f;  // this row's partial sums (at most 2 R / pix + 3 terms)
+#pragma unroll 4
+        for (int i = c_lo; i <= c_hi; ++i) {
+          const float dxp = __fsub_rn(kx, fx);
+          const float e = fmaf(__fmul_rn(dxp, dxp), a0, ey);
+          bool in = e <= ecut;
+          if (fabsf(e - ecut) <= band) in = inside_f64(T, k, i, j, cut2);
+          if (in) {
+            const float w = PROFILE == 0 ? ex2_neg(e) : 1.f;
+            const float v = __ldg(row + i);
+            rw = __fadd_rn(rw, w);
+            rm = fmaf(w, v, rm);
+          }
+          kx = __fadd_rn(kx, 1.f);
+        }
+        acc_two_sum(sw, cw, rw);
+        acc_two_sum(sm, cm, rm);
+      }
+    }
+    double m;
+    if (sw > 0.f) {
+      // float-float quotient (sm + cm) / (sw + cw): the residual of q sw is exact under fma
+      const float q = __fdiv_rn(sm, sw);
+      const float r = __fadd_rn(fmaf(-q, sw, sm), fmaf(-q, cw, cm));
+      m = (double)q + (double)__fdiv_rn(r, sw);
+    } else {
+      m = __longlong_as_double(0x7ff8000000000000LL);
+    }
+    mu_out[g] = m;
+    if (dm_out) dm_out[g] = (double)(-2.5f * log10f((float)m));
+  }
+}
+
+}  // namespace
+
+namespace rsint {
+
+cudaError_t launch_light_curves(int profile, const LcTrack* tracks, int n_tracks, int64_t n_samples, double cut2,
+                                float ecut, double* mu_out, double* dm_out, int grid, cudaStream_t s) {
+  if (profile == 0)
+    light_curve_kernel<0><<<grid, 256, 0, s>>>(tracks, n_tracks, n_samples, cut2, ecut, mu_out, dm_out);
+  else
+    light_curve_kernel<1><<<grid, 256, 0, s>>>(tracks, n_tracks, n_samples, cut2, ecut, mu_out, dm_out);
+  return cudaGetLastError();
+}
+
+}  // namespace rsint

@@ -218,3 +218,79 @@ def sample_rays(grid: RayGrid, k: int, seed: int) -> np.ndarray:
     i = rng.integers(0, grid.n[0], size=k, dtype=np.int64)
     j = rng.integers(0, grid.n[1], size=k, dtype=np.int64)
     return np.stack([i, j], axis=1)
+
+
+# Light-curve inputs ------------------------------------------------------------------------------
+
+@dataclasses.dataclass
+class Track:
+    """Straight source track: samples y_k = y0 + k step (k = 0 .. n-1) over map number ``map``."""
+    map: int
+    y0: tuple
+    step: tuple
+    n: int
+
+
+def caustic_map(npix: tuple, seed: int, n_caustics: int = 12) -> np.ndarray:
+    """A synthetic float32 magnification map [npix1, npix0] with the structure of a microlensing map:
+    a lognormal background around mu ~ 1 and fold caustics, closed curves (here circles of random
+    centre and radius) outside of which mu rises as A / sqrt(distance) within a few pixels (the
+    fold's inverse-square-root law), up to a few hundred."""
+    rng = np.random.default_rng(seed)
+    n0, n1 = int(npix[0]), int(npix[1])
+    mu = rng.lognormal(0.0, 0.25, size=(n1, n0))
+    for _ in range(n_caustics):
+        cx, cy = rng.uniform(0, n0), rng.uniform(0, n1)
+        r = rng.uniform(0.05, 0.4) * min(n0, n1)
+        amp = rng.uniform(1.0, 4.0)
+        # only the pixels within the ring's bounding box can lie within 15 pixels outside it
+        i0, i1 = max(0, int(cx - r - 16)), min(n0, int(cx + r + 17))
+        j0, j1 = max(0, int(cy - r - 16)), min(n1, int(cy + r + 17))
+        ii = np.arange(i0, i1, dtype=np.float64)[None, :]
+        jj = np.arange(j0, j1, dtype=np.float64)[:, None]
+        d = np.hypot(ii - cx, jj - cy) - r          # > 0 outside the curve
+        out = (d > 0) & (d < 15)
+        sub = mu[j0:j1, i0:i1]
+        sub[out] += amp / np.sqrt(np.maximum(d[out], 1e-3))
+    return np.minimum(mu, 500.0).astype(np.float32)
+
+
+def random_tracks(windows: list, n_per_map: int, n_samples: int, step_pix: float, seed: int,
+                  margin_pix: float = 0.0) -> list:
+    """Tracks with uniformly random start points inside each window (shrunk by margin_pix) and
+    uniformly random directions, sample spacing step_pix pixels of axis 0."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for m, w in enumerate(windows):
+        pix0 = (w.hi[0] - w.lo[0]) / w.npix[0]
+        pix1 = (w.hi[1] - w.lo[1]) / w.npix[1]
+        for _ in range(n_per_map):
+            y0 = (rng.uniform(w.lo[0] + margin_pix * pix0, w.hi[0] - margin_pix * pix0),
+                  rng.uniform(w.lo[1] + margin_pix * pix1, w.hi[1] - margin_pix * pix1))
+            th = rng.uniform(0.0, 2.0 * np.pi)
+            step = (step_pix * pix0 * np.cos(th), step_pix * pix0 * np.sin(th))
+            out.append(Track(m, (float(y0[0]), float(y0[1])), (float(step[0]), float(step[1])), int(n_samples)))
+    return out
+
+
+def light_curve_workload(n_maps: int = 64, tracks_per_map: int = 16, n_samples: int = 2048, base_seed: int = 3000):
+    """Light curves over many maps: n_maps synthetic caustic maps with the batch's map sides
+    (U{512, 640, ..., 1024} pixels) over the window [-1, 1]^2, tracks_per_map random tracks of
+    n_samples samples spaced 0.25 pixel (of a 1024-pixel map) each, and a Gaussian source of
+    standard deviation 2 pixels of a 1024-pixel map (1 to 2 pixels of the actual maps).
+    Returns (maps, windows, tracks, s)."""
+    maps, wins = [], []
+    for k in range(n_maps):
+        rng = np.random.default_rng(base_seed + k)
+        npix = int(rng.choice(np.arange(512, 1024 + 1, 128)))
+        wins.append(Window(lo=(-1.0, -1.0), hi=(1.0, 1.0), npix=(npix, npix)))
+        maps.append(caustic_map((npix, npix), seed=base_seed + 10_000 + k))
+    px = 2.0 / 1024
+    tracks = []
+    rng = np.random.default_rng(base_seed - 1)
+    for m in range(n_maps):
+        for _ in range(tracks_per_map):
+            y0 = (float(rng.uniform(-0.9, 0.9)), float(rng.uniform(-0.9, 0.9)))
+            th = float(rng.uniform(0.0, 2.0 * np.pi))
+            tracks.append(Track(m, y0, (0.25 * px * math.cos(th), 0.25 * px * math.sin(th)), n_samples))
+    return maps, wins, tracks, 2.0 * px

@@ -106,3 +106,58 @@ def test_grid_window_validation(rs):
     # unknown launch shape
     assert lib.rs_set_launch_config(0, 96, 3) == rs.RS_EINVAL
     assert len(rs.rs_launch_configs()) >= 4
+
+
+def test_struct_layouts_match_binding(rs, tmp_path):
+    """sizeof/offsetof of the ABI structs as a C compiler sees include/rs.h equal the ctypes mirrors."""
+    src = tmp_path / "layout.c"
+    src.write_text(
+        '#include <stdio.h>\n#include <stddef.h>\n#include "rs.h"\n'
+        'int main(void) {\n'
+        '  printf("%zu %zu %zu %zu\\n", sizeof(rs_ray_grid), offsetof(rs_ray_grid, n), sizeof(rs_window),'
+        ' offsetof(rs_window, npix));\n'
+        '  printf("%zu %zu %zu %zu\\n", sizeof(rs_track), offsetof(rs_track, y0), offsetof(rs_track, step),'
+        ' offsetof(rs_track, n));\n'
+        '  return 0;\n}\n')
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    lines = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")
+    g, w, t = rs._Grid, rs._Window, rs._Track
+    assert [int(v) for v in lines[0].split()] == [ctypes.sizeof(g), g.n.offset, ctypes.sizeof(w), w.npix.offset]
+    assert [int(v) for v in lines[1].split()] == [ctypes.sizeof(t), t.y0.offset, t.step.offset, t.n.offset]
+
+
+def test_light_curve_validation(rs):
+    lib = rs.load()
+    maps = (ctypes.c_void_p * 1)(16)
+    win = (rs._Window * 1)(rs._cwin(rs.Window((-1.0, -1.0), (1.0, 1.0), (64, 64))))
+    out = ctypes.c_void_p(16)
+
+    def call(tracks, profile=rs.RS_PROFILE_GAUSSIAN, s=0.1, n_maps=1, m=maps, w=win, o=out):
+        T = (rs._Track * max(1, len(tracks)))()
+        for k, (mp, y0, st, n) in enumerate(tracks):
+            T[k].map, T[k].n = mp, n
+            T[k].y0[0], T[k].y0[1] = y0
+            T[k].step[0], T[k].step[1] = st
+        return lib.rs_light_curves(n_maps, m, w, profile, s, len(tracks), T, o, None, None)
+
+    good = (0, (0.0, 0.0), (0.01, 0.0), 10)
+    assert call([], s=0.1) == rs.RS_OK                                   # nothing to do: no CUDA call
+    assert call([(0, (0.0, 0.0), (0.0, 0.0), 0)], n_maps=0, m=None, w=None, o=None) == rs.RS_OK
+    assert call([good], profile=7) == rs.RS_EINVAL
+    assert call([good], s=0.0) == rs.RS_EINVAL
+    assert call([good], s=float("nan")) == rs.RS_EINVAL
+    assert call([(1, (0.0, 0.0), (0.01, 0.0), 10)]) == rs.RS_EINVAL      # map index out of range
+    assert "map 1" in rs.rs_last_error()
+    assert call([(0, (0.0, 0.0), (0.01, 0.0), -1)]) == rs.RS_EINVAL      # negative sample count
+    assert call([(0, (float("inf"), 0.0), (0.01, 0.0), 10)]) == rs.RS_EINVAL
+    assert call([(0, (0.0, 0.0), (1e9, 0.0), 10)]) == rs.RS_EINVAL       # last sample beyond 1e9
+    assert call([good], s=1e6) == rs.RS_EINVAL                          # support beyond 2^22 pixels
+    assert call([good], o=None) == rs.RS_EINVAL
+    assert call([(0, (0.0, 0.0), (0.0, 0.0), 1 << 41)]) == rs.RS_EOVERFLOW
+    bad_win = (rs._Window * 1)(rs._cwin(rs.Window((1.0, -1.0), (1.0, 1.0), (64, 64))))
+    assert call([good], w=bad_win) == rs.RS_EINVAL
+    big = (rs._Window * 1)(rs._cwin(rs.Window((-1.0, -1.0), (1.0, 1.0), ((1 << 24) + 1, 64))))
+    assert call([good], w=big) == rs.RS_EINVAL
+    far = (rs._Window * 1)(rs._cwin(rs.Window((1e8, -1.0), (1e8 + 1e-3, 1.0), (64, 64))))
+    assert call([good], w=far) == rs.RS_EINVAL                           # |lo| / pixel beyond 2^30
