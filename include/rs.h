@@ -251,7 +251,7 @@ typedef struct {
  *   windows  : host array of n_maps source-plane windows, one per map.  Per axis npix <= 2^24
  *              and max(|lo|, |hi|) / pix <= 2^30.
  *   profile, s : RS_PROFILE_GAUSSIAN or RS_PROFILE_DISC and its size (finite, > 0; the profile's
- *              support may span at most 2^22 pixels from its centre along either axis).
+ *              support may span at most 2^20 pixels from its centre along either axis).
  *   tracks   : host array of n_tracks tracks.  Track t's samples are written at consecutive
  *              positions starting at sum_{u < t} tracks[u].n.
  *   d_mu_out : double[sum n] device, receives mu(y_k).

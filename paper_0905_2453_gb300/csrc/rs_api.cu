@@ -282,7 +282,7 @@ int lc_prepare(int n_maps, const float* const* d_mu, const rs_window* windows, i
       if (std::max(std::fabs(w->lo[k]), std::fabs(w->hi[k])) / pix[k] > 1073741824.0)
         return fail(RS_EINVAL, "map %d axis %d: max(|lo|, |hi|) / pixel must be <= 2^30", tr.map, k);
       rp[k] = R / pix[k];
-      if (!(rp[k] <= 4194304.0)) return fail(RS_EINVAL, "profile spans more than 2^22 pixels along axis %d of map %d", k, tr.map);
+      if (!(rp[k] <= 1048576.0)) return fail(RS_EINVAL, "profile spans more than 2^20 pixels along axis %d of map %d", k, tr.map);
       const double last = tr.y0[k] + (double)(tr.n - 1) * tr.step[k];
       if (!finite_coord(tr.y0[k]) || !std::isfinite(tr.step[k]) || !finite_coord(last))
         return fail(RS_EINVAL, "track %d: samples must be finite with |y| <= 1e9", t);

@@ -5,10 +5,12 @@
 // so the warp's loads of neighbouring pixels fall in the same L1 lines and every per-sample
 // float64 step (position, box, quotient) is paid once per thread, not once per pixel.  A thread
 // walks the rows of the box that bounds its profile's support and, per row, the chord of the
-// support (one pixel of margin each side).  Membership is decided from a float32 exponent
-// E = (di)^2 a0 + (dj)^2 a1 of the pixel offset (di, dj) in pixel units; pixels whose E lies within
-// a guard band of the cut repeat the float64 test ((lo + (i + 0.5) pix) - y)^2 + (...)^2 <= cut^2
-// (no fused multiply-add), so the covered pixel set is exactly that of a float64 evaluation.
+// support (half a pixel of margin each side).  With E = (di)^2 a0 + (dj)^2 a1 the float32 exponent of
+// the pixel offset (di, dj) in pixel units, the chord's interior (E below the cut by more than a
+// guard band, half a pixel of margin) is summed without tests; at the rim membership is decided from
+// E, and pixels whose E lies within the guard band repeat the float64 test
+// ((lo + (i + 0.5) pix) - y)^2 + (...)^2 <= cut^2 (no fused multiply-add), so the covered pixel set
+// is exactly that of a float64 evaluation.
 // Gaussian weights are 2^-E with the exponent pre-scaled by log2(e) (one MUFU ex2).  Each row's
 // partial sums are plain float32 (at most 2 R / pix + 3 terms); the rows are folded into compensated
 // (TwoSum) float32 pairs and the mean is their float-float quotient.
@@ -25,6 +27,10 @@ __device__ __forceinline__ void acc_two_sum(float& s, float& c, float x) {
   s = t;
 }
 
+// sqrt(x) for x >= 0 from the hardware reciprocal square root (a few ulp; used for chord bounds
+// that carry half a pixel of margin)
+__device__ __forceinline__ float sqrt_approx(float x) { return x > 0.f ? x * rsqrtf(x) : 0.f; }
+
 __device__ __forceinline__ float ex2_neg(float e) {
   float r;
   asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(-e));
@@ -40,6 +46,23 @@ __device__ __noinline__ bool inside_f64(const LcTrack& T, int64_t k, int i, int 
   const double dx = __dsub_rn(cx, yx);
   const double dy = __dsub_rn(cy, yy);
   return __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)) <= cut2;
+}
+
+// A pixel near the rim of the support: decided by the float32 exponent, or by the float64 test of
+// the definition when the exponent lies within the guard band of the cut.
+template <int PROFILE>
+__device__ __forceinline__ void rim_pixel(const LcTrack& T, int64_t k, int i, int j, int it, float fx, float a0,
+                                          float ey, float ecut, float band, double cut2,
+                                          const float* __restrict__ row, float& rw, float& rm) {
+  const float dxp = __fsub_rn((float)(i - it), fx);
+  const float e = fmaf(__fmul_rn(dxp, dxp), a0, ey);
+  bool in = e <= ecut;
+  if (fabsf(e - ecut) <= band) in = inside_f64(T, k, i, j, cut2);
+  if (in) {
+    const float w = PROFILE == 0 ? ex2_neg(e) : 1.f;
+    rw = __fadd_rn(rw, w);
+    rm = fmaf(w, __ldg(row + i), rm);
+  }
 }
 
 template <int PROFILE>
@@ -69,33 +92,55 @@ __global__ void __launch_bounds__(256) light_curve_kernel(const LcTrack* __restr
       const float rpx = (float)T.rp0, rpy = (float)T.rp1;
       const int i_lo = max(it + (int)ceilf(fx - rpx) - 1, 0), i_hi = min(it + (int)floorf(fx + rpx) + 1, T.np0 - 1);
       const int j_lo = max(jt + (int)ceilf(fy - rpy) - 1, 0), j_hi = min(jt + (int)floorf(fy + rpy) + 1, T.np1 - 1);
-      const float a0 = T.a0, a1 = T.a1, band = T.band, lim = ecut + T.band;
+      const float a0 = T.a0, a1 = T.a1, band = T.band;
+      const float lim_hi = ecut + band, lim_lo = ecut - band;
       for (int j = j_lo; j <= j_hi; ++j) {
         const float dyp = __fsub_rn((float)(j - jt), fy);
         const float ey = __fmul_rn(__fmul_rn(dyp, dyp), a1);
-        const float rem = lim - ey;
-        if (!(rem >= 0.f)) continue;
-        // chord of the support on this row, one pixel of margin each side
-        const float half = sqrtf(rem * T.inv_a0) + 1.f;
-        const int c_lo = max(it + (int)ceilf(fx - half), i_lo);
-        const int c_hi = min(it + (int)floorf(fx + half), i_hi);
-        const float* __restrict__ row = T.mu + (int64_t)j * T.np0;
-        float kx = (float)(c_lo - it);
-        float rw = 0.f, rm = 0.f;  // this row's partial sums (at most 2 R / pix + 3 terms)
-#pragma unroll 4
-        for (int i = c_lo; i <= c_hi; ++i) {
-          const float dxp = __fsub_rn(kx, fx);
-          const float e = fmaf(__fmul_rn(dxp, dxp), a0, ey);
-          bool in = e <= ecut;
-          if (fabsf(e - ecut) <= band) in = inside_f64(T, k, i, j, cut2);
-          if (in) {
-            const float w = PROFILE == 0 ? ex2_neg(e) : 1.f;
-            const float v = __ldg(row + i);
-            rw = __fadd_rn(rw, w);
-            rm = fmaf(w, v, rm);
+        const float rem_hi = lim_hi - ey;
+        if (!(rem_hi >= 0.f)) continue;
+        // chord of the support on this row (E <= cut + band), half a pixel of margin each side; float32
+        // errors of the half-chord are ~2^-24 of the support radius, far inside the guard band
+        const float h_out = sqrt_approx(rem_hi * T.inv_a0) + 0.5f;
+        const int c_lo = max(it + (int)ceilf(fx - h_out), i_lo);
+        const int c_hi = min(it + (int)floorf(fx + h_out), i_hi);
+        // interior of the chord (E <= cut - band, half a pixel of margin): inside for certain, no test
+        int n_lo = c_hi + 1, n_hi = c_hi;
+        const float rem_lo = lim_lo - ey;
+        if (rem_lo > 0.f) {
+          const float h_in = sqrt_approx(rem_lo * T.inv_a0) - 0.5f;
+          if (h_in >= 0.f) {
+            n_lo = max(it + (int)ceilf(fx - h_in), c_lo);
+            n_hi = min(it + (int)floorf(fx + h_in), c_hi);
+            if (n_lo > n_hi) {
+              n_lo = c_hi + 1;
+              n_hi = c_hi;
+            }
           }
-          kx = __fadd_rn(kx, 1.f);
         }
+        const float* __restrict__ row = T.mu + (int64_t)j * T.np0;
+        float rw = 0.f, rm = 0.f;  // this row's partial sums (at most 2 R / pix + 3 terms)
+        // rim pixels on the low side: float32 test, float64 test inside the guard band
+        for (int i = c_lo; i < n_lo; ++i) rim_pixel<PROFILE>(T, k, i, j, it, fx, a0, ey, ecut, band, cut2, row, rw, rm);
+        if (PROFILE == 0) {
+          float kx = (float)(n_lo - it);
+#pragma unroll 4
+          for (int i = n_lo; i <= n_hi; ++i) {
+            const float dxp = __fsub_rn(kx, fx);
+            const float w = ex2_neg(fmaf(__fmul_rn(dxp, dxp), a0, ey));
+            rw = __fadd_rn(rw, w);
+            rm = fmaf(w, __ldg(row + i), rm);
+            kx = __fadd_rn(kx, 1.f);
+          }
+        } else {
+          float acc = 0.f;
+#pragma unroll 4
+          for (int i = n_lo; i <= n_hi; ++i) acc = __fadd_rn(acc, __ldg(row + i));
+          rw = __fadd_rn(rw, (float)(n_hi - n_lo + 1));
+          rm = __fadd_rn(rm, acc);
+        }
+        // rim pixels on the high side
+        for (int i = n_hi + 1; i <= c_hi; ++i) rim_pixel<PROFILE>(T, k, i, j, it, fx, a0, ey, ecut, band, cut2, row, rw, rm);
         acc_two_sum(sw, cw, rw);
         acc_two_sum(sm, cm, rm);
       }

@@ -152,7 +152,7 @@ def test_light_curve_validation(rs):
     assert call([(0, (0.0, 0.0), (0.01, 0.0), -1)]) == rs.RS_EINVAL      # negative sample count
     assert call([(0, (float("inf"), 0.0), (0.01, 0.0), 10)]) == rs.RS_EINVAL
     assert call([(0, (0.0, 0.0), (1e9, 0.0), 10)]) == rs.RS_EINVAL       # last sample beyond 1e9
-    assert call([good], s=1e6) == rs.RS_EINVAL                          # support beyond 2^22 pixels
+    assert call([good], s=1e6) == rs.RS_EINVAL                          # support beyond 2^20 pixels
     assert call([good], o=None) == rs.RS_EINVAL
     assert call([(0, (0.0, 0.0), (0.0, 0.0), 1 << 41)]) == rs.RS_EOVERFLOW
     bad_win = (rs._Window * 1)(rs._cwin(rs.Window((1.0, -1.0), (1.0, 1.0), (64, 64))))

@@ -73,7 +73,7 @@ def _bound(mu_map, w, profile, s, y, ref):
     if sw == 0:
         return 0.0
     first = (wgt * delta * np.abs(mu_map - ref)).sum() / sw
-    n_r = 2.0 * (6.0 * s if profile == G else s) / pix0 + 3.0   # longest row of the support
+    n_r = min(2.0 * (6.0 * s if profile == G else s) / pix0 + 3.0, n0)   # longest row of the support
     return 2.0 * (first + (2.0 * n_r + 10.0) * U * abs(ref))
 
 
@@ -239,3 +239,14 @@ def test_plan_matches_one_shot_and_replays_in_a_graph():
         assert _bits_equal(plan.mu[:n0], ref_mu[:n0]) and _bits_equal(plan.mu[n0:], 2 * ref_mu[n0:])
     finally:
         plan.close()
+
+
+@pytest.mark.parametrize("profile,radius", [(D, 100.0), (G, 100.0 / 6.0)])
+def test_large_support_rim_crosses_map(profile, radius):
+    """A support of ~5000 pixels radius whose rim crosses the map: hundreds of rim pixels fall inside
+    the guard band and take the float64 decision; the interior of each chord is summed untested."""
+    w = _window((200, 150))
+    mu = ri.caustic_map(w.npix, seed=11)
+    tracks = [ri.Track(0, (-100.0 + 0.3, 0.2), (0.0123, 0.0071), 6),
+              ri.Track(0, (0.1, 1.0 + 100.0 - 0.4), (0.0031, -0.009), 6)]
+    _compare([mu], [w], tracks, profile, radius, f"large support {profile}")
