@@ -361,6 +361,12 @@ def run_ours(args):
     if not args.no_light_curves and world == 1:
         light = run_light_curves(rs, torch, device, stream)
 
+    # ---------------- zoom into the map (culled shooting) vs plain shooting of the finer grid
+    zoom = None
+    if not args.no_zoom and world == 1:
+        zoom = run_zoom(rs, torch, device, stream, spec)
+        zoom["culled_full_map"] = run_zoom(rs, torch, device, stream, spec, factor=1, quarter=False)
+
     # ---------------- CPU baseline (oracle, bounded sample)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -399,6 +405,7 @@ def run_ours(args):
         "cpu_baseline": cpu,
         "batched": batched,
         "light_curves": light,
+        "zoom": zoom,
         "wall_s_timed_region": wall,
     }
     print(json.dumps(line), flush=True)
@@ -530,6 +537,72 @@ def run_light_curves(rs, torch, device, stream, reps=20, cpu_samples=4096):
                        "cores": oracle.num_threads()}}
 
 
+def run_zoom(rs, torch, device, stream, spec, factor=4, reps=3, quarter=True):
+    """Zoom x factor into the central quarter (per axis) of the map (or the whole map with
+    quarter=False): culled vs plain shooting."""
+    w = spec.window
+    q = [(w.hi[k] - w.lo[k]) / (8.0 if quarter else 2.0) for k in range(2)]
+    c = [(w.hi[k] + w.lo[k]) / 2.0 for k in range(2)]
+    lo, hi = (c[0] - q[0], c[1] - q[1]), (c[0] + q[0], c[1] + q[1])
+    g = rs.zoom_grid(spec.grid, factor)
+    zw = rs.zoom_window(w, lo, hi, factor)
+    f = rs.Field.from_spec(spec, stream)
+    npix = (int(zw.npix[1]), int(zw.npix[0]))
+    cc = torch.zeros(npix, dtype=torch.int32, device=device)
+    cp = torch.zeros_like(cc)
+    oc = torch.zeros(1, dtype=torch.int64, device=device)
+    op = torch.zeros_like(oc)
+    shot = torch.zeros(1, dtype=torch.int64, device=device)
+    f.shoot(g, zw, cc, oc, stream=stream, culled=True, rays_shot=shot)   # warm-up
+    torch.cuda.synchronize(device)
+    n_shot = int(shot.item())
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        cc.zero_()
+        oc.zero_()
+        f.shoot(g, zw, cc, oc, stream=stream, culled=True)
+    e1.record(stream)
+    torch.cuda.synchronize(device)
+    t_c = e0.elapsed_time(e1) / 1e3 / reps
+    e0.record(stream)
+    f.shoot(g, zw, cp, op, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize(device)
+    t_p = e0.elapsed_time(e1) / 1e3
+    same = bool(torch.equal(cc, cp)) and bool(torch.equal(oc, op))
+    f.close()
+    n = g.n[0] * g.n[1]
+    region = "the central quarter of the map per axis" if quarter else "the whole map"
+    return {"workload": f"{args_workload_name(spec)}: x{factor} zoom into {region}, {g.n[0]}^2 rays, "
+                        f"{zw.npix[0]}^2 map",
+            "rays": n, "rays_shot": n_shot, "rays_shot_frac": n_shot / n, "culled_ms": t_c * 1e3,
+            "plain_ms": t_p * 1e3, "speedup": t_p / t_c, "bitwise_equal": same,
+            "culled_interactions_per_s_full_grid_equivalent": n * spec.n_lens / t_c}
+
+
+def run_section(args):
+    import torch
+    import paper_0905_2453_gb300 as rs
+    device = torch.device("cuda", 0)
+    torch.cuda.set_device(device)
+    stream = torch.cuda.current_stream(device)
+    if args.section == "zoom":
+        spec = workload(args.workload, seed=0)
+        if args.launch_shape:
+            b_, r_ = (int(v) for v in args.launch_shape.split("x"))
+            rs.rs_set_launch_config(spec.masses is not None, b_, r_)
+        out = {"zoom": run_zoom(rs, torch, device, stream, spec),
+               "culled_full_map": run_zoom(rs, torch, device, stream, spec, factor=1, quarter=False)}
+    else:
+        out = {"light_curves": run_light_curves(rs, torch, device, stream)}
+    print(json.dumps(out), flush=True)
+
+
+def args_workload_name(spec):
+    return getattr(spec, "name", "field")
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -540,6 +613,9 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-light-curves", action="store_true")
+    ap.add_argument("--no-zoom", action="store_true")
+    ap.add_argument("--section", choices=["zoom", "light-curves"], default=None,
+                    help="run one secondary measurement alone and print its JSON object (for profiling)")
     ap.add_argument("--batch-reps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
@@ -547,7 +623,9 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")
-    if args.impl == "reference":
+    if args.section is not None:
+        run_section(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)

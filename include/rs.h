@@ -127,6 +127,23 @@ int rs_shoot_rows(rs_field_t f, const rs_ray_grid* g, int64_t row_begin, int64_t
                   const rs_window* w, uint32_t* d_counts, uint64_t* d_out_of_window, void* stream);
 
 /*
+ * rs_shoot_culled -- rs_shoot_rows that skips rays which provably miss the window: the interactive
+ * zoom of Section 4 (a sub-window re-shot at higher resolution only needs the rays that can land
+ * in it).  Rays are grouped in cells of 16 x 16; for a cell with ray-box centre c and circumradius
+ * rho, the deflection of every ray differs from alpha(c) by at most rho sum_i m_i / (d_i (d_i - rho))
+ * (d_i = |c - x_i|), so the cell's source positions lie in a box around lam x - alpha(c); a cell
+ * whose box (widened by the float32 error band of its rays and float64 rounding) misses the window
+ * is skipped and its rays are counted out of window.  Cells with a lens within 1.02 rho of c are
+ * always shot.  Results: the same counts and out-of-window count as rs_shoot_rows, bit for bit (the
+ * shot cells use the same per-ray arithmetic and binning, certified binning included).
+ *   d_rays_shot : uint64 device counter or NULL; ACCUMULATES the number of rays actually shot.
+ * Other arguments, accumulation and errors as rs_shoot_rows.  Workspace is allocated
+ * stream-ordered (4 bytes per cell plus the re-evaluation list).
+ */
+int rs_shoot_culled(rs_field_t f, const rs_ray_grid* g, int64_t row_begin, int64_t row_end, const rs_window* w,
+                    uint32_t* d_counts, uint64_t* d_out_of_window, uint64_t* d_rays_shot, void* stream);
+
+/*
  * rs_trace -- source positions of listed rays through the float32 path, for checks.
  *   d_ray_ij : int64[2*k] device, (i, j) per ray (each within the grid).
  *   d_y      : double[2*k] device, receives (y1, y2) per ray (Eq. 6).

@@ -40,7 +40,7 @@ EXPORTED_SYMBOLS = (
     "rs_magnification", "rs_batch_create", "rs_batch_launch", "rs_batch_destroy", "rs_shoot_batch",
     "rs_field_status", "rs_last_error", "rs_version", "rs_set_launch_config", "rs_get_launch_config",
     "rs_launch_configs", "rs_trace_certified", "rs_set_certified_binning", "rs_get_certified_binning",
-    "rs_selftest_bounded_wait", "rs_shoot_rows_noalloc", "rs_light_curves",
+    "rs_selftest_bounded_wait", "rs_shoot_rows_noalloc", "rs_light_curves", "rs_shoot_culled",
     "rs_light_curve_plan_create", "rs_light_curve_plan_samples", "rs_light_curve_plan_launch",
     "rs_light_curve_plan_destroy",
 )
@@ -128,6 +128,7 @@ def load():
         "rs_get_certified_binning": ([ctypes.POINTER(i32)], i32),
         "rs_selftest_bounded_wait": ([i64, ctypes.POINTER(i32)], i32),
         "rs_shoot_rows_noalloc": ([vp, gp, i64, i64, wp, vp, vp, vp], i32),
+        "rs_shoot_culled": ([vp, gp, i64, i64, wp, vp, vp, vp, vp], i32),
         "rs_magnification": ([vp, gp, wp, vp, vp], i32),
         "rs_light_curves": ([i32, vp, vp, i32, dbl, i32, vp, vp, vp, vp], i32),
         "rs_light_curve_plan_create": ([i32, vp, vp, i32, dbl, i32, vp, ctypes.POINTER(vp)], i32),
@@ -287,6 +288,17 @@ def rs_shoot_rows_noalloc(handle: int, grid, row_begin: int, row_end: int, windo
     g, w = _cgrid(grid), _cwin(window)
     _check(load().rs_shoot_rows_noalloc(handle, ctypes.byref(g), int(row_begin), int(row_end), ctypes.byref(w), pc,
                                         po, _stream(stream)), "rs_shoot_rows_noalloc")
+
+
+def rs_shoot_culled(handle: int, grid, row_begin: int, row_end: int, window, counts, out_of_window=None,
+                    rays_shot=None, stream=None):
+    npx = int(window.npix[0]) * int(window.npix[1])
+    pc = _dptr(counts, _COUNT_DTYPES, "counts", npx)
+    po = _dptr(out_of_window, _OOW_DTYPES, "out_of_window", 1)
+    pr = _dptr(rays_shot, _OOW_DTYPES, "rays_shot", 1)
+    g, w = _cgrid(grid), _cwin(window)
+    _check(load().rs_shoot_culled(handle, ctypes.byref(g), int(row_begin), int(row_end), ctypes.byref(w), pc, po, pr,
+                                  _stream(stream)), "rs_shoot_culled")
 
 
 def rs_trace(handle: int, grid, ray_ij: torch.Tensor, y: torch.Tensor, alpha: torch.Tensor = None,
@@ -506,15 +518,29 @@ class Field:
     def info(self):
         return rs_field_info(self.handle)
 
-    def shoot(self, grid, window, counts=None, out_of_window=None, stream=None, rows=None):
+    def shoot(self, grid, window, counts=None, out_of_window=None, stream=None, rows=None, culled=False,
+              rays_shot=None):
+        """Shoot (accumulate) the grid's rays into counts; culled=True skips cells of rays that provably
+        miss the window (same results; rays_shot, if given, accumulates the rays actually shot)."""
         dev = torch.device("cuda", torch.cuda.current_device())
         if counts is None:
             counts = torch.zeros((int(window.npix[1]), int(window.npix[0])), dtype=torch.int32, device=dev)
-        if rows is None:
+        r0, r1 = (0, int(grid.n[1])) if rows is None else rows
+        if culled:
+            rs_shoot_culled(self.handle, grid, r0, r1, window, counts, out_of_window, rays_shot, stream)
+        elif rows is None:
             rs_shoot(self.handle, grid, window, counts, out_of_window, stream)
         else:
-            rs_shoot_rows(self.handle, grid, rows[0], rows[1], window, counts, out_of_window, stream)
+            rs_shoot_rows(self.handle, grid, r0, r1, window, counts, out_of_window, stream)
         return counts
+
+    def zoom(self, grid, window, lo, hi, factor: int, stream=None):
+        """Zoom into the source-plane region [lo, hi) of a map made with (grid, window): the map of that
+        region at `factor` times the pixel resolution, shot with `factor` times the ray density per axis
+        (so N_av is unchanged) and culled to the rays that can reach the region.  Returns
+        (counts, fine_grid, fine_window)."""
+        g, w = zoom_grid(grid, factor), zoom_window(window, lo, hi, factor)
+        return self.shoot(g, w, culled=True, stream=stream), g, w
 
     def trace(self, grid, ray_ij, with_alpha=False, with_err=False, certified=False, stream=None):
         """Source positions of listed rays: float32 path (default) or float-float (certified=True)."""
@@ -543,6 +569,26 @@ class Field:
             self.close()
         except Exception:
             pass
+
+
+def zoom_grid(grid, factor: int) -> RayGrid:
+    """The ray grid over the same image-plane cells with factor x factor rays per original ray cell
+    (cell-centred sub-rays)."""
+    f = int(factor)
+    if f < 1:
+        raise ValueError("factor must be >= 1")
+    sp = tuple(float(grid.spacing[k]) / f for k in range(2))
+    org = tuple(float(grid.origin[k]) - 0.5 * float(grid.spacing[k]) + 0.5 * sp[k] for k in range(2))
+    return RayGrid(org, sp, tuple(int(grid.n[k]) * f for k in range(2)))
+
+
+def zoom_window(window, lo, hi, factor: int) -> Window:
+    """The source-plane window [lo, hi) with pixels `factor` times smaller than the window's."""
+    npix = []
+    for k in range(2):
+        pix = (float(window.hi[k]) - float(window.lo[k])) / int(window.npix[k]) / int(factor)
+        npix.append(max(1, int(round((float(hi[k]) - float(lo[k])) / pix))))
+    return Window(tuple(float(v) for v in lo), tuple(float(v) for v in hi), tuple(npix))
 
 
 def magnification(counts, grid, window, stream=None):

@@ -531,6 +531,59 @@ int rs_shoot_rows(rs_field_t f, const rs_ray_grid* g, int64_t row_begin, int64_t
   return RS_OK;
 }
 
+int rs_shoot_culled(rs_field_t f, const rs_ray_grid* g, int64_t row_begin, int64_t row_end, const rs_window* w,
+                    uint32_t* d_counts, uint64_t* d_out_of_window, uint64_t* d_rays_shot, void* stream) {
+  if (!f) return fail(RS_EINVAL, "field is NULL");
+  int rc;
+  if ((rc = check_grid(g)) != RS_OK) return rc;
+  if ((rc = check_window(w)) != RS_OK) return rc;
+  if (!d_counts) return fail(RS_EINVAL, "d_counts is NULL");
+  if (row_begin < 0 || row_end < row_begin || row_end > g->n[1])
+    return fail(RS_EINVAL, "row range [%lld, %lld) outside [0, %lld]", (long long)row_begin, (long long)row_end,
+                (long long)g->n[1]);
+  if ((rc = check_field_device(f)) != RS_OK) return rc;
+  ShootDesc d;
+  if ((rc = fill_desc(f, g, row_begin, row_end, w, d_counts, d_out_of_window, &d)) != RS_OK) return rc;
+  if (d.n_rows == 0 || d.n0 == 0) return RS_OK;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  int64_t n_cx = 0;
+  const int64_t n_cells = rsint::cull_cells(d.n_rows, d.n0, &n_cx);
+  const int64_t n_coarse = rsint::cull_coarse_cells(d.n_rows, d.n0);
+  // stream-ordered workspace: [re-evaluation count | coarse count | kept count | re-evaluation list |
+  // coarse cell list | cell list]
+  const unsigned cap = g_certify ? rsint::recheck_capacity(d.n_rows * d.n0) : 0u;
+  const size_t coarse_off = 32 + sizeof(uint2) * (size_t)cap;
+  const size_t list_off = coarse_off + sizeof(unsigned) * (size_t)n_coarse;
+  void* ws = nullptr;
+  cudaError_t e = cudaMallocAsync(&ws, list_off + sizeof(unsigned) * (size_t)n_cells, s);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync (culled-shoot workspace)");
+  char* base = reinterpret_cast<char*>(ws);
+  unsigned* n_coarse_kept = reinterpret_cast<unsigned*>(base + 8);
+  unsigned* n_kept = reinterpret_cast<unsigned*>(base + 16);
+  unsigned* coarse = reinterpret_cast<unsigned*>(base + coarse_off);
+  unsigned* cells = reinterpret_cast<unsigned*>(base + list_off);
+  if (g_certify) {
+    d.rc_cap = cap;
+    d.rc_count = reinterpret_cast<unsigned int*>(base);
+    d.rc_list = reinterpret_cast<uint2*>(base + 32);
+  }
+  e = cudaMemsetAsync(base, 0, 32, s);
+  if (e == cudaSuccess)
+    e = rsint::launch_cull(d, w->hi[0], w->hi[1], coarse, n_coarse_kept, cells, n_kept,
+                           reinterpret_cast<unsigned long long*>(d_rays_shot), s);
+  if (e == cudaSuccess) {
+    const int64_t want = (n_cells + 3) / 4;
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)num_sms(f->device) * 2));
+    e = rsint::launch_shoot_cells(d, n_cx, cells, n_kept, grid, s);
+  }
+  if (e == cudaSuccess && g_certify)
+    e = rsint::launch_recheck(&d, nullptr, d.rc_list, d.rc_count, d.rc_cap, recheck_grid(f->device), s);
+  cudaError_t e2 = cudaFreeAsync(ws, s);
+  if (e == cudaSuccess) e = e2;
+  if (e != cudaSuccess) return cuda_fail(e, "culled shoot launch");
+  return RS_OK;
+}
+
 int rs_shoot(rs_field_t f, const rs_ray_grid* g, const rs_window* w, uint32_t* d_counts, uint64_t* d_out_of_window,
              void* stream) {
   if (!g) return fail(RS_EINVAL, "ray grid is NULL");

@@ -536,41 +536,14 @@ __device__ __forceinline__ float band_halfwidth(float sig, float lamabs, float x
 }
 
 // ----------------------------------------------------------------------------------------------
-// Ray tiles of a shoot call.  A CTA of WARPS warps covers WARPS consecutive grid rows (one per
-// warp) by 32 * RPT consecutive columns; lane l of a warp holds columns c0 + l + 32 k, k < RPT.
+// Eq. 6 and binning of a thread's RPT rays (ray k at grid column i_base + STRIDE k of call row
+// jrel): counts, the out-of-window count, and, with certified binning, the list of rays to
+// re-evaluate in float-float.  Every lane of the warp must call it (warp-aggregated atomics).
 // ----------------------------------------------------------------------------------------------
-template <int WARPS, int RPT>
-__host__ __device__ __forceinline__ int64_t shoot_tiles(int64_t n_rows, int64_t n0) {
-  const int64_t seg = 32 * RPT;
-  return ((n_rows + WARPS - 1) / WARPS) * ((n0 + seg - 1) / seg);
-}
-
-template <int WARPS, int RPT, int TILE, bool MASS>
-__device__ __forceinline__ bool shoot_tile(const ShootDesc& d, int64_t tile, LensSmem<TILE, WARPS>& sm,
-                                           PipeState& ps) {
-  constexpr int SEG = 32 * RPT;
-  const int64_t ncol = (d.n0 + SEG - 1) / SEG;
-  const int64_t trow = tile / ncol;
-  const int64_t tcol = tile - trow * ncol;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t jrel = trow * WARPS + warp;
-  const bool row_ok = jrel < d.n_rows;
-  const int64_t j = d.j_begin + (row_ok ? jrel : d.n_rows - 1);
-  const float x2r = ray_coord(j, d.sp1, d.or1);
-  float x1[RPT], x2[RPT];
-  bool valid[RPT];
-#pragma unroll
-  for (int k = 0; k < RPT; ++k) {
-    int64_t i = tcol * SEG + lane + 32 * k;
-    valid[k] = row_ok && i < d.n0;
-    if (i >= d.n0) i = d.n0 - 1;
-    x1[k] = ray_coord(i, d.sp0, d.or0);
-    x2[k] = x2r;
-  }
-  if (lane == 0) sm.x2row[warp] = x2r;  // read by build_row_table after the first tile barrier
-  double a1[RPT], a2[RPT];
-  float sig[RPT];
-  if (!deflect<RPT, TILE, MASS, true, WARPS>(d.f, x1, x2, a1, a2, sig, sm, ps)) return false;
+template <int RPT, int STRIDE>
+__device__ __forceinline__ void bin_rays(const ShootDesc& d, const float (&x1)[RPT], const float (&x2)[RPT],
+                                         const double (&a1)[RPT], const double (&a2)[RPT], const float (&sig)[RPT],
+                                         const bool (&valid)[RPT], int64_t jrel, int64_t i_base, int lane) {
   unsigned oow_lane = 0;
 #pragma unroll
   for (int k = 0; k < RPT; ++k) {
@@ -609,7 +582,7 @@ __device__ __forceinline__ bool shoot_tile(const ShootDesc& d, int64_t tile, Len
         if (need) {
           const unsigned slot = base + (unsigned)__popc(mask & ((1u << lane) - 1u));
           if (slot < d.rc_cap) {
-            const int64_t i = tcol * SEG + lane + 32 * k;
+            const int64_t i = i_base + STRIDE * k;
             d.rc_list[slot] = make_uint2((unsigned)d.field_id, (unsigned)(jrel * d.n0 + i));
             bin_now = false;  // counted by the float-float re-evaluation
           }
@@ -622,6 +595,46 @@ __device__ __forceinline__ bool shoot_tile(const ShootDesc& d, int64_t tile, Len
     oow_lane += __popc(miss);
   }
   if (d.oow != nullptr && lane == 0 && oow_lane != 0) atomicAdd(d.oow, (unsigned long long)oow_lane);
+}
+
+
+// ----------------------------------------------------------------------------------------------
+// Ray tiles of a shoot call.  A CTA of WARPS warps covers WARPS consecutive grid rows (one per
+// warp) by 32 * RPT consecutive columns; lane l of a warp holds columns c0 + l + 32 k, k < RPT.
+// ----------------------------------------------------------------------------------------------
+template <int WARPS, int RPT>
+__host__ __device__ __forceinline__ int64_t shoot_tiles(int64_t n_rows, int64_t n0) {
+  const int64_t seg = 32 * RPT;
+  return ((n_rows + WARPS - 1) / WARPS) * ((n0 + seg - 1) / seg);
+}
+
+template <int WARPS, int RPT, int TILE, bool MASS>
+__device__ __forceinline__ bool shoot_tile(const ShootDesc& d, int64_t tile, LensSmem<TILE, WARPS>& sm,
+                                           PipeState& ps) {
+  constexpr int SEG = 32 * RPT;
+  const int64_t ncol = (d.n0 + SEG - 1) / SEG;
+  const int64_t trow = tile / ncol;
+  const int64_t tcol = tile - trow * ncol;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t jrel = trow * WARPS + warp;
+  const bool row_ok = jrel < d.n_rows;
+  const int64_t j = d.j_begin + (row_ok ? jrel : d.n_rows - 1);
+  const float x2r = ray_coord(j, d.sp1, d.or1);
+  float x1[RPT], x2[RPT];
+  bool valid[RPT];
+#pragma unroll
+  for (int k = 0; k < RPT; ++k) {
+    int64_t i = tcol * SEG + lane + 32 * k;
+    valid[k] = row_ok && i < d.n0;
+    if (i >= d.n0) i = d.n0 - 1;
+    x1[k] = ray_coord(i, d.sp0, d.or0);
+    x2[k] = x2r;
+  }
+  if (lane == 0) sm.x2row[warp] = x2r;  // read by build_row_table after the first tile barrier
+  double a1[RPT], a2[RPT];
+  float sig[RPT];
+  if (!deflect<RPT, TILE, MASS, true, WARPS>(d.f, x1, x2, a1, a2, sig, sm, ps)) return false;
+  bin_rays<RPT, 32>(d, x1, x2, a1, a2, sig, valid, jrel, tcol * SEG + lane, lane);
   return true;
 }
 

@@ -57,6 +57,19 @@ cudaError_t launch_batch(int cfg, bool mass, const rsdev::ShootDesc* descs, cons
                          int* counter, int grid, cudaStream_t s);
 cudaError_t batch_blocks_per_sm(int cfg, bool mass, int* blocks);
 
+// Culled shooting (rs_cull.cu): cells of 16 x 16 rays, bounded first in groups of 4 x 4 cells.
+// cull_cells returns the number of 16 x 16 cells of a call (and the cells per row), cull_coarse_cells
+// the number of 64 x 64 cells; launch_cull appends the 64 x 64 cells that may reach the window to
+// `coarse` (count *n_coarse) and then the 16 x 16 cells of those that may to `list` (count *n_kept,
+// rays in *n_shot if not null), counting the rays of all others out of window; launch_shoot_cells
+// shoots the listed cells (grid: persistent CTAs of 128 threads).  Counters start at zero.
+int64_t cull_cells(int64_t n_rows, int64_t n0, int64_t* n_cx);
+int64_t cull_coarse_cells(int64_t n_rows, int64_t n0);
+cudaError_t launch_cull(const rsdev::ShootDesc& d, double hi0, double hi1, unsigned* coarse, unsigned* n_coarse,
+                        unsigned* list, unsigned* n_kept, unsigned long long* n_shot, cudaStream_t s);
+cudaError_t launch_shoot_cells(const rsdev::ShootDesc& d, int64_t n_cx, const unsigned* list, const unsigned* n_kept,
+                               int grid, cudaStream_t s);
+
 // Light curves (rs_lightcurve.cu): one descriptor per track with samples, in output order.
 struct LcTrack {
   const float* mu;          // map, float[np1][np0]
