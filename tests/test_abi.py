@@ -161,3 +161,28 @@ def test_light_curve_validation(rs):
     assert call([good], w=big) == rs.RS_EINVAL
     far = (rs._Window * 1)(rs._cwin(rs.Window((1e8, -1.0), (1e8 + 1e-3, 1.0), (64, 64))))
     assert call([good], w=far) == rs.RS_EINVAL                           # |lo| / pixel beyond 2^30
+
+
+def test_culled_shoot_validation(rs):
+    lib = rs.load()
+    g = rs._cgrid(rs.RayGrid((0.0, 0.0), (1.0, 1.0), (4, 4)))
+    w = rs._cwin(rs.Window((-1.0, -1.0), (1.0, 1.0), (4, 4)))
+    fake = ctypes.c_void_p(1)  # never dereferenced: validation fails first
+    assert lib.rs_shoot_culled(None, ctypes.byref(g), 0, 4, ctypes.byref(w), ctypes.c_void_p(16), None, None,
+                               None) == rs.RS_EINVAL
+    assert lib.rs_shoot_culled(fake, ctypes.byref(g), 3, 9, ctypes.byref(w), ctypes.c_void_p(16), None, None,
+                               None) == rs.RS_EINVAL
+    assert lib.rs_shoot_culled(fake, ctypes.byref(g), 0, 4, ctypes.byref(w), None, None, None, None) == rs.RS_EINVAL
+    bad = rs._cwin(rs.Window((1.0, -1.0), (1.0, 1.0), (4, 4)))
+    assert lib.rs_shoot_culled(fake, ctypes.byref(g), 0, 4, ctypes.byref(bad), ctypes.c_void_p(16), None, None,
+                               None) == rs.RS_EINVAL
+
+
+def test_zoom_geometry(rs):
+    g = rs.RayGrid((-10.0 + 0.01, -10.0 + 0.01), (0.02, 0.02), (1000, 1000))
+    z = rs.zoom_grid(g, 4)
+    assert z.n == (4000, 4000) and abs(z.spacing[0] - 0.005) < 1e-15
+    assert abs(z.origin[0] - (-10.0 + 0.0025)) < 1e-12           # cell-centred sub-rays
+    w = rs.Window((-2.0, -2.0), (2.0, 2.0), (256, 256))
+    zw = rs.zoom_window(w, (0.0, -1.0), (1.0, 0.5), 4)
+    assert zw.npix == (256, 384)
