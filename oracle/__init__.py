@@ -9,8 +9,9 @@ over rays, no fused multiply-add, no fast-math); this module compiles it with
 gcc and exposes it through ctypes with numpy arrays.  What each function
 computes and which passage of the paper it follows is stated in the C file:
 Eq. 2 with the per-lens steps of Appendix A (deflection), Eq. 6 (lens map with
-kappa_c and gamma), Eq. 4 (mu = N / N_av), Section 2.1 step 4 (binning) and
-the light curves of Section 1 (a source profile moved across the map).
+kappa_c and gamma), Eq. 4 (mu = N / N_av), Section 2.1 step 4 (binning),
+the light curves of Section 1 (a source profile moved across the map) and the
+moving lenses of Section 4 (positions per time step).
 
 Parity status: every function here is pinned by ``tests/test_oracle_pins.py``
 (exact rational brute force, zero-lens and linear-map lattice counts, the
@@ -18,7 +19,9 @@ single point-lens magnification law, mirror symmetry, conservation,
 superposition and the 2-D Gauss law of a uniform disc); ``light_curve`` by
 ``tests/test_oracle_lightcurve.py`` (constant and linear maps, Gauss circle
 lattice counts of the disc profile, the magnitude scale, and a point lens seen
-through a Gaussian source against Gauss-Hermite quadrature of the analytic law).
+through a Gaussian source against Gauss-Hermite quadrature of the analytic law);
+``lens_positions`` by ``tests/test_oracle_motion.py`` (rest and still cases, and
+the translation covariance of a moving lens's map).
 """
 from __future__ import annotations
 
@@ -83,6 +86,8 @@ def load_library(path: str):
     lib.oracle_set_num_threads.restype = None
     lib.oracle_light_curve.argtypes = [vp, vp, vp, vp, ctypes.c_int, ctypes.c_double, vp, vp, ctypes.c_int64, vp, vp]
     lib.oracle_light_curve.restype = None
+    lib.oracle_lens_positions.argtypes = [vp, vp, ctypes.c_int64, ctypes.c_double, vp]
+    lib.oracle_lens_positions.restype = None
     return lib
 
 
@@ -210,6 +215,18 @@ def light_curve(mu, lo, hi, profile, s, y0, step, n):
     lib.oracle_light_curve(_ptr(m), _ptr(npx), _ptr(l), _ptr(h), int(profile), float(s), _ptr(a), _ptr(b),
                            int(n), _ptr(out), _ptr(mag))
     return out, mag
+
+
+def lens_positions(lens_xy, vel_xy, t):
+    """Positions float32 [n, 2] of lenses moving in straight lines, at time t (see the C file)."""
+    lib = _load()
+    xy = np.ascontiguousarray(np.asarray(lens_xy, dtype=np.float32).reshape(-1, 2))
+    v = np.ascontiguousarray(np.asarray(vel_xy, dtype=np.float32).reshape(-1, 2))
+    if xy.shape != v.shape:
+        raise ValueError("positions and velocities differ in shape")
+    out = np.empty_like(xy)
+    lib.oracle_lens_positions(_ptr(xy), _ptr(v), int(xy.shape[0]), float(t), _ptr(out))
+    return out
 
 
 # Convenience wrappers over rs_inputs.Field objects --------------------------------

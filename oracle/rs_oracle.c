@@ -277,3 +277,17 @@ void oracle_light_curve(const double* mu, const int32_t npix[2], const double lo
     if (mag_out) mag_out[k] = -2.5 * log10(m);
   }
 }
+
+/*
+ * Lens positions of a moving field at time t (Section 4: the motion of individual stars changes
+ * the caustic network; maps are then made per time step).  The paper gives no formula; the reading
+ * used here: straight-line motion, x_i(t) = x_i + v_i t per axis, evaluated in double (product,
+ * then sum, no fma) from the float32 position and velocity and rounded to float32, the precision of
+ * the lens arrays.  xy, vel, out: float [2 n], interleaved (x1, x2) per lens.
+ */
+void oracle_lens_positions(const float* xy, const float* vel, int64_t n, double t, float* out) {
+  for (int64_t i = 0; i < 2 * n; ++i) {
+    const double moved = (double)xy[i] + (double)vel[i] * t;
+    out[i] = (float)moved;
+  }
+}
