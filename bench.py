@@ -367,6 +367,11 @@ def run_ours(args):
         zoom = run_zoom(rs, torch, device, stream, spec)
         zoom["culled_full_map"] = run_zoom(rs, torch, device, stream, spec, factor=1, quarter=False)
 
+    # ---------------- a time series of maps with moving lenses (one batch launch per 16 steps)
+    frames = None
+    if not args.no_frames and world == 1:
+        frames = run_frames(rs, torch, device, stream, spec)
+
     # ---------------- CPU baseline (oracle, bounded sample)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -406,6 +411,7 @@ def run_ours(args):
         "batched": batched,
         "light_curves": light,
         "zoom": zoom,
+        "frames": frames,
         "wall_s_timed_region": wall,
     }
     print(json.dumps(line), flush=True)
@@ -594,9 +600,52 @@ def run_section(args):
             rs.rs_set_launch_config(spec.masses is not None, b_, r_)
         out = {"zoom": run_zoom(rs, torch, device, stream, spec),
                "culled_full_map": run_zoom(rs, torch, device, stream, spec, factor=1, quarter=False)}
+    elif args.section == "frames":
+        spec = workload(args.workload, seed=0)
+        out = {"frames": run_frames(rs, torch, device, stream, spec)}
     else:
         out = {"light_curves": run_light_curves(rs, torch, device, stream)}
     print(json.dumps(out), flush=True)
+
+
+def run_frames(rs, torch, device, stream, spec, n_frames=16, dt=1.0, sigma_v=0.1, reps=2):
+    """A time series of maps of the workload field with moving lenses: n_frames moving fields in one
+    batch, each stepped to its own time before every launch."""
+    vel = ri.lens_velocities(spec.n_lens, sigma_v, seed=7)
+    frames = [rs.Field(spec.lens_xy, spec.masses, spec.kappa_c, spec.gamma, stream, velocities=vel)
+              for _ in range(n_frames)]
+    b = rs.Batch(frames, [spec.grid] * n_frames, [spec.window] * n_frames)
+
+    def step(r):
+        for k, fr in enumerate(frames):
+            fr.set_time((r * n_frames + k) * dt, stream)
+        b.launch(stream)
+
+    step(0)
+    torch.cuda.synchronize(device)
+    # check one frame against a plain shoot of a static field at the moved positions (bitwise)
+    import oracle
+    xy = oracle.lens_positions(spec.lens_xy, vel, (n_frames - 1) * dt)
+    st = rs.Field(xy, spec.masses, spec.kappa_c, spec.gamma, stream)
+    ref = st.shoot(spec.grid, spec.window, stream=stream)
+    torch.cuda.synchronize(device)
+    same = bool(torch.equal(ref, b.counts[n_frames - 1]))
+    st.close()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for r in range(1, reps + 1):
+        step(r)
+    e1.record(stream)
+    torch.cuda.synchronize(device)
+    t = e0.elapsed_time(e1) / 1e3 / reps
+    b.close()
+    for fr in frames:
+        fr.close()
+    return {"workload": f"{args_workload_name(spec)} with Gaussian lens velocities sigma {sigma_v} per axis, "
+                        f"{n_frames} time steps of {dt} per batch launch",
+            "frames_per_s": n_frames / t, "ms_per_frame": t / n_frames * 1e3,
+            "interactions_per_s": n_frames * spec.interactions / t, "frame_equals_static_field_at_moved_positions": same,
+            "reps": reps}
 
 
 def args_workload_name(spec):
@@ -614,7 +663,8 @@ def main():
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-light-curves", action="store_true")
     ap.add_argument("--no-zoom", action="store_true")
-    ap.add_argument("--section", choices=["zoom", "light-curves"], default=None,
+    ap.add_argument("--no-frames", action="store_true")
+    ap.add_argument("--section", choices=["zoom", "light-curves", "frames"], default=None,
                     help="run one secondary measurement alone and print its JSON object (for profiling)")
     ap.add_argument("--batch-reps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -103,6 +103,25 @@ int rs_create_field(const float* lens_xy, const float* masses, int64_t n_lens, d
 /* rs_destroy_field -- release a field (synchronises its device first).  NULL is a no-op. */
 int rs_destroy_field(rs_field_t f);
 
+/*
+ * Moving lenses (Section 4: the stars move, so the caustic network and the map change with time;
+ * one map per time step).  rs_create_moving_field -- as rs_create_field, plus vel_xy (float[2*n_lens],
+ * interleaved (v1, v2) per lens, finite; host or device as inputs_on_device) in coordinate units per
+ * unit time.  The field keeps positions and velocities at t = 0 on the device (16 extra bytes per
+ * lens) and starts at t = 0.  Synchronous.
+ * rs_field_set_time -- move the field's lenses to time t, in place and stream-ordered:
+ *   x_i(t) = (float)((double)x_i + (double)v_i * t) per axis (product, then sum, no fused multiply-add).
+ *   Work already enqueued on `stream` sees the old positions, work enqueued after it the new ones;
+ *   work on other streams must be ordered by the caller.  Batches that include the field read its
+ *   lenses at launch, so a planned batch of moving fields can be replayed after each time step.
+ *   Errors: RS_EINVAL (not a moving field, t not finite, or |x| + |v| |t| beyond 1e9).
+ * rs_field_time -- the field's current time.
+ */
+int rs_create_moving_field(const float* lens_xy, const float* vel_xy, const float* masses, int64_t n_lens,
+                           double kappa_c, double gamma, int inputs_on_device, void* stream, rs_field_t* out);
+int rs_field_set_time(rs_field_t f, double t, void* stream);
+int rs_field_time(rs_field_t f, double* t);
+
 /* Number of lenses, and whether the field carries per-lens masses (1) or unit masses (0). */
 int rs_field_info(rs_field_t f, int64_t* n_lens, int* has_masses);
 

@@ -41,6 +41,7 @@ EXPORTED_SYMBOLS = (
     "rs_field_status", "rs_last_error", "rs_version", "rs_set_launch_config", "rs_get_launch_config",
     "rs_launch_configs", "rs_trace_certified", "rs_set_certified_binning", "rs_get_certified_binning",
     "rs_selftest_bounded_wait", "rs_shoot_rows_noalloc", "rs_light_curves", "rs_shoot_culled",
+    "rs_create_moving_field", "rs_field_set_time", "rs_field_time",
     "rs_light_curve_plan_create", "rs_light_curve_plan_samples", "rs_light_curve_plan_launch",
     "rs_light_curve_plan_destroy",
 )
@@ -118,6 +119,9 @@ def load():
     gp, wp = ctypes.POINTER(_Grid), ctypes.POINTER(_Window)
     sig = {
         "rs_create_field": ([vp, vp, i64, dbl, dbl, i32, vp, ctypes.POINTER(vp)], i32),
+        "rs_create_moving_field": ([vp, vp, vp, i64, dbl, dbl, i32, vp, ctypes.POINTER(vp)], i32),
+        "rs_field_set_time": ([vp, dbl, vp], i32),
+        "rs_field_time": ([vp, ctypes.POINTER(dbl)], i32),
         "rs_destroy_field": ([vp], i32),
         "rs_field_info": ([vp, ctypes.POINTER(i64), ctypes.POINTER(i32)], i32),
         "rs_shoot": ([vp, gp, wp, vp, vp, vp], i32),
@@ -213,6 +217,34 @@ def rs_last_error() -> str:
     return load().rs_last_error().decode(errors="replace")
 
 
+def _lens_inputs(lens_xy, masses, vel_xy=None):
+    """Contiguous float32 copies (device tensors stay on the device) and their pointers."""
+    on_dev = isinstance(lens_xy, torch.Tensor) and lens_xy.is_cuda
+    if on_dev:
+        xy = lens_xy.detach().to(torch.float32).contiguous()
+        n = xy.numel() // 2
+        m = None if masses is None else masses.detach().to(device=xy.device, dtype=torch.float32).contiguous()
+        v = None if vel_xy is None else torch.as_tensor(vel_xy).detach().to(device=xy.device,
+                                                                             dtype=torch.float32).contiguous()
+        ptr = lambda a: None if a is None else a.data_ptr()  # noqa: E731
+        size = lambda a: a.numel()  # noqa: E731
+    else:
+        import numpy as np
+
+        def host(a):
+            return None if a is None else np.ascontiguousarray(
+                np.asarray(a.cpu() if isinstance(a, torch.Tensor) else a, dtype=np.float32))
+        xy, m, v = host(lens_xy), host(masses), host(vel_xy)
+        n = xy.size // 2
+        ptr = lambda a: None if a is None or a.size == 0 else a.ctypes.data  # noqa: E731
+        size = lambda a: a.size  # noqa: E731
+    if m is not None and size(m) != n:
+        raise ValueError("masses length differs from lens count")
+    if v is not None and size(v) != 2 * n:
+        raise ValueError("velocities must have one (v1, v2) pair per lens")
+    return on_dev, n, (xy, m, v), (ptr(xy), ptr(m), ptr(v))
+
+
 def rs_create_field(lens_xy, masses, kappa_c: float, gamma: float, stream=None) -> int:
     """Create a field from lens positions [n, 2] and masses [n] (or None for unit masses).
 
@@ -220,26 +252,7 @@ def rs_create_field(lens_xy, masses, kappa_c: float, gamma: float, stream=None) 
     tensors are read on the device.  Returns the opaque handle (int).
     """
     lib = load()
-    on_dev = isinstance(lens_xy, torch.Tensor) and lens_xy.is_cuda
-    keep = []
-    if on_dev:
-        xy = lens_xy.detach().to(torch.float32).contiguous()
-        n = xy.numel() // 2
-        m = None if masses is None else masses.detach().to(device=xy.device, dtype=torch.float32).contiguous()
-        keep += [xy, m]
-        pxy, pm = xy.data_ptr(), (None if m is None else m.data_ptr())
-    else:
-        import numpy as np
-        xy = np.ascontiguousarray(np.asarray(lens_xy.cpu() if isinstance(lens_xy, torch.Tensor) else lens_xy,
-                                             dtype=np.float32))
-        n = xy.size // 2
-        m = None if masses is None else np.ascontiguousarray(
-            np.asarray(masses.cpu() if isinstance(masses, torch.Tensor) else masses, dtype=np.float32))
-        keep += [xy, m]
-        pxy = xy.ctypes.data if n > 0 else None
-        pm = None if m is None else m.ctypes.data
-    if m is not None and (m.numel() if on_dev else m.size) != n:
-        raise ValueError("masses length differs from lens count")
+    on_dev, n, keep, (pxy, pm, _) = _lens_inputs(lens_xy, masses)
     h = ctypes.c_void_p()
     st = _stream(stream)
     rc = lib.rs_create_field(pxy, pm, n, float(kappa_c), float(gamma), 1 if on_dev else 0, st, ctypes.byref(h))
@@ -247,6 +260,27 @@ def rs_create_field(lens_xy, masses, kappa_c: float, gamma: float, stream=None) 
     if on_dev:
         torch.cuda.ExternalStream(st).synchronize()  # device inputs may be freed after return
     return h.value
+
+
+def rs_create_moving_field(lens_xy, vel_xy, masses, kappa_c: float, gamma: float, stream=None) -> int:
+    """A field whose lenses move with velocities vel_xy [n, 2]; starts at t = 0 (see rs_field_set_time)."""
+    lib = load()
+    on_dev, n, keep, (pxy, pm, pv) = _lens_inputs(lens_xy, masses, vel_xy)
+    h = ctypes.c_void_p()
+    st = _stream(stream)
+    _check(lib.rs_create_moving_field(pxy, pv, pm, n, float(kappa_c), float(gamma), 1 if on_dev else 0, st,
+                                      ctypes.byref(h)), "rs_create_moving_field")
+    return h.value
+
+
+def rs_field_set_time(handle: int, t: float, stream=None) -> None:
+    _check(load().rs_field_set_time(handle, float(t), _stream(stream)), "rs_field_set_time")
+
+
+def rs_field_time(handle: int) -> float:
+    t = ctypes.c_double()
+    _check(load().rs_field_time(handle, ctypes.byref(t)), "rs_field_time")
+    return float(t.value)
 
 
 def rs_destroy_field(handle: int) -> None:
@@ -506,9 +540,21 @@ def rs_launch_configs():
 class Field:
     """Owning wrapper of an rs_field handle."""
 
-    def __init__(self, lens_xy, masses=None, kappa_c: float = 0.0, gamma: float = 0.0, stream=None):
-        self.handle = rs_create_field(lens_xy, masses, kappa_c, gamma, stream)
+    def __init__(self, lens_xy, masses=None, kappa_c: float = 0.0, gamma: float = 0.0, stream=None,
+                 velocities=None):
+        if velocities is None:
+            self.handle = rs_create_field(lens_xy, masses, kappa_c, gamma, stream)
+        else:
+            self.handle = rs_create_moving_field(lens_xy, velocities, masses, kappa_c, gamma, stream)
         self.kappa_c, self.gamma = float(kappa_c), float(gamma)
+
+    def set_time(self, t: float, stream=None):
+        """Move the lenses of a moving field to time t (stream-ordered, in place)."""
+        rs_field_set_time(self.handle, t, stream)
+
+    @property
+    def time(self) -> float:
+        return rs_field_time(self.handle)
 
     @classmethod
     def from_spec(cls, spec, stream=None):

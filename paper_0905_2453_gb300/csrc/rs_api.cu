@@ -25,6 +25,9 @@ struct rs_field {
   unsigned int* status;
   double kappa_c, gamma;
   FieldDev dev;
+  // moving fields: {x1, x2, v1, v2} at t = 0 per lens, bounds of |x| and |v|, current time
+  float4* motion = nullptr;
+  double max_x = 0.0, max_v = 0.0, time = 0.0;
 };
 
 struct rs_batch {
@@ -152,6 +155,27 @@ __global__ void pack_lenses_kernel(const float* __restrict__ xy, const float* __
       lens4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
       if (mass2) mass2[i] = make_float2(0.f, 0.f);
     }
+  }
+}
+
+// Moving fields: {x1, x2, v1, v2} per lens at t = 0.
+__global__ void motion_pack_kernel(const float* __restrict__ xy, const float* __restrict__ v, int64_t n,
+                                   float4* __restrict__ motion) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const float2 p = reinterpret_cast<const float2*>(xy)[i];
+    const float2 q = reinterpret_cast<const float2*>(v)[i];
+    motion[i] = make_float4(p.x, p.y, q.x, q.y);
+  }
+}
+
+// Lens positions at time t: x + v t in double (product, then sum, no fma), rounded to float32; the
+// packed layout of pack_lenses_kernel (padding lenses untouched).
+__global__ void move_lenses_kernel(const float4* __restrict__ motion, int64_t n, double t, float4* __restrict__ lens4) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const float4 m = motion[i];
+    const float x1 = __double2float_rn(__dadd_rn((double)m.x, __dmul_rn((double)m.z, t)));
+    const float x2 = __double2float_rn(__dadd_rn((double)m.y, __dmul_rn((double)m.w, t)));
+    lens4[i] = make_float4(x1, x1, x2, x2);
   }
 }
 
@@ -469,7 +493,95 @@ int rs_destroy_field(rs_field_t f) {
   cudaFree(f->lens4);
   cudaFree(f->mass2);
   cudaFree(f->status);
+  cudaFree(f->motion);
   delete f;
+  return RS_OK;
+}
+
+int rs_create_moving_field(const float* lens_xy, const float* vel_xy, const float* masses, int64_t n_lens,
+                           double kappa_c, double gamma, int inputs_on_device, void* stream, rs_field_t* out) {
+  if (!out) return fail(RS_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (n_lens > 0 && !vel_xy) return fail(RS_EINVAL, "vel_xy is NULL");
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  // bounds of |x| and |v| for the coordinate check of rs_field_set_time (host copies of device inputs)
+  std::vector<float> hxy, hv;
+  const float* pxy = lens_xy;
+  const float* pv = vel_xy;
+  if (inputs_on_device && n_lens > 0) {
+    hxy.resize(2 * n_lens);
+    hv.resize(2 * n_lens);
+    cudaError_t e = cudaMemcpy(hxy.data(), lens_xy, sizeof(float) * 2 * n_lens, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(hv.data(), vel_xy, sizeof(float) * 2 * n_lens, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy (moving-field bounds)");
+    pxy = hxy.data();
+    pv = hv.data();
+  }
+  double max_x = 0.0, max_v = 0.0;
+  for (int64_t i = 0; i < 2 * n_lens; ++i) {
+    if (!finite_coord((double)pxy[i])) return fail(RS_EINVAL, "lens coordinate %lld not finite or beyond 1e9", (long long)i);
+    if (!std::isfinite(pv[i])) return fail(RS_EINVAL, "velocity %lld not finite", (long long)i);
+    max_x = std::max(max_x, std::fabs((double)pxy[i]));
+    max_v = std::max(max_v, std::fabs((double)pv[i]));
+  }
+  rs_field_t f = nullptr;
+  int rc = rs_create_field(lens_xy, masses, n_lens, kappa_c, gamma, inputs_on_device, stream, &f);
+  if (rc != RS_OK) return rc;
+  float* tmp = nullptr;
+  cudaError_t e = cudaMalloc(&f->motion, sizeof(float4) * (size_t)std::max<int64_t>(n_lens, 1));
+  if (e == cudaSuccess && n_lens > 0) {
+    const float* dxy = lens_xy;
+    const float* dv = vel_xy;
+    if (!inputs_on_device) {
+      e = cudaMalloc(&tmp, sizeof(float) * 4 * n_lens);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(tmp, lens_xy, sizeof(float) * 2 * n_lens, cudaMemcpyHostToDevice, s);
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(tmp + 2 * n_lens, vel_xy, sizeof(float) * 2 * n_lens, cudaMemcpyHostToDevice, s);
+      dxy = tmp;
+      dv = tmp + 2 * n_lens;
+    }
+    if (e == cudaSuccess) {
+      const int threads = 256;
+      const int blocks = (int)std::min<int64_t>((n_lens + threads - 1) / threads, (int64_t)num_sms(f->device) * 16);
+      motion_pack_kernel<<<blocks, threads, 0, s>>>(dxy, dv, n_lens, f->motion);
+      e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // staging consumed; positions ready
+  }
+  cudaFree(tmp);
+  if (e != cudaSuccess) {
+    rc = cuda_fail(e, "moving-field upload");
+    rs_destroy_field(f);
+    return rc;
+  }
+  f->max_x = max_x;
+  f->max_v = max_v;
+  *out = f;
+  return RS_OK;
+}
+
+int rs_field_set_time(rs_field_t f, double t, void* stream) {
+  if (!f) return fail(RS_EINVAL, "field is NULL");
+  if (!f->motion) return fail(RS_EINVAL, "field has no velocities (create it with rs_create_moving_field)");
+  if (!std::isfinite(t)) return fail(RS_EINVAL, "time must be finite");
+  if (!(f->max_x + f->max_v * std::fabs(t) <= kCoordLimit))
+    return fail(RS_EINVAL, "lens coordinates at t = %g may exceed 1e9", t);
+  int rc;
+  if ((rc = check_field_device(f)) != RS_OK) return rc;
+  f->time = t;
+  if (f->n_lens == 0) return RS_OK;
+  const int threads = 256;
+  const int blocks = (int)std::min<int64_t>((f->n_lens + threads - 1) / threads, (int64_t)num_sms(f->device) * 16);
+  move_lenses_kernel<<<blocks, threads, 0, reinterpret_cast<cudaStream_t>(stream)>>>(f->motion, f->n_lens, t,
+                                                                                     f->lens4);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "move_lenses_kernel launch");
+  return RS_OK;
+}
+
+int rs_field_time(rs_field_t f, double* t) {
+  if (!f || !t) return fail(RS_EINVAL, "NULL argument");
+  *t = f->time;
   return RS_OK;
 }
 

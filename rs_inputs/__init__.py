@@ -294,3 +294,10 @@ def light_curve_workload(n_maps: int = 64, tracks_per_map: int = 16, n_samples: 
             th = float(rng.uniform(0.0, 2.0 * np.pi))
             tracks.append(Track(m, y0, (0.25 * px * math.cos(th), 0.25 * px * math.sin(th)), n_samples))
     return maps, wins, tracks, 2.0 * px
+
+
+def lens_velocities(n: int, sigma_v: float, seed: int) -> np.ndarray:
+    """Isotropic Gaussian lens velocities, float32 [n, 2], standard deviation sigma_v per axis
+    (Einstein radii per unit time): the random stellar motions of a time series of maps."""
+    rng = np.random.default_rng([seed, 2])
+    return (rng.normal(size=(n, 2)) * sigma_v).astype(np.float32)
