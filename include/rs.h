@@ -163,6 +163,27 @@ int rs_shoot_culled(rs_field_t f, const rs_ray_grid* g, int64_t row_begin, int64
                     uint32_t* d_counts, uint64_t* d_out_of_window, uint64_t* d_rays_shot, void* stream);
 
 /*
+ * rs_shoot_staged -- rs_shoot_rows for a field given as n_parts lens partitions (Section 3.3's
+ * billion-lens scheme: the deflection of every ray is summed one partition at a time, the
+ * partially deflected rays carried in device memory between the passes, and the rays are mapped
+ * and binned after the last partition).  For fields of 2^31 lenses or more, or lenses held as
+ * shards.  The lens order is partition 0's lenses, then partition 1's, ...; every partition but
+ * the last must hold a multiple of 256 lenses, and all share device, mass mode, kappa_c and gamma.
+ * The carried state is the shoot kernel's own accumulator set (24 bytes per ray, stream-ordered
+ * allocation; rays are processed in row blocks of at most 2 GiB of state), so the float32
+ * deflections, error bands and counts equal those of one rs_shoot_rows over a single field
+ * holding all the lenses, bit for bit; with certified binning on, the listed rays are
+ * re-evaluated in float-float partition by partition (same guarantee as rs_shoot_rows).
+ * Other arguments, accumulation and errors as rs_shoot_rows.
+ */
+int rs_shoot_staged(int n_parts, const rs_field_t* parts, const rs_ray_grid* g, int64_t row_begin, int64_t row_end,
+                    const rs_window* w, uint32_t* d_counts, uint64_t* d_out_of_window, void* stream);
+
+/* Device memory budget (bytes, >= 1 MiB; default 2 GiB) for the carried per-ray state of
+ * rs_shoot_staged: calls whose state would exceed it run in row blocks (same results). */
+int rs_set_staged_state_budget(uint64_t bytes);
+
+/*
  * rs_trace -- source positions of listed rays through the float32 path, for checks.
  *   d_ray_ij : int64[2*k] device, (i, j) per ray (each within the grid).
  *   d_y      : double[2*k] device, receives (y1, y2) per ray (Eq. 6).

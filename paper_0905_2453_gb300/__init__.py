@@ -41,7 +41,8 @@ EXPORTED_SYMBOLS = (
     "rs_field_status", "rs_last_error", "rs_version", "rs_set_launch_config", "rs_get_launch_config",
     "rs_launch_configs", "rs_trace_certified", "rs_set_certified_binning", "rs_get_certified_binning",
     "rs_selftest_bounded_wait", "rs_shoot_rows_noalloc", "rs_light_curves", "rs_shoot_culled",
-    "rs_create_moving_field", "rs_field_set_time", "rs_field_time",
+    "rs_create_moving_field", "rs_field_set_time", "rs_field_time", "rs_shoot_staged",
+    "rs_set_staged_state_budget",
     "rs_light_curve_plan_create", "rs_light_curve_plan_samples", "rs_light_curve_plan_launch",
     "rs_light_curve_plan_destroy",
 )
@@ -133,6 +134,8 @@ def load():
         "rs_selftest_bounded_wait": ([i64, ctypes.POINTER(i32)], i32),
         "rs_shoot_rows_noalloc": ([vp, gp, i64, i64, wp, vp, vp, vp], i32),
         "rs_shoot_culled": ([vp, gp, i64, i64, wp, vp, vp, vp, vp], i32),
+        "rs_shoot_staged": ([i32, vp, gp, i64, i64, wp, vp, vp, vp], i32),
+        "rs_set_staged_state_budget": ([ctypes.c_uint64], i32),
         "rs_magnification": ([vp, gp, wp, vp, vp], i32),
         "rs_light_curves": ([i32, vp, vp, i32, dbl, i32, vp, vp, vp, vp], i32),
         "rs_light_curve_plan_create": ([i32, vp, vp, i32, dbl, i32, vp, ctypes.POINTER(vp)], i32),
@@ -333,6 +336,22 @@ def rs_shoot_culled(handle: int, grid, row_begin: int, row_end: int, window, cou
     g, w = _cgrid(grid), _cwin(window)
     _check(load().rs_shoot_culled(handle, ctypes.byref(g), int(row_begin), int(row_end), ctypes.byref(w), pc, po, pr,
                                   _stream(stream)), "rs_shoot_culled")
+
+
+def rs_shoot_staged(handles, grid, row_begin: int, row_end: int, window, counts, out_of_window=None, stream=None):
+    """Shoot a field given as lens partitions (handles, in lens order; all but the last a multiple of 256)."""
+    n = len(handles)
+    H = (ctypes.c_void_p * max(1, n))(*handles)
+    npx = int(window.npix[0]) * int(window.npix[1])
+    pc = _dptr(counts, _COUNT_DTYPES, "counts", npx)
+    po = _dptr(out_of_window, _OOW_DTYPES, "out_of_window", 1)
+    g, w = _cgrid(grid), _cwin(window)
+    _check(load().rs_shoot_staged(n, H, ctypes.byref(g), int(row_begin), int(row_end), ctypes.byref(w), pc, po,
+                                  _stream(stream)), "rs_shoot_staged")
+
+
+def rs_set_staged_state_budget(nbytes: int) -> None:
+    _check(load().rs_set_staged_state_budget(int(nbytes)), "rs_set_staged_state_budget")
 
 
 def rs_trace(handle: int, grid, ray_ij: torch.Tensor, y: torch.Tensor, alpha: torch.Tensor = None,

@@ -67,6 +67,8 @@ thread_local std::string g_err;
 int g_cfg[2] = {rsint::kDefaultCfg, rsint::kDefaultCfg};
 // Certified binning (float-float re-evaluation of rays inside their error band of a pixel edge).
 int g_certify = 1;
+// Device memory for the per-ray state of a staged (lens-partitioned) shoot; larger calls run in row blocks.
+size_t g_staged_budget = (size_t)2 << 30;
 
 int recheck_grid(int device) {
   int v = 0;
@@ -696,6 +698,76 @@ int rs_shoot_culled(rs_field_t f, const rs_ray_grid* g, int64_t row_begin, int64
   return RS_OK;
 }
 
+int rs_shoot_staged(int n_parts, const rs_field_t* parts, const rs_ray_grid* g, int64_t row_begin, int64_t row_end,
+                    const rs_window* w, uint32_t* d_counts, uint64_t* d_out_of_window, void* stream) {
+  if (n_parts < 1 || !parts) return fail(RS_EINVAL, "need n_parts >= 1 lens partitions");
+  for (int p = 0; p < n_parts; ++p) {
+    if (!parts[p]) return fail(RS_EINVAL, "partition %d is NULL", p);
+    const rs_field* a = parts[p];
+    const rs_field* b = parts[0];
+    if (a->device != b->device || a->dev.has_mass != b->dev.has_mass || a->kappa_c != b->kappa_c ||
+        a->gamma != b->gamma)
+      return fail(RS_EINVAL, "partition %d differs from partition 0 in device, mass mode, kappa_c or gamma", p);
+    if (p + 1 < n_parts && a->n_lens % rsdev::kRenorm != 0)
+      return fail(RS_EINVAL, "partition %d holds %lld lenses: all but the last must hold a multiple of %d", p,
+                  (long long)a->n_lens, rsdev::kRenorm);
+  }
+  int rc;
+  if ((rc = check_grid(g)) != RS_OK) return rc;
+  if ((rc = check_window(w)) != RS_OK) return rc;
+  if (!d_counts) return fail(RS_EINVAL, "d_counts is NULL");
+  if (row_begin < 0 || row_end < row_begin || row_end > g->n[1])
+    return fail(RS_EINVAL, "row range [%lld, %lld) outside [0, %lld]", (long long)row_begin, (long long)row_end,
+                (long long)g->n[1]);
+  if ((rc = check_field_device(parts[0])) != RS_OK) return rc;
+  ShootDesc d;
+  if ((rc = fill_desc(parts[0], g, row_begin, row_end, w, d_counts, d_out_of_window, &d)) != RS_OK) return rc;
+  if (d.n_rows == 0 || d.n0 == 0) return RS_OK;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  // ray blocks whose carried state fits the budget (the state is 24 bytes per ray, padded to tiles)
+  const size_t budget = g_staged_budget;
+  const size_t per4 = rsint::staged_state_bytes(4, d.n0);
+  const int64_t rows_blk = std::max<int64_t>(4, (int64_t)(budget / per4) * 4);
+  const int64_t rows_max = std::min<int64_t>(rows_blk, d.n_rows);
+  const size_t state_bytes = rsint::staged_state_bytes(rows_max, d.n0);
+  const unsigned cap = g_certify ? rsint::recheck_capacity(rows_max * d.n0) : 0u;
+  const size_t list_off = (state_bytes + 255) / 256 * 256;
+  const size_t ff_off = list_off + 16 + sizeof(uint2) * (size_t)cap;
+  void* ws = nullptr;
+  cudaError_t e = cudaMallocAsync(&ws, ff_off + sizeof(float4) * (size_t)cap, s);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync (staged-shoot workspace)");
+  char* base = reinterpret_cast<char*>(ws);
+  uint64_t* state = reinterpret_cast<uint64_t*>(base);
+  float4* ff = reinterpret_cast<float4*>(base + ff_off);
+  if (g_certify) {
+    d.rc_cap = cap;
+    d.rc_count = reinterpret_cast<unsigned int*>(base + list_off);
+    d.rc_list = reinterpret_cast<uint2*>(base + list_off + 16);
+  }
+  const int rgrid = recheck_grid(parts[0]->device);
+  for (int64_t r0 = 0; r0 < d.n_rows && e == cudaSuccess; r0 += rows_blk) {
+    ShootDesc db = d;
+    db.j_begin = d.j_begin + r0;
+    db.n_rows = std::min<int64_t>(rows_blk, d.n_rows - r0);
+    if (g_certify) e = cudaMemsetAsync(db.rc_count, 0, sizeof(unsigned int), s);
+    for (int p = 0; p < n_parts && e == cudaSuccess; ++p) {
+      db.f = parts[p]->dev;
+      e = rsint::launch_staged(db, state, p == 0, p == n_parts - 1, s);
+    }
+    if (g_certify) {
+      for (int p = 0; p < n_parts && e == cudaSuccess; ++p) {
+        db.f = parts[p]->dev;
+        e = rsint::launch_recheck_part(db, db.rc_list, db.rc_count, db.rc_cap, ff, p == 0, rgrid, s);
+      }
+      if (e == cudaSuccess) e = rsint::launch_recheck_bin(db, db.rc_list, db.rc_count, db.rc_cap, ff, rgrid, s);
+    }
+  }
+  cudaError_t e2 = cudaFreeAsync(ws, s);
+  if (e == cudaSuccess) e = e2;
+  if (e != cudaSuccess) return cuda_fail(e, "staged shoot launch");
+  return RS_OK;
+}
+
 int rs_shoot(rs_field_t f, const rs_ray_grid* g, const rs_window* w, uint32_t* d_counts, uint64_t* d_out_of_window,
              void* stream) {
   if (!g) return fail(RS_EINVAL, "ray grid is NULL");
@@ -752,6 +824,12 @@ int rs_selftest_bounded_wait(int64_t limit_ns, int* status) {
 
 int rs_set_certified_binning(int enabled) {
   g_certify = enabled ? 1 : 0;
+  return RS_OK;
+}
+
+int rs_set_staged_state_budget(uint64_t bytes) {
+  if (bytes < ((uint64_t)1 << 20)) return fail(RS_EINVAL, "the staged state budget must be at least 1 MiB");
+  g_staged_budget = (size_t)bytes;
   return RS_OK;
 }
 

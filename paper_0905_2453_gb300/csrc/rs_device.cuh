@@ -389,21 +389,31 @@ __device__ __forceinline__ void build_row_table(LensSmem<TILE, ROWS>& sm, int b)
 // then stop; the status word has been set).  The arithmetic per ray depends only on the ray and
 // the field.
 // ----------------------------------------------------------------------------------------------
+// Per-ray accumulators of the deflection sum, packed two rays per 64-bit register: two-float
+// (hi, lo) sums of alpha1 and alpha2, and the error-band sums of squared and absolute group partials.
+template <int NP>
+struct DeflectAcc {
+  uint64_t H1[NP], L1[NP], H2[NP], L2[NP], SS[NP], AB[NP];
+};
+
+// Accumulate the field's lenses into acc (X1/X2: packed ray coordinates).  The arithmetic depends on
+// a lens's index within the field only through the group (32) and renormalisation (256) schedule,
+// so a field split into parts of multiples of 256 lenses, accumulated part after part, gives
+// bitwise the sums of the whole field.  Returns false if a bounded wait gave up (the CTA must then
+// stop; the status word has been set).
 template <int RPT, int TILE, bool MASS, bool ROW, int ROWS>
-__device__ __forceinline__ bool deflect(const FieldDev& f, const float (&x1)[RPT], const float (&x2)[RPT],
-                                        double (&a1)[RPT], double (&a2)[RPT], float (&sig)[RPT],
-                                        LensSmem<TILE, ROWS>& sm, PipeState& ps) {
-  static_assert(RPT % 2 == 0, "rays per thread must be even (packed pairs)");
+__device__ __forceinline__ bool deflect_accumulate(const FieldDev& f, const uint64_t (&X1)[RPT / 2],
+                                                   const uint64_t (&X2)[RPT / 2], DeflectAcc<RPT / 2>& acc,
+                                                   LensSmem<TILE, ROWS>& sm, PipeState& ps) {
   static_assert(TILE % kGroup == 0 && kGroup % 8 == 0, "lens tile must hold whole lens groups");
   static_assert(kRenorm % kGroup == 0, "renormalisation falls on group boundaries");
   constexpr int NP = RPT / 2;
-  uint64_t X1[NP], X2[NP], H1[NP], L1[NP], H2[NP], L2[NP], SS[NP], AB[NP];
-#pragma unroll
-  for (int q = 0; q < NP; ++q) {
-    X1[q] = f2_pack(x1[2 * q], x1[2 * q + 1]);
-    X2[q] = f2_pack(x2[2 * q], x2[2 * q + 1]);
-    H1[q] = L1[q] = H2[q] = L2[q] = SS[q] = AB[q] = 0ull;
-  }
+  uint64_t (&H1)[NP] = acc.H1;
+  uint64_t (&L1)[NP] = acc.L1;
+  uint64_t (&H2)[NP] = acc.H2;
+  uint64_t (&L2)[NP] = acc.L2;
+  uint64_t (&SS)[NP] = acc.SS;
+  uint64_t (&AB)[NP] = acc.AB;
   const int n = f.n_lens;
   const int ntiles = (n + TILE - 1) / TILE;
   const uint32_t rt = smem_u32(&sm.rowtab[ROW ? (threadIdx.x >> 5) : 0][0]);
@@ -505,6 +515,20 @@ __device__ __forceinline__ bool deflect(const FieldDev& f, const float (&x1)[RPT
     if (t + 1 < ntiles) (void)mbar_wait_bounded(&sm.bar[(t + 1) & 1], ps.parity[(t + 1) & 1]);
     return false;
   }
+  return true;
+}
+
+// alpha (float64) and the error-band estimate sig of each ray from its accumulators.
+template <int RPT>
+__device__ __forceinline__ void deflect_finish(const DeflectAcc<RPT / 2>& acc, double (&a1)[RPT], double (&a2)[RPT],
+                                               float (&sig)[RPT]) {
+  constexpr int NP = RPT / 2;
+  const uint64_t (&H1)[NP] = acc.H1;
+  const uint64_t (&L1)[NP] = acc.L1;
+  const uint64_t (&H2)[NP] = acc.H2;
+  const uint64_t (&L2)[NP] = acc.L2;
+  const uint64_t (&SS)[NP] = acc.SS;
+  const uint64_t (&AB)[NP] = acc.AB;
 #pragma unroll
   for (int q = 0; q < NP; ++q) {
     float h, hB, l, lB;
@@ -525,6 +549,32 @@ __device__ __forceinline__ bool deflect(const FieldDev& f, const float (&x1)[RPT
     sig[2 * q] = kSigmaScale * sqrtf(h) + kSystematicScale * l + 8e-15f * (fabsf(h1a) + fabsf(h2a));
     sig[2 * q + 1] = kSigmaScale * sqrtf(hB) + kSystematicScale * lB + 8e-15f * (fabsf(h1b) + fabsf(h2b));
   }
+}
+
+
+template <int RPT>
+__device__ __forceinline__ void pack_rays(const float (&x1)[RPT], const float (&x2)[RPT], uint64_t (&X1)[RPT / 2],
+                                          uint64_t (&X2)[RPT / 2]) {
+#pragma unroll
+  for (int q = 0; q < RPT / 2; ++q) {
+    X1[q] = f2_pack(x1[2 * q], x1[2 * q + 1]);
+    X2[q] = f2_pack(x2[2 * q], x2[2 * q + 1]);
+  }
+}
+
+template <int RPT, int TILE, bool MASS, bool ROW, int ROWS>
+__device__ __forceinline__ bool deflect(const FieldDev& f, const float (&x1)[RPT], const float (&x2)[RPT],
+                                        double (&a1)[RPT], double (&a2)[RPT], float (&sig)[RPT],
+                                        LensSmem<TILE, ROWS>& sm, PipeState& ps) {
+  static_assert(RPT % 2 == 0, "rays per thread must be even (packed pairs)");
+  constexpr int NP = RPT / 2;
+  uint64_t X1[NP], X2[NP];
+  pack_rays<RPT>(x1, x2, X1, X2);
+  DeflectAcc<NP> acc;
+#pragma unroll
+  for (int q = 0; q < NP; ++q) acc.H1[q] = acc.L1[q] = acc.H2[q] = acc.L2[q] = acc.SS[q] = acc.AB[q] = 0ull;
+  if (!deflect_accumulate<RPT, TILE, MASS, ROW, ROWS>(f, X1, X2, acc, sm, ps)) return false;
+  deflect_finish<RPT>(acc, a1, a2, sig);
   return true;
 }
 

@@ -70,6 +70,19 @@ cudaError_t launch_cull(const rsdev::ShootDesc& d, double hi0, double hi1, unsig
 cudaError_t launch_shoot_cells(const rsdev::ShootDesc& d, int64_t n_cx, const unsigned* list, const unsigned* n_kept,
                                int grid, cudaStream_t s);
 
+// Lens-partitioned shooting (rs_staged.cu), default launch shape (4 warps x 8 rays): the per-ray
+// accumulator state of a call of n_rows x n0 rays takes staged_state_bytes; launch_staged adds the
+// partition d.f to it (first: start from zero; last: map and bin instead of storing).  The listed
+// rays of certified binning are re-evaluated partition by partition into ff (16 bytes per entry)
+// and binned by launch_recheck_bin.
+int64_t staged_tiles(int64_t n_rows, int64_t n0);
+size_t staged_state_bytes(int64_t n_rows, int64_t n0);
+cudaError_t launch_staged(const rsdev::ShootDesc& d, uint64_t* state, bool first, bool last, cudaStream_t s);
+cudaError_t launch_recheck_part(const rsdev::ShootDesc& d, const uint2* list, const unsigned int* count,
+                                unsigned int cap, float4* ff, bool first, int grid, cudaStream_t s);
+cudaError_t launch_recheck_bin(const rsdev::ShootDesc& d, const uint2* list, const unsigned int* count,
+                               unsigned int cap, const float4* ff, int grid, cudaStream_t s);
+
 // Light curves (rs_lightcurve.cu): one descriptor per track with samples, in output order.
 struct LcTrack {
   const float* mu;          // map, float[np1][np0]

@@ -6,77 +6,12 @@
 // far cheaper on GB300 than float64 -- then mapped (Eq. 6) and binned exactly as in the shoot
 // epilogue.  One warp per listed ray: the lanes split the lens loop (coalesced lens loads) and a
 // fixed reduction tree combines them, so the result is deterministic.
+#include "rs_ff.cuh"
 #include "rs_internal.h"
 
 namespace {
 
 using namespace rsdev;
-
-// s + e = a + b exactly (Knuth).
-__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
-  s = __fadd_rn(a, b);
-  const float bb = __fsub_rn(s, a);
-  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
-}
-// s + e = a + b exactly when |a| >= |b| (Dekker).
-__device__ __forceinline__ void fast_two_sum(float a, float b, float& s, float& e) {
-  s = __fadd_rn(a, b);
-  e = __fsub_rn(b, __fsub_rn(s, a));
-}
-// (ah, al) += (bh, bl)
-__device__ __forceinline__ void ff_add(float& ah, float& al, float bh, float bl) {
-  float s, e;
-  two_sum(ah, bh, s, e);
-  e = __fadd_rn(e, __fadd_rn(al, bl));
-  fast_two_sum(s, e, ah, al);
-}
-
-// One lens term of Eq. 2 for ray (x1, x2) in float-float, added to (A1h, A1l), (A2h, A2l).
-template <bool MASS>
-__device__ __forceinline__ void lens_term_ff(const FieldDev& f, int l, float x1, float x2, float& A1h, float& A1l,
-                                             float& A2h, float& A2l) {
-  const float4 L = __ldg(f.lens4 + l);
-  // exact differences x - x_l as float pairs
-  float ah, al, bh, bl;
-  two_sum(x1, -L.x, ah, al);
-  two_sum(x2, -L.z, bh, bl);
-  // r^2 = (ah + al)^2 + (bh + bl)^2 to ~2^-46 relative (al^2, bl^2 dropped)
-  const float p = __fmul_rn(ah, ah);
-  float pe = __fmaf_rn(ah, ah, -p);
-  pe = __fmaf_rn(__fmul_rn(2.f, ah), al, pe);
-  const float q = __fmul_rn(bh, bh);
-  float qe = __fmaf_rn(bh, bh, -q);
-  qe = __fmaf_rn(__fmul_rn(2.f, bh), bl, qe);
-  float s, se;
-  two_sum(p, q, s, se);
-  se = __fadd_rn(se, __fadd_rn(pe, qe));
-  float rh, rl;
-  fast_two_sum(s, se, rh, rl);
-  // w = 1 / r^2: approximate reciprocal plus one Newton correction from the exact residual
-  const float w0 = rcp_approx(rh);
-  float e = __fmaf_rn(-rh, w0, 1.f);
-  e = __fmaf_rn(-rl, w0, e);
-  float wh, wl;
-  fast_two_sum(w0, __fmul_rn(w0, e), wh, wl);
-  if (MASS) {
-    const float m = __ldg(f.mass2 + l).x;
-    const float mh = __fmul_rn(wh, m);
-    float ml = __fmaf_rn(wh, m, -mh);
-    ml = __fmaf_rn(wl, m, ml);
-    fast_two_sum(mh, ml, wh, wl);
-  }
-  // terms w * d, accumulated in float-float
-  const float t1h = __fmul_rn(wh, ah);
-  float t1l = __fmaf_rn(wh, ah, -t1h);
-  t1l = __fmaf_rn(wh, al, t1l);
-  t1l = __fmaf_rn(wl, ah, t1l);
-  const float t2h = __fmul_rn(wh, bh);
-  float t2l = __fmaf_rn(wh, bh, -t2h);
-  t2l = __fmaf_rn(wh, bl, t2l);
-  t2l = __fmaf_rn(wl, bh, t2l);
-  ff_add(A1h, A1l, t1h, t1l);
-  ff_add(A2h, A2l, t2h, t2l);
-}
 
 // Deflection of one ray by all lenses of the field in float-float, spread over the 32 lanes of
 // a warp: lane k sums lenses k, k + 32, ... in order; the 32 partial sums are combined by a fixed

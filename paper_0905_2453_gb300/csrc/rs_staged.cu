@@ -1,0 +1,186 @@
+// Lens-partitioned ("staged") shooting, the billion-lens scheme of Section 3.3: the deflection of
+// every ray is summed over the lenses of one partition at a time, the partially deflected rays
+// carried between passes, and the rays are mapped and binned after the last partition.  The carried
+// state is the shoot kernel's own per-ray accumulators (two-float alpha sums and error-band sums),
+// so with partitions of multiples of 256 lenses the final sums are bitwise those of one pass over
+// all lenses.  Certified binning re-evaluates the listed rays in float-float, again partition by
+// partition.
+#include "rs_ff.cuh"
+#include "rs_internal.h"
+
+namespace {
+
+using namespace rsdev;
+
+constexpr int kWarps = 4, kRpt = 8, kNp = kRpt / 2, kBlock = kWarps * 32;
+
+// State layout: word k (0..6*kNp-1) of thread t of tile T at state[(T * 6 * kNp + k) * kBlock + t],
+// coalesced across the threads of a CTA.
+__device__ __forceinline__ void state_io(uint64_t* __restrict__ st, DeflectAcc<kNp>& a, bool store) {
+  uint64_t* w[6] = {a.H1, a.L1, a.H2, a.L2, a.SS, a.AB};
+#pragma unroll
+  for (int k = 0; k < 6; ++k)
+#pragma unroll
+    for (int q = 0; q < kNp; ++q) {
+      uint64_t* p = st + (size_t)(k * kNp + q) * kBlock;
+      if (store)
+        p[0] = w[k][q];
+      else
+        w[k][q] = p[0];
+    }
+}
+
+template <bool MASS>
+__global__ void __launch_bounds__(kBlock, 2) staged_kernel(const ShootDesc d, uint64_t* __restrict__ state, int first,
+                                                           int last) {
+  __shared__ LensSmem<rsint::kTile, kWarps> sm;
+  PipeState ps;
+  pipe_init(sm.bar, ps);
+  constexpr int SEG = 32 * kRpt;
+  const int64_t tile = blockIdx.x;
+  const int64_t ncol = (d.n0 + SEG - 1) / SEG;
+  const int64_t trow = tile / ncol;
+  const int64_t tcol = tile - trow * ncol;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t jrel = trow * kWarps + warp;
+  const bool row_ok = jrel < d.n_rows;
+  const int64_t j = d.j_begin + (row_ok ? jrel : d.n_rows - 1);
+  const float x2r = ray_coord(j, d.sp1, d.or1);
+  float x1[kRpt], x2[kRpt];
+  bool valid[kRpt];
+#pragma unroll
+  for (int k = 0; k < kRpt; ++k) {
+    int64_t i = tcol * SEG + lane + 32 * k;
+    valid[k] = row_ok && i < d.n0;
+    if (i >= d.n0) i = d.n0 - 1;
+    x1[k] = ray_coord(i, d.sp0, d.or0);
+    x2[k] = x2r;
+  }
+  if (lane == 0) sm.x2row[warp] = x2r;
+  uint64_t X1[kNp], X2[kNp];
+  pack_rays<kRpt>(x1, x2, X1, X2);
+  DeflectAcc<kNp> acc;
+  uint64_t* st = state + (size_t)tile * 6 * kNp * kBlock + threadIdx.x;
+  if (first) {
+#pragma unroll
+    for (int q = 0; q < kNp; ++q) acc.H1[q] = acc.L1[q] = acc.H2[q] = acc.L2[q] = acc.SS[q] = acc.AB[q] = 0ull;
+  } else {
+    state_io(st, acc, false);
+  }
+  if (!deflect_accumulate<kRpt, rsint::kTile, MASS, true, kWarps>(d.f, X1, X2, acc, sm, ps)) return;
+  if (!last) {
+    state_io(st, acc, true);
+    return;
+  }
+  double a1[kRpt], a2[kRpt];
+  float sig[kRpt];
+  deflect_finish<kRpt>(acc, a1, a2, sig);
+  bin_rays<kRpt, 32>(d, x1, x2, a1, a2, sig, valid, jrel, tcol * SEG + lane, lane);
+}
+
+// ---- float-float re-evaluation of the listed rays, partition by partition ----------------------
+
+// Partial float-float deflection of each listed ray by one partition, added to ff[e] = {A1h, A1l,
+// A2h, A2l} (set on the first partition).  One warp per listed ray, lanes split the partition's
+// lenses, fixed reduction tree.
+template <bool MASS>
+__global__ void __launch_bounds__(128) recheck_part_kernel(const ShootDesc d, const uint2* __restrict__ list,
+                                                           const unsigned int* __restrict__ count, unsigned int cap,
+                                                           float4* __restrict__ ff, int first) {
+  const unsigned int n = min(*count, cap);
+  const unsigned int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const unsigned int nwarps = (gridDim.x * blockDim.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  for (unsigned int e = warp; e < n; e += nwarps) {
+    const int64_t r = (int64_t)list[e].y;
+    const int64_t jrel = r / d.n0;
+    const int64_t i = r - jrel * d.n0;
+    const float x1 = ray_coord(i, d.sp0, d.or0);
+    const float x2 = ray_coord(d.j_begin + jrel, d.sp1, d.or1);
+    float A1h = 0.f, A1l = 0.f, A2h = 0.f, A2l = 0.f;
+    for (int l = lane; l < d.f.n_lens; l += 32) lens_term_ff<MASS>(d.f, l, x1, x2, A1h, A1l, A2h, A2l);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      const float b1h = __shfl_down_sync(0xffffffffu, A1h, off);
+      const float b1l = __shfl_down_sync(0xffffffffu, A1l, off);
+      const float b2h = __shfl_down_sync(0xffffffffu, A2h, off);
+      const float b2l = __shfl_down_sync(0xffffffffu, A2l, off);
+      ff_add(A1h, A1l, b1h, b1l);
+      ff_add(A2h, A2l, b2h, b2l);
+    }
+    if (lane == 0) {
+      if (!first) {
+        const float4 o = ff[e];
+        ff_add(A1h, A1l, o.x, o.y);
+        ff_add(A2h, A2l, o.z, o.w);
+      }
+      ff[e] = make_float4(A1h, A1l, A2h, A2l);
+    }
+  }
+}
+
+// Map and bin the listed rays from their float-float deflections (as the single-pass re-evaluation).
+__global__ void __launch_bounds__(128) recheck_bin_kernel(const ShootDesc d, const uint2* __restrict__ list,
+                                                          const unsigned int* __restrict__ count, unsigned int cap,
+                                                          const float4* __restrict__ ff) {
+  const unsigned int n = min(*count, cap);
+  for (unsigned int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
+    const int64_t r = (int64_t)list[e].y;
+    const int64_t jrel = r / d.n0;
+    const int64_t i = r - jrel * d.n0;
+    const float x1 = ray_coord(i, d.sp0, d.or0);
+    const float x2 = ray_coord(d.j_begin + jrel, d.sp1, d.or1);
+    const float4 a = ff[e];
+    const double a1 = (double)a.x + (double)a.y, a2 = (double)a.z + (double)a.w;
+    const double y1 = __dsub_rn(__dmul_rn(d.f.lam1, (double)x1), a1);
+    const double y2 = __dsub_rn(__dmul_rn(d.f.lam2, (double)x2), a2);
+    const double u1 = __dmul_rn(__dsub_rn(y1, d.lo0), d.sc0);
+    const double u2 = __dmul_rn(__dsub_rn(y2, d.lo1), d.sc1);
+    const bool inwin = (u1 >= 0.0) && (u1 < (double)d.np0) && (u2 >= 0.0) && (u2 < (double)d.np1);
+    if (inwin) {
+      atomicAdd(d.counts + (size_t)(int)floor(u2) * (size_t)d.np0 + (size_t)(int)floor(u1), 1u);
+    } else if (d.oow != nullptr) {
+      atomicAdd(d.oow, 1ull);
+    }
+  }
+}
+
+}  // namespace
+
+namespace rsint {
+
+int64_t staged_tiles(int64_t n_rows, int64_t n0) { return shoot_tiles<kWarps, kRpt>(n_rows, n0); }
+
+size_t staged_state_bytes(int64_t n_rows, int64_t n0) {
+  return (size_t)staged_tiles(n_rows, n0) * 6 * kNp * kBlock * sizeof(uint64_t);
+}
+
+cudaError_t launch_staged(const rsdev::ShootDesc& d, uint64_t* state, bool first, bool last, cudaStream_t s) {
+  const int64_t grid = staged_tiles(d.n_rows, d.n0);
+  if (grid <= 0) return cudaSuccess;
+  if (grid >= ((int64_t)1 << 31)) return cudaErrorInvalidValue;
+  if (d.f.has_mass)
+    staged_kernel<true><<<(unsigned)grid, kBlock, 0, s>>>(d, state, first ? 1 : 0, last ? 1 : 0);
+  else
+    staged_kernel<false><<<(unsigned)grid, kBlock, 0, s>>>(d, state, first ? 1 : 0, last ? 1 : 0);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_recheck_part(const rsdev::ShootDesc& d, const uint2* list, const unsigned int* count,
+                                unsigned int cap, float4* ff, bool first, int grid, cudaStream_t s) {
+  if (cap == 0) return cudaSuccess;
+  if (d.f.has_mass)
+    recheck_part_kernel<true><<<grid, 128, 0, s>>>(d, list, count, cap, ff, first ? 1 : 0);
+  else
+    recheck_part_kernel<false><<<grid, 128, 0, s>>>(d, list, count, cap, ff, first ? 1 : 0);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_recheck_bin(const rsdev::ShootDesc& d, const uint2* list, const unsigned int* count,
+                               unsigned int cap, const float4* ff, int grid, cudaStream_t s) {
+  if (cap == 0) return cudaSuccess;
+  recheck_bin_kernel<<<grid, 128, 0, s>>>(d, list, count, cap, ff);
+  return cudaGetLastError();
+}
+
+}  // namespace rsint
