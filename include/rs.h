@@ -179,9 +179,25 @@ int rs_shoot_culled(rs_field_t f, const rs_ray_grid* g, int64_t row_begin, int64
 int rs_shoot_staged(int n_parts, const rs_field_t* parts, const rs_ray_grid* g, int64_t row_begin, int64_t row_end,
                     const rs_window* w, uint32_t* d_counts, uint64_t* d_out_of_window, void* stream);
 
+/*
+ * rs_shoot_streamed -- rs_shoot_staged for lenses held in HOST memory (out-of-core: more lenses than
+ * fit the device, or than one field may hold).  The lenses (h_lens_xy: float[2*n_lens] interleaved,
+ * h_masses: float[n_lens] or NULL for unit masses, n_lens may exceed 2^31) stream through the device
+ * in passes of lenses_per_pass lenses (a multiple of 1024, at most 2^30) via two pinned staging
+ * buffers and two device buffers: the host copy and upload of the next partition overlap the pass
+ * over the current one on the GPU.  With certified binning on, a second sweep streams the lenses
+ * again for the float-float re-evaluation of the listed rays.  Results as rs_shoot_staged (bit for
+ * bit those of one pass over all lenses).  Synchronous: returns when the counts are complete.
+ * Device memory: 72 bytes per lens of a pass plus the ray state.  Errors: as rs_shoot_rows, and
+ * RS_ETIMEOUT if a bounded wait for a lens tile gave up.
+ */
+int rs_shoot_streamed(const float* h_lens_xy, const float* h_masses, int64_t n_lens, double kappa_c, double gamma,
+                      int64_t lenses_per_pass, const rs_ray_grid* g, int64_t row_begin, int64_t row_end,
+                      const rs_window* w, uint32_t* d_counts, uint64_t* d_out_of_window, void* stream);
+
 /* Device memory budget (bytes, >= 1 MiB; default 2 GiB) for the carried per-ray state of
  * rs_shoot_staged: calls whose state would exceed it run in row blocks (same results). */
-int rs_set_staged_state_budget(uint64_t bytes);
+int rs_set_staged_state_budget(uint64_t bytes);  /* also used by rs_shoot_streamed */
 
 /*
  * rs_trace -- source positions of listed rays through the float32 path, for checks.

@@ -41,7 +41,7 @@ EXPORTED_SYMBOLS = (
     "rs_field_status", "rs_last_error", "rs_version", "rs_set_launch_config", "rs_get_launch_config",
     "rs_launch_configs", "rs_trace_certified", "rs_set_certified_binning", "rs_get_certified_binning",
     "rs_selftest_bounded_wait", "rs_shoot_rows_noalloc", "rs_light_curves", "rs_shoot_culled",
-    "rs_create_moving_field", "rs_field_set_time", "rs_field_time", "rs_shoot_staged",
+    "rs_create_moving_field", "rs_field_set_time", "rs_field_time", "rs_shoot_staged", "rs_shoot_streamed",
     "rs_set_staged_state_budget",
     "rs_light_curve_plan_create", "rs_light_curve_plan_samples", "rs_light_curve_plan_launch",
     "rs_light_curve_plan_destroy",
@@ -136,6 +136,7 @@ def load():
         "rs_shoot_culled": ([vp, gp, i64, i64, wp, vp, vp, vp, vp], i32),
         "rs_shoot_staged": ([i32, vp, gp, i64, i64, wp, vp, vp, vp], i32),
         "rs_set_staged_state_budget": ([ctypes.c_uint64], i32),
+        "rs_shoot_streamed": ([vp, vp, i64, dbl, dbl, i64, gp, i64, i64, wp, vp, vp, vp], i32),
         "rs_magnification": ([vp, gp, wp, vp, vp], i32),
         "rs_light_curves": ([i32, vp, vp, i32, dbl, i32, vp, vp, vp, vp], i32),
         "rs_light_curve_plan_create": ([i32, vp, vp, i32, dbl, i32, vp, ctypes.POINTER(vp)], i32),
@@ -348,6 +349,26 @@ def rs_shoot_staged(handles, grid, row_begin: int, row_end: int, window, counts,
     g, w = _cgrid(grid), _cwin(window)
     _check(load().rs_shoot_staged(n, H, ctypes.byref(g), int(row_begin), int(row_end), ctypes.byref(w), pc, po,
                                   _stream(stream)), "rs_shoot_staged")
+
+
+def rs_shoot_streamed(lens_xy, masses, kappa_c: float, gamma: float, lenses_per_pass: int, grid, row_begin: int,
+                      row_end: int, window, counts, out_of_window=None, stream=None):
+    """Shoot lenses held in host memory (numpy [n, 2] float32, masses [n] or None), streamed through the
+    device lenses_per_pass at a time.  Synchronous."""
+    import numpy as np
+    xy = np.ascontiguousarray(np.asarray(lens_xy, dtype=np.float32).reshape(-1, 2))
+    m = None if masses is None else np.ascontiguousarray(np.asarray(masses, dtype=np.float32).reshape(-1))
+    n = xy.shape[0]
+    if m is not None and m.size != n:
+        raise ValueError("masses length differs from lens count")
+    npx = int(window.npix[0]) * int(window.npix[1])
+    pc = _dptr(counts, _COUNT_DTYPES, "counts", npx)
+    po = _dptr(out_of_window, _OOW_DTYPES, "out_of_window", 1)
+    g, w = _cgrid(grid), _cwin(window)
+    _check(load().rs_shoot_streamed(xy.ctypes.data if n else None, None if m is None else m.ctypes.data, n,
+                                    float(kappa_c), float(gamma), int(lenses_per_pass), ctypes.byref(g),
+                                    int(row_begin), int(row_end), ctypes.byref(w), pc, po, _stream(stream)),
+           "rs_shoot_streamed")
 
 
 def rs_set_staged_state_budget(nbytes: int) -> None:

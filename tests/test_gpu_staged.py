@@ -85,3 +85,50 @@ def test_n1e4_in_four_partitions():
     ref, oref = shoot_gpu(spec)
     got, o = _staged(spec, [2560, 5120, 7680])
     assert np.array_equal(got, ref) and o == oref
+
+
+def _streamed(spec, per_pass, rows=None, window=None):
+    m = rs()
+    g, w = spec.grid, window or spec.window
+    c = torch.zeros((int(w.npix[1]), int(w.npix[0])), dtype=torch.int32, device=dev())
+    o = torch.zeros(1, dtype=torch.int64, device=dev())
+    r0, r1 = rows or (0, int(g.n[1]))
+    m.rs_shoot_streamed(spec.lens_xy, spec.masses, spec.kappa_c, spec.gamma, per_pass, g, r0, r1, w, c, o)
+    return c.cpu().numpy().view(np.uint32), int(o.item())
+
+
+@pytest.mark.parametrize("certify", [True, False])
+@pytest.mark.parametrize("mass", ["equal", "salpeter"])
+def test_streamed_from_host_equals_single_pass(certify, mass):
+    """Lenses streamed from host memory 1024 or 3072 at a time (5 or 2 passes)."""
+    m = rs()
+    m.rs_set_certified_binning(certify)
+    try:
+        spec = ri.disc_field("ss", 5000, 0.5, 0.05, 0.2, 768, 96, seed=31, mass=mass)
+        ref, oref = shoot_gpu(spec)
+        for per_pass in (1024, 3072):
+            got, o = _streamed(spec, per_pass)
+            assert np.array_equal(got, ref) and o == oref, per_pass
+    finally:
+        m.rs_set_certified_binning(True)
+
+
+def test_streamed_row_blocks_rows_and_empty_field():
+    m = rs()
+    spec = ri.disc_field("ssb", 2500, 0.4, 0.0, 0.3, 800, 80, seed=6, mass="equal")
+    m.rs_set_staged_state_budget(1 << 20)
+    try:
+        got, o = _streamed(spec, 1024)
+        got_rows, o_rows = _streamed(spec, 2048, rows=(33, 500))
+    finally:
+        m.rs_set_staged_state_budget(2 << 30)
+    ref, oref = oracle.shoot_field(spec)
+    assert np.array_equal(got, ref) and o == oref
+    ref_rows, oref_rows = shoot_gpu(spec, rows=(33, 500))
+    assert np.array_equal(got_rows, ref_rows) and o_rows == oref_rows
+    empty = ri.Field("e", np.zeros((0, 2), np.float32), None, 0.1, 0.2, spec.grid, spec.window)
+    got0, o0 = _streamed(empty, 1024)
+    ref0, oref0 = oracle.shoot_field(empty)
+    assert np.array_equal(got0, ref0) and o0 == oref0
+    with pytest.raises(m.RSError):
+        _streamed(spec, 1000)                    # not a multiple of 1024
