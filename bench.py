@@ -372,6 +372,11 @@ def run_ours(args):
     if not args.no_frames and world == 1:
         frames = run_frames(rs, torch, device, stream, spec)
 
+    # ---------------- lens-partitioned shooting: device shards and host-streamed lenses
+    staged = None
+    if not args.no_staged and world == 1:
+        staged = run_staged(rs, torch, device, stream, spec)
+
     # ---------------- CPU baseline (oracle, bounded sample)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -412,6 +417,7 @@ def run_ours(args):
         "light_curves": light,
         "zoom": zoom,
         "frames": frames,
+        "staged": staged,
         "wall_s_timed_region": wall,
     }
     print(json.dumps(line), flush=True)
@@ -600,6 +606,9 @@ def run_section(args):
             rs.rs_set_launch_config(spec.masses is not None, b_, r_)
         out = {"zoom": run_zoom(rs, torch, device, stream, spec),
                "culled_full_map": run_zoom(rs, torch, device, stream, spec, factor=1, quarter=False)}
+    elif args.section == "staged":
+        spec = workload(args.workload, seed=0)
+        out = {"staged": run_staged(rs, torch, device, stream, spec)}
     elif args.section == "frames":
         spec = workload(args.workload, seed=0)
         out = {"frames": run_frames(rs, torch, device, stream, spec)}
@@ -648,6 +657,69 @@ def run_frames(rs, torch, device, stream, spec, n_frames=16, dt=1.0, sigma_v=0.1
             "reps": reps}
 
 
+def run_staged(rs, torch, device, stream, spec, parts=4, reps=3):
+    """The workload field as lens partitions (device-resident shards) and streamed from host memory,
+    against the plain one-field shoot: times and bit-equality."""
+    n = spec.n_lens
+    per = max(256, (n + parts - 1) // parts // 256 * 256)
+    cuts = list(range(per, n, per))
+    bounds = [0] + cuts + [n]
+    shards = [rs.Field(spec.lens_xy[a:b], None if spec.masses is None else spec.masses[a:b], spec.kappa_c,
+                       spec.gamma, stream) for a, b in zip(bounds[:-1], bounds[1:])]
+    plain = rs.Field.from_spec(spec, stream)
+    npix = (int(spec.window.npix[1]), int(spec.window.npix[0]))
+    out = {}
+    ref = torch.zeros(npix, dtype=torch.int32, device=device)
+    ref_o = torch.zeros(1, dtype=torch.int64, device=device)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize(device)
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize(device)
+        return e0.elapsed_time(e1) / reps
+
+    def plain_fn():
+        ref.zero_()
+        ref_o.zero_()
+        plain.shoot(spec.grid, spec.window, ref, ref_o, stream=stream)
+
+    t_plain = timed(plain_fn)
+    c = torch.zeros_like(ref)
+    o = torch.zeros_like(ref_o)
+
+    def staged_fn():
+        c.zero_()
+        o.zero_()
+        rs.rs_shoot_staged([f.handle for f in shards], spec.grid, 0, int(spec.grid.n[1]), spec.window, c, o, stream)
+
+    t_staged = timed(staged_fn)
+    same_staged = bool(torch.equal(c, ref)) and bool(torch.equal(o, ref_o))
+    per_pass = max(1024, (n + parts - 1) // parts // 1024 * 1024)
+
+    def streamed_fn():
+        c.zero_()
+        o.zero_()
+        rs.rs_shoot_streamed(spec.lens_xy, spec.masses, spec.kappa_c, spec.gamma, per_pass, spec.grid, 0,
+                             int(spec.grid.n[1]), spec.window, c, o, stream)
+
+    t_streamed = timed(streamed_fn)
+    same_streamed = bool(torch.equal(c, ref)) and bool(torch.equal(o, ref_o))
+    for f in shards + [plain]:
+        f.close()
+    out = {"workload": f"{args_workload_name(spec)}: {len(shards)} device shards of <= {per} lenses; host-resident "
+                       f"lenses streamed {per_pass} per pass",
+           "plain_ms": t_plain, "staged_ms": t_staged, "streamed_ms": t_streamed,
+           "staged_interactions_per_s": spec.interactions / (t_staged / 1e3),
+           "streamed_interactions_per_s": spec.interactions / (t_streamed / 1e3),
+           "staged_bitwise_equal": same_staged, "streamed_bitwise_equal": same_streamed, "reps": reps}
+    return out
+
+
 def args_workload_name(spec):
     return getattr(spec, "name", "field")
 
@@ -664,7 +736,8 @@ def main():
     ap.add_argument("--no-light-curves", action="store_true")
     ap.add_argument("--no-zoom", action="store_true")
     ap.add_argument("--no-frames", action="store_true")
-    ap.add_argument("--section", choices=["zoom", "light-curves", "frames"], default=None,
+    ap.add_argument("--no-staged", action="store_true")
+    ap.add_argument("--section", choices=["zoom", "light-curves", "frames", "staged"], default=None,
                     help="run one secondary measurement alone and print its JSON object (for profiling)")
     ap.add_argument("--batch-reps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")

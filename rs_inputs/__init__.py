@@ -301,3 +301,25 @@ def lens_velocities(n: int, sigma_v: float, seed: int) -> np.ndarray:
     (Einstein radii per unit time): the random stellar motions of a time series of maps."""
     rng = np.random.default_rng([seed, 2])
     return (rng.normal(size=(n, 2)) * sigma_v).astype(np.float32)
+
+
+def disc_lenses_large(n: int, radius: float, seed: int, chunk: int = 1 << 24, threads: int = 16) -> np.ndarray:
+    """float32 [n, 2] unit-mass lens positions uniform in a disc, for lens counts beyond what the
+    float64 temporaries of disc_lenses allow (billions): chunk k of `chunk` lenses is drawn from its
+    own stream (seed [seed, 7, k]) with r = R sqrt(u1), theta = 2 pi u2, several chunks in parallel."""
+    from concurrent.futures import ThreadPoolExecutor
+    xy = np.empty((n, 2), dtype=np.float32)
+
+    def fill(k):
+        a = k * chunk
+        m = min(chunk, n - a)
+        rng = np.random.default_rng([seed, 7, k])
+        u = rng.random((2, m))
+        r = radius * np.sqrt(u[0])
+        th = 2.0 * math.pi * u[1]
+        xy[a:a + m, 0] = r * np.cos(th)
+        xy[a:a + m, 1] = r * np.sin(th)
+
+    with ThreadPoolExecutor(max_workers=threads) as ex:
+        list(ex.map(fill, range((n + chunk - 1) // chunk)))
+    return xy
