@@ -30,7 +30,16 @@ def test_streamed_beyond_2_31_lenses_one_row_vs_oracle():
     m.rs_shoot_streamed(xy, None, 0.0, 0.1, 1 << 28, g, 7, 8, w, counts, oow)
     got = counts.cpu().numpy().view(np.uint32)
     t2 = time.perf_counter()
-    ref, oref = oracle.shoot(xy, None, 0.0, 0.1, g.origin, g.spacing, g.n, w.lo, w.hi, w.npix, rows=(7, 8))
+    # the oracle's source positions of the 16 rays, one ray per host thread (each call single-threaded)
+    from concurrent.futures import ThreadPoolExecutor
+
+    def one(i):
+        oracle.set_num_threads(1)
+        return oracle.trace(xy, None, 0.0, 0.1, g.origin, g.spacing, np.array([[i, 7]], np.int64))[0][0]
+
+    with ThreadPoolExecutor(max_workers=16) as ex:
+        y = np.array(list(ex.map(one, range(16))))
+    ref, oref = oracle.bin_positions(y, w.lo, w.hi, w.npix)
     t3 = time.perf_counter()
     print(f"lenses {t1 - t0:.1f} s, streamed shoot {t2 - t1:.1f} s, oracle {t3 - t2:.1f} s")
     assert int(got.sum()) + int(oow.item()) == 16
