@@ -37,14 +37,16 @@
  *     distances serves both lenses (Montgomery's simultaneous inversion).
  *     Per ray, partial sums over consecutive groups of 32 lenses (in lens index
  *     order) are folded into a two-float (hi, lo) accumulator with an
- *     error-free TwoSum; (hi, lo) is renormalised after every 256 lenses.  The deflection alpha = hi + lo, Eq. 6 and the pixel
- *     index are then evaluated in double precision.
+ *     error-free TwoSum; (hi, lo) is renormalised after every 256 lenses.  With
+ *     alpha = hi + lo, Eq. 6 and the pixel coordinate u are evaluated in
+ *     float-float arithmetic (~2^-44 relative; rs_trace reports y in float64).
  *   - The per-ray arithmetic does not depend on launch configuration, so
  *     counts are bitwise reproducible and equal between rs_shoot,
  *     rs_shoot_rows sharding, and the batched path.
- *   - Binning: u_k = (y_k - lo_k) * (npix_k / (hi_k - lo_k)); a ray is in the
- *     window iff 0 <= u_k < npix_k on both axes (NaN fails), pixel
- *     p_k = floor(u_k).  Counts are uint32, row-major [p2][p1].  A ray that
+ *   - Binning (the definition, float64): u_k = (y_k - lo_k) * (npix_k / (hi_k - lo_k));
+ *     a ray is in the window iff 0 <= u_k < npix_k on both axes (NaN fails),
+ *     pixel p_k = floor(u_k).  With certified binning (below) the counts follow
+ *     this definition applied to the exact deflection.  Counts are uint32, row-major [p2][p1].  A ray that
  *     hits a lens exactly has a non-finite deflection and is out of window.
  */
 #ifndef RS_H
@@ -76,7 +78,7 @@ typedef struct {
   int64_t n[2];
 } rs_ray_grid;
 
-/* Source-plane window: half-open [lo, hi) per axis split into npix pixels; hi > lo, npix >= 1. */
+/* Source-plane window: half-open [lo, hi) per axis split into npix pixels; hi > lo, 1 <= npix <= 2^22. */
 typedef struct {
   double lo[2];
   double hi[2];

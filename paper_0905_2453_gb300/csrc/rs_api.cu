@@ -114,6 +114,7 @@ int check_window(const rs_window* w) {
     if (!(std::isfinite(w->lo[k]) && std::isfinite(w->hi[k]) && w->hi[k] > w->lo[k]))
       return fail(RS_EINVAL, "window axis %d: need finite lo < hi", k);
     if (w->npix[k] < 1) return fail(RS_EINVAL, "window npix[%d] < 1", k);
+    if (w->npix[k] > (1 << 22)) return fail(RS_EINVAL, "window npix[%d] > 2^22", k);
     const double sc = (double)w->npix[k] / (w->hi[k] - w->lo[k]);
     if (!(std::isfinite(sc) && sc > 0.0)) return fail(RS_EINVAL, "window axis %d: degenerate pixel scale", k);
   }
@@ -247,6 +248,17 @@ int fill_desc(const rs_field* f, const rs_ray_grid* g, int64_t row_begin, int64_
   d->np1 = w->npix[1];
   d->counts = d_counts;
   d->oow = reinterpret_cast<unsigned long long*>(d_oow);
+  // float-float splits for the float32 epilogue (hi = nearest float, lo = nearest float of the rest)
+  auto split = [](double v, float& h, float& l) {
+    h = (float)v;
+    l = (float)(v - (double)h);
+  };
+  split(d->f.lam1, d->lam1h, d->lam1l);
+  split(d->f.lam2, d->lam2h, d->lam2l);
+  split(d->lo0, d->lo0h, d->lo0l);
+  split(d->lo1, d->lo1h, d->lo1l);
+  split(d->sc0, d->sc0h, d->sc0l);
+  split(d->sc1, d->sc1h, d->sc1l);
   return RS_OK;
 }
 

@@ -182,10 +182,9 @@ __global__ void __launch_bounds__(128, 2) shoot_cells_kernel(const ShootDesc d, 
       x1[k] = ray_coord(i, d.sp0, d.or0);
       x2[k] = x2r;
     }
-    double a1[RPT], a2[RPT];
-    float sig[RPT];
-    if (!deflect<RPT, rsint::kTile, MASS, false, 1>(d.f, x1, x2, a1, a2, sig, sm, ps)) return;
-    bin_rays<RPT, 1>(d, x1, x2, a1, a2, sig, valid, jrel, i_base, lane);
+    float a1h[RPT], a1l[RPT], a2h[RPT], a2l[RPT], sig[RPT];
+    if (!deflect_pairs<RPT, rsint::kTile, MASS, false, 1>(d.f, x1, x2, a1h, a1l, a2h, a2l, sig, sm, ps)) return;
+    bin_rays<RPT, 1>(d, x1, x2, a1h, a1l, a2h, a2l, sig, valid, jrel, i_base, lane);
   }
 }
 

@@ -198,6 +198,8 @@ struct ShootDesc {
   unsigned int* rc_count;     // entries requested so far (may exceed rc_cap)
   unsigned int rc_cap;        // capacity of rc_list
   int32_t field_id;           // index of this field in its batch (0 for a single-field call)
+  // float-float splits (hi + lo) of lam1, lam2, lo0, lo1, sc0, sc1 for the float32 epilogue
+  float lam1h, lam1l, lam2h, lam2l, lo0h, lo0l, lo1h, lo1l, sc0h, sc0l, sc1h, sc1l;
 };
 
 // Certified binning: a ray whose float32 source position lies within kSigmaSafety * sigma of a
@@ -518,39 +520,27 @@ __device__ __forceinline__ bool deflect_accumulate(const FieldDev& f, const uint
   return true;
 }
 
-// alpha (float64) and the error-band estimate sig of each ray from its accumulators.
+// alpha as float pairs (hi, lo: alpha = hi + lo exactly, |lo| <= ulp(hi) / 2) and the error-band
+// estimate sig of each ray from its accumulators.
 template <int RPT>
-__device__ __forceinline__ void deflect_finish(const DeflectAcc<RPT / 2>& acc, double (&a1)[RPT], double (&a2)[RPT],
-                                               float (&sig)[RPT]) {
+__device__ __forceinline__ void deflect_finish(const DeflectAcc<RPT / 2>& acc, float (&a1h)[RPT], float (&a1l)[RPT],
+                                               float (&a2h)[RPT], float (&a2l)[RPT], float (&sig)[RPT]) {
   constexpr int NP = RPT / 2;
-  const uint64_t (&H1)[NP] = acc.H1;
-  const uint64_t (&L1)[NP] = acc.L1;
-  const uint64_t (&H2)[NP] = acc.H2;
-  const uint64_t (&L2)[NP] = acc.L2;
-  const uint64_t (&SS)[NP] = acc.SS;
-  const uint64_t (&AB)[NP] = acc.AB;
 #pragma unroll
   for (int q = 0; q < NP; ++q) {
-    float h, hB, l, lB;
-    f2_unpack(H1[q], h, hB);
-    f2_unpack(L1[q], l, lB);
-    a1[2 * q] = (double)h + (double)l;
-    a1[2 * q + 1] = (double)hB + (double)lB;
-    f2_unpack(H2[q], h, hB);
-    f2_unpack(L2[q], l, lB);
-    a2[2 * q] = (double)h + (double)l;
-    a2[2 * q + 1] = (double)hB + (double)lB;
+    f2_unpack(acc.H1[q], a1h[2 * q], a1h[2 * q + 1]);
+    f2_unpack(acc.L1[q], a1l[2 * q], a1l[2 * q + 1]);
+    f2_unpack(acc.H2[q], a2h[2 * q], a2h[2 * q + 1]);
+    f2_unpack(acc.L2[q], a2l[2 * q], a2l[2 * q + 1]);
+    float s, sB, b, bB;
+    f2_unpack(acc.SS[q], s, sB);
+    f2_unpack(acc.AB[q], b, bB);
     // |alpha| enters through the float64 epilogue rounding (~1e-16 |alpha|): 8e-15 (|hi1| + |hi2|)
-    float h1a, h1b, h2a, h2b;
-    f2_unpack(H1[q], h1a, h1b);
-    f2_unpack(H2[q], h2a, h2b);
-    f2_unpack(SS[q], h, hB);
-    f2_unpack(AB[q], l, lB);
-    sig[2 * q] = kSigmaScale * sqrtf(h) + kSystematicScale * l + 8e-15f * (fabsf(h1a) + fabsf(h2a));
-    sig[2 * q + 1] = kSigmaScale * sqrtf(hB) + kSystematicScale * lB + 8e-15f * (fabsf(h1b) + fabsf(h2b));
+    sig[2 * q] = kSigmaScale * sqrtf(s) + kSystematicScale * b + 8e-15f * (fabsf(a1h[2 * q]) + fabsf(a2h[2 * q]));
+    sig[2 * q + 1] =
+        kSigmaScale * sqrtf(sB) + kSystematicScale * bB + 8e-15f * (fabsf(a1h[2 * q + 1]) + fabsf(a2h[2 * q + 1]));
   }
 }
-
 
 template <int RPT>
 __device__ __forceinline__ void pack_rays(const float (&x1)[RPT], const float (&x2)[RPT], uint64_t (&X1)[RPT / 2],
@@ -563,9 +553,10 @@ __device__ __forceinline__ void pack_rays(const float (&x1)[RPT], const float (&
 }
 
 template <int RPT, int TILE, bool MASS, bool ROW, int ROWS>
-__device__ __forceinline__ bool deflect(const FieldDev& f, const float (&x1)[RPT], const float (&x2)[RPT],
-                                        double (&a1)[RPT], double (&a2)[RPT], float (&sig)[RPT],
-                                        LensSmem<TILE, ROWS>& sm, PipeState& ps) {
+__device__ __forceinline__ bool deflect_pairs(const FieldDev& f, const float (&x1)[RPT], const float (&x2)[RPT],
+                                              float (&a1h)[RPT], float (&a1l)[RPT], float (&a2h)[RPT],
+                                              float (&a2l)[RPT], float (&sig)[RPT], LensSmem<TILE, ROWS>& sm,
+                                              PipeState& ps) {
   static_assert(RPT % 2 == 0, "rays per thread must be even (packed pairs)");
   constexpr int NP = RPT / 2;
   uint64_t X1[NP], X2[NP];
@@ -574,7 +565,22 @@ __device__ __forceinline__ bool deflect(const FieldDev& f, const float (&x1)[RPT
 #pragma unroll
   for (int q = 0; q < NP; ++q) acc.H1[q] = acc.L1[q] = acc.H2[q] = acc.L2[q] = acc.SS[q] = acc.AB[q] = 0ull;
   if (!deflect_accumulate<RPT, TILE, MASS, ROW, ROWS>(f, X1, X2, acc, sm, ps)) return false;
-  deflect_finish<RPT>(acc, a1, a2, sig);
+  deflect_finish<RPT>(acc, a1h, a1l, a2h, a2l, sig);
+  return true;
+}
+
+// As deflect_pairs, with alpha in float64 (hi + lo, exact).
+template <int RPT, int TILE, bool MASS, bool ROW, int ROWS>
+__device__ __forceinline__ bool deflect(const FieldDev& f, const float (&x1)[RPT], const float (&x2)[RPT],
+                                        double (&a1)[RPT], double (&a2)[RPT], float (&sig)[RPT],
+                                        LensSmem<TILE, ROWS>& sm, PipeState& ps) {
+  float a1h[RPT], a1l[RPT], a2h[RPT], a2l[RPT];
+  if (!deflect_pairs<RPT, TILE, MASS, ROW, ROWS>(f, x1, x2, a1h, a1l, a2h, a2l, sig, sm, ps)) return false;
+#pragma unroll
+  for (int k = 0; k < RPT; ++k) {
+    a1[k] = (double)a1h[k] + (double)a1l[k];
+    a2[k] = (double)a2h[k] + (double)a2l[k];
+  }
   return true;
 }
 
@@ -586,42 +592,85 @@ __device__ __forceinline__ float band_halfwidth(float sig, float lamabs, float x
 }
 
 // ----------------------------------------------------------------------------------------------
+// One axis of Eq. 6 and of the pixel coordinate in float-float: y = lam x - alpha and
+// u = (y - lo) * sc with lam, lo, sc given as float pairs (hi + lo) and alpha = ah + al.  Returns
+// kUOk with p = floor(u) and f = u - p in [0, 1) (rounded to float); kUFar if |u| >= 2^22; kUNaN if
+// u is not a number (a ray on a lens).  eu bounds the float-float rounding of u (2^-40 of the
+// magnitudes involved; the arithmetic keeps ~2^-45).
+// ----------------------------------------------------------------------------------------------
+constexpr int kUOk = 0, kUFar = 1, kUNaN = 2;
+
+__device__ __forceinline__ int ff_pixel(float x, float lh, float ll, float ah, float al, float loh, float lol,
+                                        float sch, float scl, int& p, float& f, float& eu) {
+  const float pr = __fmul_rn(lh, x);
+  const float pe = __fmaf_rn(lh, x, -pr);                 // lh x = pr + pe exactly
+  float s = __fadd_rn(pr, -ah);
+  float bb = __fsub_rn(s, pr);
+  float t = __fadd_rn(__fsub_rn(pr, __fsub_rn(s, bb)), __fsub_rn(-ah, bb));  // pr - ah = s + t exactly
+  t = __fadd_rn(t, __fadd_rn(pe, __fmaf_rn(ll, x, -al)));   // y = s + t
+  float v = __fadd_rn(s, -loh);
+  bb = __fsub_rn(v, s);
+  float w = __fadd_rn(__fsub_rn(s, __fsub_rn(v, bb)), __fsub_rn(-loh, bb));  // s - loh = v + w exactly
+  w = __fadd_rn(w, __fsub_rn(t, lol));                    // y - lo = v + w
+  const float uh = __fmul_rn(v, sch);
+  const float ue = __fadd_rn(__fmaf_rn(v, sch, -uh), __fmaf_rn(w, sch, __fmul_rn(v, scl)));  // u = uh + ue
+  eu = 0x1p-40f * ((fabsf(pr) + fabsf(ah) + fabsf(loh)) * sch + fabsf(uh) + 1.f);
+  if (!(fabsf(uh) < 0x1p22f)) {
+    p = -1;
+    f = 0.f;
+    return (uh == uh && ue == ue) ? kUFar : kUNaN;
+  }
+  float kf = floorf(uh);
+  float fr = __fadd_rn(__fsub_rn(uh, kf), ue);            // uh - kf is exact
+  if (fr < 0.f) {
+    kf -= 1.f;
+    fr = __fadd_rn(fr, 1.f);
+  } else if (fr >= 1.f) {
+    kf += 1.f;
+    fr = __fsub_rn(fr, 1.f);
+  }
+  if (fr >= 1.f) fr = 0x1.fffffep-1f;                     // rounding of a fraction just below 1
+  p = (int)kf;
+  f = fr;
+  return kUOk;
+}
+
+// ----------------------------------------------------------------------------------------------
 // Eq. 6 and binning of a thread's RPT rays (ray k at grid column i_base + STRIDE k of call row
 // jrel): counts, the out-of-window count, and, with certified binning, the list of rays to
 // re-evaluate in float-float.  Every lane of the warp must call it (warp-aggregated atomics).
 // ----------------------------------------------------------------------------------------------
 template <int RPT, int STRIDE>
 __device__ __forceinline__ void bin_rays(const ShootDesc& d, const float (&x1)[RPT], const float (&x2)[RPT],
-                                         const double (&a1)[RPT], const double (&a2)[RPT], const float (&sig)[RPT],
-                                         const bool (&valid)[RPT], int64_t jrel, int64_t i_base, int lane) {
+                                         const float (&a1h)[RPT], const float (&a1l)[RPT], const float (&a2h)[RPT],
+                                         const float (&a2l)[RPT], const float (&sig)[RPT], const bool (&valid)[RPT],
+                                         int64_t jrel, int64_t i_base, int lane) {
   unsigned oow_lane = 0;
 #pragma unroll
   for (int k = 0; k < RPT; ++k) {
-    // Eq. 6 in float64: product rounded, then difference rounded (no fma), as specified
-    const double y1 = __dsub_rn(__dmul_rn(d.f.lam1, (double)x1[k]), a1[k]);
-    const double y2 = __dsub_rn(__dmul_rn(d.f.lam2, (double)x2[k]), a2[k]);
-    const double u1 = __dmul_rn(__dsub_rn(y1, d.lo0), d.sc0);
-    const double u2 = __dmul_rn(__dsub_rn(y2, d.lo1), d.sc1);
-    // pixel index in float64 (as the definition); |u| >= 2^31 or NaN is out of any window
-    const bool fin = (fabs(u1) < 2147483648.0) && (fabs(u2) < 2147483648.0);
-    const double fl1 = floor(u1), fl2 = floor(u2);
-    const int p1 = fin ? (int)fl1 : -1;
-    const int p2 = fin ? (int)fl2 : -1;
-    const bool inwin = fin && (p1 >= 0) && (p1 < d.np0) && (p2 >= 0) && (p2 < d.np1);
+    // Eq. 6 and u = (y - lo) * npix / (hi - lo) in float-float (~2^-44 relative): pixel index p and
+    // fraction f of u, and the bound eu on the float-float rounding (pixel units)
+    int p1, p2;
+    float f1, f2, eu1, eu2;
+    const int st1 = ff_pixel(x1[k], d.lam1h, d.lam1l, a1h[k], a1l[k], d.lo0h, d.lo0l, d.sc0h, d.sc0l, p1, f1, eu1);
+    const int st2 = ff_pixel(x2[k], d.lam2h, d.lam2l, a2h[k], a2l[k], d.lo1h, d.lo1l, d.sc1h, d.sc1l, p2, f2, eu2);
+    const bool inwin = st1 == kUOk && st2 == kUOk && (p1 >= 0) && (p1 < d.np0) && (p2 >= 0) && (p2 < d.np1);
     bool bin_now = valid[k];
     if (d.rc_list != nullptr) {
       // Certain: the band [u - du, u + du] lies inside one pixel of the window, or outside the window
-      // on some axis.  Tested in float with margins for the float rounding of u (~|u| 2^-23) and of
-      // the exact fractional part f = u - floor(u).
+      // on some axis.  Margins: the band in pixel units, the float-float rounding, and 1e-7 for the
+      // float rounding of the fraction.
       const float band = band_halfwidth(sig[k], d.f.lamabs, x1[k], x2[k]);
-      const float du1 = band * d.scf0, du2 = band * d.scf1;
-      const float f1 = (float)(u1 - fl1), f2 = (float)(u2 - fl2);
-      const float uf1 = (float)p1 + f1, uf2 = (float)p2 + f2;
-      const float mo1 = du1 + 1.2e-7f * fabsf(uf1) + 1e-7f, mo2 = du2 + 1.2e-7f * fabsf(uf2) + 1e-7f;
-      const float mf1 = du1 + 1e-7f, mf2 = du2 + 1e-7f;
-      const bool out_sure = !fin || (uf1 + mo1 < 0.f) || (uf1 - mo1 >= (float)d.np0) || (uf2 + mo2 < 0.f) ||
-                            (uf2 - mo2 >= (float)d.np1);
-      const bool in_sure = inwin && (f1 >= mf1) && (f1 <= 1.f - mf1) && (f2 >= mf2) && (f2 <= 1.f - mf2);
+      const float m1 = band * d.scf0 + eu1 + 1e-7f, m2 = band * d.scf1 + eu2 + 1e-7f;
+      // with u = p + f: u + m < 0 iff p <= -2, or p = -1 and 1 - f > m; u - m >= np iff p > np, or
+      // p = np and f >= m (margins below 1/2; wider bands are never certain)
+      const bool ok1 = st1 == kUOk && m1 < 0.5f, ok2 = st2 == kUOk && m2 < 0.5f;
+      const bool out1 = ok1 && (p1 <= -2 || (p1 == -1 && 1.f - f1 > m1) || p1 > d.np0 || (p1 == d.np0 && f1 >= m1));
+      const bool out2 = ok2 && (p2 <= -2 || (p2 == -1 && 1.f - f2 > m2) || p2 > d.np1 || (p2 == d.np1 && f2 >= m2));
+      // a non-finite position is out of window by definition; |u| >= 2^22 is when the window is narrower
+      const bool out_sure = st1 == kUNaN || st2 == kUNaN || (st1 == kUFar && d.np0 <= (1 << 21)) ||
+                            (st2 == kUFar && d.np1 <= (1 << 21)) || out1 || out2;
+      const bool in_sure = inwin && ok1 && ok2 && (f1 >= m1) && (f1 <= 1.f - m1) && (f2 >= m2) && (f2 <= 1.f - m2);
       const bool need = valid[k] && !out_sure && !in_sure;
       const unsigned mask = __ballot_sync(0xffffffffu, need);
       if (mask != 0u) {
@@ -646,7 +695,6 @@ __device__ __forceinline__ void bin_rays(const ShootDesc& d, const float (&x1)[R
   }
   if (d.oow != nullptr && lane == 0 && oow_lane != 0) atomicAdd(d.oow, (unsigned long long)oow_lane);
 }
-
 
 // ----------------------------------------------------------------------------------------------
 // Ray tiles of a shoot call.  A CTA of WARPS warps covers WARPS consecutive grid rows (one per
@@ -681,10 +729,9 @@ __device__ __forceinline__ bool shoot_tile(const ShootDesc& d, int64_t tile, Len
     x2[k] = x2r;
   }
   if (lane == 0) sm.x2row[warp] = x2r;  // read by build_row_table after the first tile barrier
-  double a1[RPT], a2[RPT];
-  float sig[RPT];
-  if (!deflect<RPT, TILE, MASS, true, WARPS>(d.f, x1, x2, a1, a2, sig, sm, ps)) return false;
-  bin_rays<RPT, 32>(d, x1, x2, a1, a2, sig, valid, jrel, tcol * SEG + lane, lane);
+  float a1h[RPT], a1l[RPT], a2h[RPT], a2l[RPT], sig[RPT];
+  if (!deflect_pairs<RPT, TILE, MASS, true, WARPS>(d.f, x1, x2, a1h, a1l, a2h, a2l, sig, sm, ps)) return false;
+  bin_rays<RPT, 32>(d, x1, x2, a1h, a1l, a2h, a2l, sig, valid, jrel, tcol * SEG + lane, lane);
   return true;
 }
 

@@ -72,10 +72,9 @@ __global__ void __launch_bounds__(kBlock, 2) staged_kernel(const ShootDesc d, ui
     state_io(st, acc, true);
     return;
   }
-  double a1[kRpt], a2[kRpt];
-  float sig[kRpt];
-  deflect_finish<kRpt>(acc, a1, a2, sig);
-  bin_rays<kRpt, 32>(d, x1, x2, a1, a2, sig, valid, jrel, tcol * SEG + lane, lane);
+  float a1h[kRpt], a1l[kRpt], a2h[kRpt], a2l[kRpt], sig[kRpt];
+  deflect_finish<kRpt>(acc, a1h, a1l, a2h, a2l, sig);
+  bin_rays<kRpt, 32>(d, x1, x2, a1h, a1l, a2h, a2l, sig, valid, jrel, tcol * SEG + lane, lane);
 }
 
 // ---- float-float re-evaluation of the listed rays, partition by partition ----------------------
