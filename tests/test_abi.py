@@ -97,7 +97,8 @@ def test_grid_window_validation(rs):
         assert lib.rs_shoot(fake, ctypes.byref(g), ctypes.byref(w), ctypes.c_void_p(16), None, None) == rs.RS_EINVAL
     g = rs._cgrid(rs.RayGrid((0.0, 0.0), (1.0, 1.0), (4, 4)))
     for bw in [rs.Window((1.0, -1.0), (1.0, 1.0), (4, 4)), rs.Window((-1.0, -1.0), (1.0, 1.0), (0, 4)),
-               rs.Window((-1.0, float("inf")), (1.0, 1.0), (4, 4))]:
+               rs.Window((-1.0, float("inf")), (1.0, 1.0), (4, 4)),
+               rs.Window((-1.0, -1.0), (1.0, 1.0), ((1 << 22) + 1, 1))]:
         ww = rs._cwin(bw)
         assert lib.rs_shoot(fake, ctypes.byref(g), ctypes.byref(ww), ctypes.c_void_p(16), None, None) == rs.RS_EINVAL
     # row range outside the grid
