@@ -288,3 +288,21 @@ def test_n1e8_sampled_rays():
     f = ri.n1e8_field()
     ij = ri.sample_rays(f.grid, 64, seed=41)
     _check_per_ray(f, ij, "N=1e8", rigorous=False)
+
+
+def test_far_from_origin_certified_map():
+    """Lenses, rays and window far from the origin (|y| ~ 3e4, pixels of 2e-3): the float-float epilogue
+    must resolve u = (y - lo) / pix where y and lo nearly cancel; the certified map equals the oracle's."""
+    cx, cy = 30000.0, -20000.0
+    rng = np.random.default_rng(17)
+    r = 6.0 * np.sqrt(rng.random(60))
+    th = 2 * np.pi * rng.random(60)
+    xy = np.stack([cx + r * np.cos(th), cy + r * np.sin(th)], 1).astype(np.float32)
+    g = ri.RayGrid(origin=(cx - 4.0 + 1 / 256, cy - 4.0 + 1 / 256), spacing=(1 / 128, 1 / 128), n=(1024, 1024))
+    # no shear, no smooth convergence: y ~ x - alpha stays near (cx, cy)
+    w = ri.Window(lo=(cx - 0.25, cy - 0.25), hi=(cx + 0.25, cy + 0.25), npix=(250, 250))
+    f = ri.Field("far", xy, None, 0.0, 0.0, g, w)
+    counts, oow = shoot_gpu(f)
+    ref, oref = oracle.shoot_field(f)
+    assert counts.sum() > 0
+    assert np.array_equal(counts, ref) and oow == oref
