@@ -274,19 +274,21 @@ def test_certified_trace_matches_oracle_large_fields():
 
 
 def test_n1e6_salpeter_sampled_rays_float32_and_map_invariants():
-    """1e6 Salpeter lenses, 16384^2 grid: sampled rays (float32 path within its bounds and bands),
-    and the certified map of a 1024-row block conserves rays."""
+    """1e6 Salpeter lenses, 16384^2 grid: 1e5 sampled rays (float32 path within its band, float-float
+    within 1e-5 px; the rigorous operation-count bound on 256 of them), and the certified map of a
+    1024-row block conserves rays."""
     f = ri.n1e6_salpeter_field()
-    ij = ri.sample_rays(f.grid, 256, seed=31)
-    y_gpu, y_ref, st = _check_per_ray(f, ij, "N=1e6")
+    ij = ri.sample_rays(f.grid, 100000, seed=31)
+    _check_per_ray(f, ij[:256], "N=1e6 (bound)")
+    y_gpu, y_ref, st = _check_per_ray(f, ij, "N=1e6", rigorous=False)
     counts, oow = shoot_gpu(f, rows=(7680, 8704))
     assert int(counts.sum()) + oow == 1024 * f.grid.n[0]
 
 
 def test_n1e8_sampled_rays():
-    """1e8 lenses with stored unit masses (2.4 GB on the device), 8192^2 grid: 64 sampled rays."""
+    """1e8 lenses with stored unit masses (2.4 GB on the device), 8192^2 grid: 512 sampled rays."""
     f = ri.n1e8_field()
-    ij = ri.sample_rays(f.grid, 64, seed=41)
+    ij = ri.sample_rays(f.grid, 512, seed=41)
     _check_per_ray(f, ij, "N=1e8", rigorous=False)
 
 
