@@ -355,6 +355,7 @@ def run_ours(args):
     batched = None
     if not args.no_batch and world == 1:
         batched = run_batched(rs, torch, device, stream, reps=args.batch_reps)
+        batched["small_fields"] = run_batched_small(rs, torch, device, stream)
 
     # ---------------- light curves over many maps (one launch)
     light = None
@@ -423,6 +424,50 @@ def run_ours(args):
     print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
+
+
+def run_batched_small(rs, torch, device, stream, n_fields=256, reps=5):
+    """Many small maps (the 100-lens, 1000^2-ray configuration, seeds 2000 + k): one persistent graph
+    launch against one rs_shoot call per field (each: list allocation, shoot, re-evaluation)."""
+    specs = [ri.tiny_field(seed=2000 + k) for k in range(n_fields)]
+    fields = [rs.Field.from_spec(s, stream) for s in specs]
+    b = rs.Batch(fields, [s.grid for s in specs], [s.window for s in specs])
+    counts_plain = [torch.zeros_like(c) for c in b.counts]
+    oow_plain = torch.zeros(len(specs), dtype=torch.int64, device=device)
+
+    def plain():
+        for c in counts_plain:
+            c.zero_()
+        oow_plain.zero_()
+        for k, f in enumerate(fields):
+            rs.rs_shoot(f.handle, specs[k].grid, specs[k].window, counts_plain[k], oow_plain[k:k + 1], stream)
+
+    b.launch(stream)
+    plain()
+    torch.cuda.synchronize(device)
+    same = all(torch.equal(b.counts[k], counts_plain[k]) for k in range(len(specs))) and \
+        torch.equal(b.out_of_window, oow_plain)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        b.launch(stream)
+    e1.record(stream)
+    torch.cuda.synchronize(device)
+    t_batch = e0.elapsed_time(e1) / 1e3 / reps
+    t0 = time.perf_counter()
+    e0.record(stream)
+    for _ in range(reps):
+        plain()
+    e1.record(stream)
+    torch.cuda.synchronize(device)
+    t_plain = max(e0.elapsed_time(e1) / 1e3, time.perf_counter() - t0) / reps
+    inter = sum(s.interactions for s in specs)
+    b.close()
+    for f in fields:
+        f.close()
+    return {"workload": f"{n_fields} fields of 100 equal-mass lenses, 1000^2 rays, 256^2 maps",
+            "maps_per_s": n_fields / t_batch, "plain_maps_per_s": n_fields / t_plain, "speedup": t_plain / t_batch,
+            "interactions_per_s": inter / t_batch, "bitwise_equal": bool(same), "reps": reps}
 
 
 def run_batched(rs, torch, device, stream, reps=3):
@@ -606,6 +651,8 @@ def run_section(args):
             rs.rs_set_launch_config(spec.masses is not None, b_, r_)
         out = {"zoom": run_zoom(rs, torch, device, stream, spec),
                "culled_full_map": run_zoom(rs, torch, device, stream, spec, factor=1, quarter=False)}
+    elif args.section == "batch-small":
+        out = {"small_fields": run_batched_small(rs, torch, device, stream)}
     elif args.section == "staged":
         spec = workload(args.workload, seed=0)
         out = {"staged": run_staged(rs, torch, device, stream, spec)}
@@ -737,7 +784,7 @@ def main():
     ap.add_argument("--no-zoom", action="store_true")
     ap.add_argument("--no-frames", action="store_true")
     ap.add_argument("--no-staged", action="store_true")
-    ap.add_argument("--section", choices=["zoom", "light-curves", "frames", "staged"], default=None,
+    ap.add_argument("--section", choices=["zoom", "light-curves", "frames", "staged", "batch-small"], default=None,
                     help="run one secondary measurement alone and print its JSON object (for profiling)")
     ap.add_argument("--batch-reps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
