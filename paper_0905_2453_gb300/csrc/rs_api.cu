@@ -136,6 +136,18 @@ struct DeviceGuard {
   }
 };
 
+// The arguments every shoot call shares: grid, row range, window and the counts buffer.
+int check_call(const rs_ray_grid* g, int64_t row_begin, int64_t row_end, const rs_window* w, const uint32_t* d_counts) {
+  int rc;
+  if ((rc = check_grid(g)) != RS_OK) return rc;
+  if ((rc = check_window(w)) != RS_OK) return rc;
+  if (!d_counts) return fail(RS_EINVAL, "d_counts is NULL");
+  if (row_begin < 0 || row_end < row_begin || row_end > g->n[1])
+    return fail(RS_EINVAL, "row range [%lld, %lld) outside [0, %lld]", (long long)row_begin, (long long)row_end,
+                (long long)g->n[1]);
+  return RS_OK;
+}
+
 int check_field_device(const rs_field* f) {
   int cur = -1;
   cudaError_t e = cudaGetDevice(&cur);
@@ -625,12 +637,7 @@ int rs_shoot_rows(rs_field_t f, const rs_ray_grid* g, int64_t row_begin, int64_t
                   uint32_t* d_counts, uint64_t* d_out_of_window, void* stream) {
   if (!f) return fail(RS_EINVAL, "field is NULL");
   int rc;
-  if ((rc = check_grid(g)) != RS_OK) return rc;
-  if ((rc = check_window(w)) != RS_OK) return rc;
-  if (!d_counts) return fail(RS_EINVAL, "d_counts is NULL");
-  if (row_begin < 0 || row_end < row_begin || row_end > g->n[1])
-    return fail(RS_EINVAL, "row range [%lld, %lld) outside [0, %lld]", (long long)row_begin, (long long)row_end,
-                (long long)g->n[1]);
+  if ((rc = check_call(g, row_begin, row_end, w, d_counts)) != RS_OK) return rc;
   if ((rc = check_field_device(f)) != RS_OK) return rc;
   ShootDesc d;
   if ((rc = fill_desc(f, g, row_begin, row_end, w, d_counts, d_out_of_window, &d)) != RS_OK) return rc;
@@ -661,12 +668,7 @@ int rs_shoot_culled(rs_field_t f, const rs_ray_grid* g, int64_t row_begin, int64
                     uint32_t* d_counts, uint64_t* d_out_of_window, uint64_t* d_rays_shot, void* stream) {
   if (!f) return fail(RS_EINVAL, "field is NULL");
   int rc;
-  if ((rc = check_grid(g)) != RS_OK) return rc;
-  if ((rc = check_window(w)) != RS_OK) return rc;
-  if (!d_counts) return fail(RS_EINVAL, "d_counts is NULL");
-  if (row_begin < 0 || row_end < row_begin || row_end > g->n[1])
-    return fail(RS_EINVAL, "row range [%lld, %lld) outside [0, %lld]", (long long)row_begin, (long long)row_end,
-                (long long)g->n[1]);
+  if ((rc = check_call(g, row_begin, row_end, w, d_counts)) != RS_OK) return rc;
   if ((rc = check_field_device(f)) != RS_OK) return rc;
   ShootDesc d;
   if ((rc = fill_desc(f, g, row_begin, row_end, w, d_counts, d_out_of_window, &d)) != RS_OK) return rc;
@@ -725,12 +727,7 @@ int rs_shoot_staged(int n_parts, const rs_field_t* parts, const rs_ray_grid* g, 
                   (long long)a->n_lens, rsdev::kRenorm);
   }
   int rc;
-  if ((rc = check_grid(g)) != RS_OK) return rc;
-  if ((rc = check_window(w)) != RS_OK) return rc;
-  if (!d_counts) return fail(RS_EINVAL, "d_counts is NULL");
-  if (row_begin < 0 || row_end < row_begin || row_end > g->n[1])
-    return fail(RS_EINVAL, "row range [%lld, %lld) outside [0, %lld]", (long long)row_begin, (long long)row_end,
-                (long long)g->n[1]);
+  if ((rc = check_call(g, row_begin, row_end, w, d_counts)) != RS_OK) return rc;
   if ((rc = check_field_device(parts[0])) != RS_OK) return rc;
   ShootDesc d;
   if ((rc = fill_desc(parts[0], g, row_begin, row_end, w, d_counts, d_out_of_window, &d)) != RS_OK) return rc;
@@ -794,12 +791,7 @@ int rs_shoot_streamed(const float* h_lens_xy, const float* h_masses, int64_t n_l
     for (int64_t i = 0; i < n_lens; ++i)
       if (!(std::isfinite(h_masses[i]) && h_masses[i] >= 0.f)) return fail(RS_EINVAL, "mass %lld not finite or negative", (long long)i);
   int rc;
-  if ((rc = check_grid(g)) != RS_OK) return rc;
-  if ((rc = check_window(w)) != RS_OK) return rc;
-  if (!d_counts) return fail(RS_EINVAL, "d_counts is NULL");
-  if (row_begin < 0 || row_end < row_begin || row_end > g->n[1])
-    return fail(RS_EINVAL, "row range [%lld, %lld) outside [0, %lld]", (long long)row_begin, (long long)row_end,
-                (long long)g->n[1]);
+  if ((rc = check_call(g, row_begin, row_end, w, d_counts)) != RS_OK) return rc;
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
@@ -1347,12 +1339,7 @@ extern "C" int rs_shoot_rows_noalloc(rs_field_t f, const rs_ray_grid* g, int64_t
                                      void* stream) {
   if (!f) return fail(RS_EINVAL, "field is NULL");
   int rc;
-  if ((rc = check_grid(g)) != RS_OK) return rc;
-  if ((rc = check_window(w)) != RS_OK) return rc;
-  if (!d_counts) return fail(RS_EINVAL, "d_counts is NULL");
-  if (row_begin < 0 || row_end < row_begin || row_end > g->n[1])
-    return fail(RS_EINVAL, "row range [%lld, %lld) outside [0, %lld]", (long long)row_begin, (long long)row_end,
-                (long long)g->n[1]);
+  if ((rc = check_call(g, row_begin, row_end, w, d_counts)) != RS_OK) return rc;
   if ((rc = check_field_device(f)) != RS_OK) return rc;
   ShootDesc d;
   if ((rc = fill_desc(f, g, row_begin, row_end, w, d_counts, d_out_of_window, &d)) != RS_OK) return rc;
