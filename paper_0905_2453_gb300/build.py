@@ -1,8 +1,8 @@
 """Build librs.so in-tree with nvcc for sm_103a (GB300).
 
-Three translation units are compiled in parallel (plain/trace kernels, the
-persistent batch kernel, the C-ABI host layer) and linked into
-``paper_0905_2453_gb300/librs.so``.  No PyTorch headers or libraries are
+The translation units (C-ABI host layer; plain, trace, batch, float-float
+re-evaluation, light-curve, culled and staged kernels) are compiled in parallel
+and linked into ``paper_0905_2453_gb300/librs.so``.  No PyTorch headers or libraries are
 involved: the library is plain CUDA C++ with a C ABI (``include/rs.h``).
 """
 from __future__ import annotations
