@@ -35,7 +35,7 @@
  *     the pairs (three of every four with unit masses, every other pair with
  *     per-lens masses) one reciprocal of the product of the two squared
  *     distances serves both lenses (Montgomery's simultaneous inversion).
- *     Per ray, partial sums over consecutive groups of 32 lenses (in lens index
+ *     Per ray, partial sums over consecutive groups of 64 lenses (in lens index
  *     order) are folded into a two-float (hi, lo) accumulator with an
  *     error-free TwoSum; (hi, lo) is renormalised after every 256 lenses.  With
  *     alpha = hi + lo, Eq. 6 and the pixel coordinate u are evaluated in
@@ -224,8 +224,8 @@ int rs_trace_certified(rs_field_t f, const rs_ray_grid* g, const int64_t* d_ray_
 
 /*
  * Certified binning (on by default).  The float32 shoot attaches to every ray an error band:
- * 10 u sqrt(32 sum_g (P1_g^2 + P2_g^2)) + 2 u sum_g (|P1_g| + |P2_g|) (u = 2^-24, P_g the float32
- * partial sums of its 32-lens groups): the random rounding, plus coherent errors (the far field
+ * 10 u sqrt(64 sum_g (P1_g^2 + P2_g^2)) + 2 u sum_g (|P1_g| + |P2_g|) (u = 2^-24, P_g the float32
+ * partial sums of its 64-lens groups): the random rounding, plus coherent errors (the far field
  * sees the ray's coordinate only to the precision of the lens-ray difference; a bias of the
  * approximate reciprocal).  A ray whose source position lies within that band of a pixel or window edge is
  * not binned by the float32 result but re-evaluated with rs_trace_certified's arithmetic and

@@ -17,12 +17,13 @@
 //     two rcp.approx (MUFU), [mul.f32x2 by the mass], fma.f32x2 x2.  These are
 //     the ten flops per interaction of the paper's Appendix A; the reciprocal
 //     on the MUFU pipe sets the throughput ceiling.
-//   * Per ray, each group of kGroup = 32 consecutive lenses is summed from zero
+//   * Per ray, each group of kGroup = 64 consecutive lenses is summed from zero
 //     in float32, then folded into a two-float (hi, lo) accumulator with an
 //     error-free TwoSum, so the deflection keeps its low-order bits over 1e8
-//     lenses.  alpha = hi + lo, Eq. 6 and the pixel index are evaluated in
-//     float64 once per ray (the only float64 work, Section 4's remark on
-//     using double precision only where it is needed).
+//     lenses.  alpha = hi + lo, Eq. 6 and the pixel coordinate are evaluated
+//     in float-float once per ray (Section 4's remark on using extra precision
+//     only where it is needed; float64 only for the ray coordinates and for
+//     rays re-evaluated by certified binning).
 //   * Binning: one global atomic add per in-window ray; out-of-window rays
 //     are counted per warp with a ballot and one 64-bit atomic per warp.
 //
@@ -36,7 +37,7 @@
 
 namespace rsdev {
 
-constexpr int kGroup = 32;                 // lenses per float32 partial sum (fixed: part of the arithmetic)
+constexpr int kGroup = 64;                 // lenses per float32 partial sum (fixed: part of the arithmetic)
 constexpr int kRenorm = 256;               // (hi, lo) renormalised after every 256 lenses (fixed: arithmetic)
 constexpr int kLensPad = 1024;             // device lens arrays are padded to a multiple of this
 constexpr uint64_t kWaitLimitNs = 1000000000ull;  // bounded mbarrier wait: 1 s
@@ -206,9 +207,9 @@ struct ShootDesc {
 // pixel edge (sigma: the per-ray error estimate below) is re-evaluated in float-float arithmetic
 // before it is counted.
 constexpr float kSigmaSafety = 10.0f;
-// sigma = u sqrt(32 sum_g (P1_g^2 + P2_g^2)): the rounding of a 32-lens float32 group partial is a
-// random walk of at most 32 steps of ~u |P_g|; u = 2^-24.
-constexpr float kSigmaScale = 5.9604645e-08f * 5.656854249f * kSigmaSafety;
+// sigma = u sqrt(64 sum_g (P1_g^2 + P2_g^2)): the rounding of a 64-lens float32 group partial is a
+// random walk of at most 64 steps of ~u |P_g|; u = 2^-24.
+constexpr float kSigmaScale = 5.9604645e-08f * 8.0f * kSigmaSafety;
 // Coherent errors: the rounding of d1 = x1 - x1_lens keeps the ray's x1 only to ulp(d1) for lenses
 // much farther away than |x1| -- the same shift for every lens of a binade, i.e. a systematic
 // displacement of the ray seen by the far field -- and a bias of the approximate reciprocal
@@ -399,7 +400,7 @@ struct DeflectAcc {
 };
 
 // Accumulate the field's lenses into acc (X1/X2: packed ray coordinates).  The arithmetic depends on
-// a lens's index within the field only through the group (32) and renormalisation (256) schedule,
+// a lens's index within the field only through the group (64) and renormalisation (256) schedule,
 // so a field split into parts of multiples of 256 lenses, accumulated part after part, gives
 // bitwise the sums of the whole field.  Returns false if a bounded wait gave up (the CTA must then
 // stop; the status word has been set).

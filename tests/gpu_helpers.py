@@ -119,9 +119,9 @@ U32 = 2.0 ** -24
 # Worst-case relative error constants of the float32 body (units of u = 2^-24):
 #   per term: d1/d2 rounding (1), d^2 and the fma forming r^2 (2), rcp.approx (<= 1 ulp: 2),
 #   shared-reciprocal product and back-multiply (2), mass multiply (1)          -> 8
-#   accumulation of a 32-lens group in float32: gamma_32 ~ 32                   -> 32
-# The (hi, lo) TwoSum fold across groups is error-free; the float64 epilogue adds ~1e-16.
-K_TERM, K_GROUP = 8.0, 32.0
+#   accumulation of a 64-lens group in float32: gamma_64 ~ 64                   -> 64
+# The (hi, lo) TwoSum fold across groups is error-free; rs_trace's float64 epilogue adds ~1e-16.
+K_TERM, K_GROUP = 8.0, 64.0
 
 
 def per_ray_bound(field_spec, x, y_ref):
