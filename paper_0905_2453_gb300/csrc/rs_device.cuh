@@ -1,10 +1,10 @@
 // Device side of the inverse ray-shooting path (sm_103a).
 //
 // What one CTA computes: a tile of BLOCK x RPT rays of a regular image-plane
-// grid, deflected by all lenses of a field (Eq. 2, a direct sum; the paper's
-// ray x lens decomposition of Eq. 5 with lens tiles staged through shared
-// memory, Section 2.2), mapped to the source plane with the macro-model of
-// Eq. 6 and binned into a uint32 count map (Eq. 4 counts).
+// grid (one grid row per warp), deflected by all lenses of a field (Eq. 2, a
+// direct sum; the paper's ray x lens decomposition of Eq. 5 with lens tiles
+// staged through shared memory, Section 2.2), mapped to the source plane with
+// the macro-model of Eq. 6 and binned into a uint32 count map (Eq. 4 counts).
 //
 // GB300 mapping
 //   * Lens tiles of TILE lenses are copied global -> shared by the bulk-copy
@@ -13,10 +13,14 @@
 //   * Lenses are stored duplicated, {x1, x1, x2, x2} (and {m, m}), so one
 //     shared-memory load yields the 64-bit operand pairs of the packed
 //     f32x2 instructions: every packed op advances two rays against one lens.
-//   * Per lens and ray pair: sub.f32x2 x2, mul.f32x2, fma.f32x2 (|d|^2),
-//     two rcp.approx (MUFU), [mul.f32x2 by the mass], fma.f32x2 x2.  These are
-//     the ten flops per interaction of the paper's Appendix A; the reciprocal
-//     on the MUFU pipe sets the throughput ceiling.
+//   * The rays of a warp share one grid row, so (x2 - x2_lens) and its square
+//     come from a per-row table built in shared memory once per lens tile.
+//   * Per lens and ray pair: sub.f32x2, fma.f32x2 (|d|^2), the reciprocal,
+//     [mul.f32x2 by the mass], fma.f32x2 x2 -- the ten flops per interaction of
+//     the paper's Appendix A.  For three of every four lens pairs (unit masses;
+//     one of two with masses) one rcp.approx of the product of the two squared
+//     distances serves both lenses (Montgomery's simultaneous inversion), which
+//     balances the MUFU pipe (16 reciprocals/clk/SM) against the FMA pipe.
 //   * Per ray, each group of kGroup = 64 consecutive lenses is summed from zero
 //     in float32, then folded into a two-float (hi, lo) accumulator with an
 //     error-free TwoSum, so the deflection keeps its low-order bits over 1e8
