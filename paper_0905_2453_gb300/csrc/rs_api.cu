@@ -380,7 +380,7 @@ extern "C" {
 
 const char* rs_last_error(void) { return g_err.c_str(); }
 
-const char* rs_version(void) { return "rs-gb300 0.1 (sm_103a)"; }
+const char* rs_version(void) { return "rs-gb300 0.2 (sm_103a)"; }
 
 int rs_set_launch_config(int has_masses, int block, int rays_per_thread) {
   const int c = rsint::find_cfg(block, rays_per_thread);

@@ -5,7 +5,7 @@ thread, see ``rs_launch_configs``).  All of them compute bitwise identical
 results, so the choice only affects speed.  ``autotune`` times every shape on a
 proxy run (a block of the workload's own grid rows) with CUDA events, selects the
 fastest with ``rs_set_launch_config`` and caches the choice in a JSON file keyed
-by (GPU name, mass mode, lens-count bucket, row-length bucket).  This replaces the
+by (GPU name, library version, mass mode, lens-count bucket, row-length bucket).  This replaces the
 paper's occupancy-calculator choice of 128 or 256 threads (Section 2.2).
 """
 from __future__ import annotations
@@ -16,7 +16,7 @@ import os
 
 import torch
 
-from . import rs_launch_configs, rs_set_launch_config, rs_shoot_rows
+from . import rs_launch_configs, rs_set_launch_config, rs_shoot_rows, rs_version
 
 DEFAULT_CACHE = os.path.join(os.environ.get("XDG_CACHE_HOME", os.path.expanduser("~/.cache")),
                              "rs_gb300", "tune.json")
@@ -29,7 +29,8 @@ def _bucket(v: int) -> int:
 def cache_key(field, grid) -> str:
     n_lens, has_mass = field.info()
     name = torch.cuda.get_device_name(torch.cuda.current_device())
-    return f"{name}|mass={int(has_mass)}|N=2^{_bucket(n_lens)}|n0=2^{_bucket(int(grid.n[0]))}"
+    return (f"{name}|{rs_version()}|mass={int(has_mass)}|N=2^{_bucket(n_lens)}"
+            f"|n0=2^{_bucket(int(grid.n[0]))}")
 
 
 def _load(path):
