@@ -23,13 +23,17 @@ import torch
 from . import build as _build
 
 __all__ = [
-    "RS_OK", "RS_EINVAL", "RS_ENOMEM", "RS_ECUDA", "RS_EOVERFLOW", "RS_ETIMEOUT", "RSError",
-    "RayGrid", "Window", "Field", "Batch", "load", "lib_path",
+    "RS_OK", "RS_EINVAL", "RS_ENOMEM", "RS_ECUDA", "RS_EOVERFLOW", "RS_ETIMEOUT", "RS_PROFILE_GAUSSIAN",
+    "RS_PROFILE_DISC", "RSError", "RayGrid", "Window", "Track", "Field", "Batch", "LightCurvePlan", "load",
+    "lib_path", "magnification", "light_curves", "zoom_grid", "zoom_window", "EXPORTED_SYMBOLS",
     "rs_create_field", "rs_destroy_field", "rs_field_info", "rs_shoot", "rs_shoot_rows", "rs_trace",
     "rs_magnification", "rs_batch_create", "rs_batch_launch", "rs_batch_destroy", "rs_shoot_batch",
     "rs_field_status", "rs_last_error", "rs_version", "rs_set_launch_config", "rs_get_launch_config",
     "rs_launch_configs", "rs_trace_certified", "rs_set_certified_binning", "rs_get_certified_binning",
-    "rs_selftest_bounded_wait", "rs_shoot_rows_noalloc", "EXPORTED_SYMBOLS",
+    "rs_selftest_bounded_wait", "rs_shoot_rows_noalloc", "rs_light_curves", "rs_shoot_culled",
+    "rs_create_moving_field", "rs_field_set_time", "rs_field_time", "rs_shoot_staged", "rs_shoot_streamed",
+    "rs_set_staged_state_budget", "rs_light_curve_plan_create", "rs_light_curve_plan_samples",
+    "rs_light_curve_plan_launch", "rs_light_curve_plan_destroy",
 ]
 
 RS_OK, RS_EINVAL, RS_ENOMEM, RS_ECUDA, RS_EOVERFLOW, RS_ETIMEOUT = 0, 1, 2, 3, 4, 5

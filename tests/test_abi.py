@@ -187,3 +187,10 @@ def test_zoom_geometry(rs):
     w = rs.Window((-2.0, -2.0), (2.0, 2.0), (256, 256))
     zw = rs.zoom_window(w, (0.0, -1.0), (1.0, 0.5), 4)
     assert zw.npix == (256, 384)
+
+
+def test_python_names_cover_the_boundary(rs):
+    """Every C entry point has a Python function of the same name, listed in __all__."""
+    for name in rs.EXPORTED_SYMBOLS:
+        assert name in rs.__all__ and callable(getattr(rs, name)), name
+    assert all(hasattr(rs, n) for n in rs.__all__)
