@@ -393,6 +393,14 @@ int rs_shoot_rows_noalloc(rs_field_t f, const rs_ray_grid* g, int64_t row_begin,
  */
 int rs_selftest_bounded_wait(int64_t limit_ns, int* status);
 
+/*
+ * rs_set_alloc_failure -- allocation-failure injection (failure-detection support; no paper
+ * counterpart).  n >= 0: the n-th following device or pinned-host allocation made by the library
+ * (0: the next one, counted across threads) reports an out-of-memory error instead of allocating,
+ * once; n = -1 disarms.  The failing call returns RS_ENOMEM after releasing what it had allocated.
+ */
+int rs_set_alloc_failure(int64_t n);
+
 /* Thread-local message for the last nonzero status returned on this thread. */
 const char* rs_last_error(void);
 

@@ -32,7 +32,7 @@ __all__ = [
     "rs_launch_configs", "rs_trace_certified", "rs_set_certified_binning", "rs_get_certified_binning",
     "rs_selftest_bounded_wait", "rs_shoot_rows_noalloc", "rs_light_curves", "rs_shoot_culled",
     "rs_create_moving_field", "rs_field_set_time", "rs_field_time", "rs_shoot_staged", "rs_shoot_streamed",
-    "rs_set_staged_state_budget", "rs_light_curve_plan_create", "rs_light_curve_plan_samples",
+    "rs_set_staged_state_budget", "rs_set_alloc_failure", "rs_light_curve_plan_create", "rs_light_curve_plan_samples",
     "rs_light_curve_plan_launch", "rs_light_curve_plan_destroy",
 ]
 
@@ -46,7 +46,7 @@ EXPORTED_SYMBOLS = (
     "rs_launch_configs", "rs_trace_certified", "rs_set_certified_binning", "rs_get_certified_binning",
     "rs_selftest_bounded_wait", "rs_shoot_rows_noalloc", "rs_light_curves", "rs_shoot_culled",
     "rs_create_moving_field", "rs_field_set_time", "rs_field_time", "rs_shoot_staged", "rs_shoot_streamed",
-    "rs_set_staged_state_budget",
+    "rs_set_staged_state_budget", "rs_set_alloc_failure",
     "rs_light_curve_plan_create", "rs_light_curve_plan_samples", "rs_light_curve_plan_launch",
     "rs_light_curve_plan_destroy",
 )
@@ -140,6 +140,7 @@ def load():
         "rs_shoot_culled": ([vp, gp, i64, i64, wp, vp, vp, vp, vp], i32),
         "rs_shoot_staged": ([i32, vp, gp, i64, i64, wp, vp, vp, vp], i32),
         "rs_set_staged_state_budget": ([ctypes.c_uint64], i32),
+        "rs_set_alloc_failure": ([i64], i32),
         "rs_shoot_streamed": ([vp, vp, i64, dbl, dbl, i64, gp, i64, i64, wp, vp, vp, vp], i32),
         "rs_magnification": ([vp, gp, wp, vp, vp], i32),
         "rs_light_curves": ([i32, vp, vp, i32, dbl, i32, vp, vp, vp, vp], i32),
@@ -373,6 +374,11 @@ def rs_shoot_streamed(lens_xy, masses, kappa_c: float, gamma: float, lenses_per_
                                     float(kappa_c), float(gamma), int(lenses_per_pass), ctypes.byref(g),
                                     int(row_begin), int(row_end), ctypes.byref(w), pc, po, _stream(stream)),
            "rs_shoot_streamed")
+
+
+def rs_set_alloc_failure(n: int) -> None:
+    """Make the n-th following library allocation fail once (n = -1 disarms); failure-detection tests."""
+    _check(load().rs_set_alloc_failure(int(n)), "rs_set_alloc_failure")
 
 
 def rs_set_staged_state_budget(nbytes: int) -> None:

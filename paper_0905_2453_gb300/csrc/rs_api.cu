@@ -6,6 +6,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <atomic>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -69,6 +70,44 @@ int g_cfg[2] = {rsint::kDefaultCfg, rsint::kDefaultCfg};
 int g_certify = 1;
 // Device memory for the per-ray state of a staged (lens-partitioned) shoot; larger calls run in row blocks.
 size_t g_staged_budget = (size_t)2 << 30;
+
+// Allocation-failure injection (test support): when armed with n >= 0, the n-th following library
+// allocation (0: the next one) reports cudaErrorMemoryAllocation instead of allocating.
+std::atomic<int64_t> g_alloc_fail_in{-1};
+
+bool inject_alloc_failure() {
+  int64_t v = g_alloc_fail_in.load();
+  while (v >= 0)
+    if (g_alloc_fail_in.compare_exchange_weak(v, v - 1)) return v == 0;
+  return false;
+}
+
+template <class T>
+cudaError_t dev_alloc(T** p, size_t bytes) {
+  if (inject_alloc_failure()) {
+    *p = nullptr;
+    return cudaErrorMemoryAllocation;
+  }
+  return cudaMalloc(reinterpret_cast<void**>(p), bytes);
+}
+
+template <class T>
+cudaError_t dev_alloc_async(T** p, size_t bytes, cudaStream_t s) {
+  if (inject_alloc_failure()) {
+    *p = nullptr;
+    return cudaErrorMemoryAllocation;
+  }
+  return cudaMallocAsync(reinterpret_cast<void**>(p), bytes, s);
+}
+
+template <class T>
+cudaError_t host_alloc(T** p, size_t bytes) {
+  if (inject_alloc_failure()) {
+    *p = nullptr;
+    return cudaErrorMemoryAllocation;
+  }
+  return cudaMallocHost(reinterpret_cast<void**>(p), bytes);
+}
 
 int recheck_grid(int device) {
   int v = 0;
@@ -444,9 +483,9 @@ int rs_create_field(const float* lens_xy, const float* masses, int64_t n_lens, d
     cudaFree(tmp_m);
     delete f;
   };
-  if ((e = cudaMalloc(&f->lens4, sizeof(float4) * f->n_pad)) != cudaSuccess ||
-      (has_mass && (e = cudaMalloc(&f->mass2, sizeof(float2) * f->n_pad)) != cudaSuccess) ||
-      (e = cudaMalloc(&f->status, sizeof(unsigned int))) != cudaSuccess) {
+  if ((e = dev_alloc(&f->lens4, sizeof(float4) * f->n_pad)) != cudaSuccess ||
+      (has_mass && (e = dev_alloc(&f->mass2, sizeof(float2) * f->n_pad)) != cudaSuccess) ||
+      (e = dev_alloc(&f->status, sizeof(unsigned int))) != cudaSuccess) {
     int rc = cuda_fail(e, "cudaMalloc (field)");
     cleanup();
     return rc;
@@ -454,8 +493,8 @@ int rs_create_field(const float* lens_xy, const float* masses, int64_t n_lens, d
   const float* src_xy = lens_xy;
   const float* src_m = masses;
   if (!inputs_on_device && n_lens > 0) {
-    if ((e = cudaMalloc(&tmp_xy, sizeof(float) * 2 * n_lens)) != cudaSuccess ||
-        (has_mass && (e = cudaMalloc(&tmp_m, sizeof(float) * n_lens)) != cudaSuccess)) {
+    if ((e = dev_alloc(&tmp_xy, sizeof(float) * 2 * n_lens)) != cudaSuccess ||
+        (has_mass && (e = dev_alloc(&tmp_m, sizeof(float) * n_lens)) != cudaSuccess)) {
       int rc = cuda_fail(e, "cudaMalloc (staging)");
       cleanup();
       return rc;
@@ -554,12 +593,12 @@ int rs_create_moving_field(const float* lens_xy, const float* vel_xy, const floa
   int rc = rs_create_field(lens_xy, masses, n_lens, kappa_c, gamma, inputs_on_device, stream, &f);
   if (rc != RS_OK) return rc;
   float* tmp = nullptr;
-  cudaError_t e = cudaMalloc(&f->motion, sizeof(float4) * (size_t)std::max<int64_t>(n_lens, 1));
+  cudaError_t e = dev_alloc(&f->motion, sizeof(float4) * (size_t)std::max<int64_t>(n_lens, 1));
   if (e == cudaSuccess && n_lens > 0) {
     const float* dxy = lens_xy;
     const float* dv = vel_xy;
     if (!inputs_on_device) {
-      e = cudaMalloc(&tmp, sizeof(float) * 4 * n_lens);
+      e = dev_alloc(&tmp, sizeof(float) * 4 * n_lens);
       if (e == cudaSuccess) e = cudaMemcpyAsync(tmp, lens_xy, sizeof(float) * 2 * n_lens, cudaMemcpyHostToDevice, s);
       if (e == cudaSuccess)
         e = cudaMemcpyAsync(tmp + 2 * n_lens, vel_xy, sizeof(float) * 2 * n_lens, cudaMemcpyHostToDevice, s);
@@ -648,7 +687,7 @@ int rs_shoot_rows(rs_field_t f, const rs_ray_grid* g, int64_t row_begin, int64_t
   if (g_certify) {
     // stream-ordered workspace: [count | pad | list of {field, ray}]
     d.rc_cap = rsint::recheck_capacity(d.n_rows * d.n0);
-    if ((e = cudaMallocAsync(&ws, 16 + sizeof(uint2) * (size_t)d.rc_cap, s)) != cudaSuccess)
+    if ((e = dev_alloc_async(&ws, 16 + sizeof(uint2) * (size_t)d.rc_cap, s)) != cudaSuccess)
       return cuda_fail(e, "cudaMallocAsync (re-evaluation list)");
     d.rc_count = reinterpret_cast<unsigned int*>(ws);
     d.rc_list = reinterpret_cast<uint2*>(reinterpret_cast<char*>(ws) + 16);
@@ -683,7 +722,7 @@ int rs_shoot_culled(rs_field_t f, const rs_ray_grid* g, int64_t row_begin, int64
   const size_t coarse_off = 32 + sizeof(uint2) * (size_t)cap;
   const size_t list_off = coarse_off + sizeof(unsigned) * (size_t)n_coarse;
   void* ws = nullptr;
-  cudaError_t e = cudaMallocAsync(&ws, list_off + sizeof(unsigned) * (size_t)n_cells, s);
+  cudaError_t e = dev_alloc_async(&ws, list_off + sizeof(unsigned) * (size_t)n_cells, s);
   if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync (culled-shoot workspace)");
   char* base = reinterpret_cast<char*>(ws);
   unsigned* n_coarse_kept = reinterpret_cast<unsigned*>(base + 8);
@@ -743,7 +782,7 @@ int rs_shoot_staged(int n_parts, const rs_field_t* parts, const rs_ray_grid* g, 
   const size_t list_off = (state_bytes + 255) / 256 * 256;
   const size_t ff_off = list_off + 16 + sizeof(uint2) * (size_t)cap;
   void* ws = nullptr;
-  cudaError_t e = cudaMallocAsync(&ws, ff_off + sizeof(float4) * (size_t)cap, s);
+  cudaError_t e = dev_alloc_async(&ws, ff_off + sizeof(float4) * (size_t)cap, s);
   if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync (staged-shoot workspace)");
   char* base = reinterpret_cast<char*>(ws);
   uint64_t* state = reinterpret_cast<uint64_t*>(base);
@@ -838,14 +877,14 @@ int rs_shoot_streamed(const float* h_lens_xy, const float* h_masses, int64_t n_l
   const size_t off_m = raw_xy, off_l4 = (off_m + raw_m + 255) / 256 * 256;
   const size_t off_m2 = off_l4 + sizeof(float4) * (size_t)P, dbytes = off_m2 + (mass ? sizeof(float2) * (size_t)P : 0);
   for (int b = 0; b < 2 && e == cudaSuccess; ++b) {
-    if ((e = cudaMalloc(reinterpret_cast<void**>(&r.dbuf[b]), dbytes)) != cudaSuccess) break;
-    if ((e = cudaMallocHost(reinterpret_cast<void**>(&r.hbuf[b]), raw_xy + raw_m)) != cudaSuccess) break;
+    if ((e = dev_alloc(&r.dbuf[b], dbytes)) != cudaSuccess) break;
+    if ((e = host_alloc(&r.hbuf[b], raw_xy + raw_m)) != cudaSuccess) break;
     if ((e = cudaEventCreateWithFlags(&r.ready[b], cudaEventDisableTiming)) != cudaSuccess) break;
     if ((e = cudaEventCreateWithFlags(&r.freed[b], cudaEventDisableTiming)) != cudaSuccess) break;
     e = cudaEventCreateWithFlags(&r.copied[b], cudaEventDisableTiming);
   }
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&r.cs, cudaStreamNonBlocking);
-  if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&r.status), sizeof(unsigned int));
+  if (e == cudaSuccess) e = dev_alloc(&r.status, sizeof(unsigned int));
   if (e == cudaSuccess) e = cudaMemset(r.status, 0, sizeof(unsigned int));
   // state and re-evaluation workspace, as rs_shoot_staged
   const int64_t rows_blk = std::max<int64_t>(4, (int64_t)(g_staged_budget / rsint::staged_state_bytes(4, d.n0)) * 4);
@@ -854,7 +893,7 @@ int rs_shoot_streamed(const float* h_lens_xy, const float* h_masses, int64_t n_l
   const unsigned cap = g_certify ? rsint::recheck_capacity(rows_max * d.n0) : 0u;
   const size_t list_off = (state_bytes + 255) / 256 * 256;
   const size_t ff_off = list_off + 16 + sizeof(uint2) * (size_t)cap;
-  if (e == cudaSuccess) e = cudaMalloc(&r.ws, ff_off + sizeof(float4) * (size_t)cap);
+  if (e == cudaSuccess) e = dev_alloc(&r.ws, ff_off + sizeof(float4) * (size_t)cap);
   if (e != cudaSuccess) return cuda_fail(e, "streamed-shoot resources");
   char* base = reinterpret_cast<char*>(r.ws);
   uint64_t* state = reinterpret_cast<uint64_t*>(base);
@@ -979,7 +1018,7 @@ int rs_selftest_bounded_wait(int64_t limit_ns, int* status) {
   if (!status) return fail(RS_EINVAL, "status is NULL");
   if (limit_ns < 0 || limit_ns > 2000000000LL) return fail(RS_EINVAL, "limit_ns must be in [0, 2e9]");
   unsigned int* d = nullptr;
-  cudaError_t e = cudaMalloc(&d, sizeof(unsigned int));
+  cudaError_t e = dev_alloc(&d, sizeof(unsigned int));
   if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc (self-test)");
   selftest_wait_kernel<<<1, 32>>>((uint64_t)limit_ns, d);
   e = cudaGetLastError();
@@ -993,6 +1032,12 @@ int rs_selftest_bounded_wait(int64_t limit_ns, int* status) {
 
 int rs_set_certified_binning(int enabled) {
   g_certify = enabled ? 1 : 0;
+  return RS_OK;
+}
+
+int rs_set_alloc_failure(int64_t n) {
+  if (n < -1) return fail(RS_EINVAL, "n must be >= -1");
+  g_alloc_fail_in.store(n);
   return RS_OK;
 }
 
@@ -1044,7 +1089,7 @@ int rs_light_curves(int n_maps, const float* const* d_mu, const rs_window* windo
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   rsint::LcTrack* d_table = nullptr;
   const size_t bytes = plan.table.size() * sizeof(rsint::LcTrack);
-  if ((e = cudaMallocAsync(reinterpret_cast<void**>(&d_table), bytes, st)) != cudaSuccess)
+  if ((e = dev_alloc_async(&d_table, bytes, st)) != cudaSuccess)
     return cuda_fail(e, "cudaMallocAsync (track table)");
   e = cudaMemcpyAsync(d_table, plan.table.data(), bytes, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess)
@@ -1077,7 +1122,7 @@ int rs_light_curve_plan_create(int n_maps, const float* const* d_mu, const rs_wi
   p->grid = lc_grid(p->device, plan.total);
   if (p->n_tracks > 0) {
     const size_t bytes = plan.table.size() * sizeof(rsint::LcTrack);
-    if ((e = cudaMalloc(reinterpret_cast<void**>(&p->d_table), bytes)) != cudaSuccess) {
+    if ((e = dev_alloc(&p->d_table, bytes)) != cudaSuccess) {
       delete p;
       return cuda_fail(e, "cudaMalloc (track table)");
     }
@@ -1200,11 +1245,11 @@ int rs_batch_create(int n_fields, const rs_field_t* fields, const rs_ray_grid* g
     for (int k = 0; k < n_fields; ++k) total += descs[k].n_rows * descs[k].n0;
     b->rc_cap = rsint::recheck_capacity(total);
   }
-  if ((e = cudaMalloc(&b->d_descs, sizeof(ShootDesc) * n_fields)) != cudaSuccess ||
-      (e = cudaMalloc(&b->d_items, sizeof(int2) * std::max<size_t>(1, h_items.size()))) != cudaSuccess ||
-      (e = cudaMalloc(&b->d_counter, 2 * sizeof(int))) != cudaSuccess ||
-      (b->rc_cap > 0 && (e = cudaMalloc(&b->d_rc_list, sizeof(uint2) * (size_t)b->rc_cap)) != cudaSuccess) ||
-      (b->rc_cap > 0 && (e = cudaMalloc(&b->d_rc_count, sizeof(unsigned int))) != cudaSuccess)) {
+  if ((e = dev_alloc(&b->d_descs, sizeof(ShootDesc) * n_fields)) != cudaSuccess ||
+      (e = dev_alloc(&b->d_items, sizeof(int2) * std::max<size_t>(1, h_items.size()))) != cudaSuccess ||
+      (e = dev_alloc(&b->d_counter, 2 * sizeof(int))) != cudaSuccess ||
+      (b->rc_cap > 0 && (e = dev_alloc(&b->d_rc_list, sizeof(uint2) * (size_t)b->rc_cap)) != cudaSuccess) ||
+      (b->rc_cap > 0 && (e = dev_alloc(&b->d_rc_count, sizeof(unsigned int))) != cudaSuccess)) {
     rc = cuda_fail(e, "cudaMalloc (batch)");
     cleanup();
     return rc;
