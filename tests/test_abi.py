@@ -194,3 +194,35 @@ def test_python_names_cover_the_boundary(rs):
     for name in rs.EXPORTED_SYMBOLS:
         assert name in rs.__all__ and callable(getattr(rs, name)), name
     assert all(hasattr(rs, n) for n in rs.__all__)
+
+
+def test_widening_entry_points_validate_before_cuda(rs):
+    """Moving fields, staged and streamed shoots, plans and the injection hook reject bad arguments on the
+    host (no CUDA call is made, so these run without a GPU)."""
+    lib = rs.load()
+    h = ctypes.c_void_p()
+    xy = (ctypes.c_float * 4)(0.0, 1.0, 2.0, 3.0)
+    v_bad = (ctypes.c_float * 4)(0.0, float("nan"), 0.0, 0.0)
+    assert lib.rs_create_moving_field(xy, None, None, 2, 0.0, 0.0, 0, None, ctypes.byref(h)) == rs.RS_EINVAL
+    assert lib.rs_create_moving_field(xy, v_bad, None, 2, 0.0, 0.0, 0, None, ctypes.byref(h)) == rs.RS_EINVAL
+    assert lib.rs_field_set_time(None, 1.0, None) == rs.RS_EINVAL
+    t = ctypes.c_double()
+    assert lib.rs_field_time(None, ctypes.byref(t)) == rs.RS_EINVAL
+    g = rs._cgrid(rs.RayGrid((0.0, 0.0), (1.0, 1.0), (4, 4)))
+    w = rs._cwin(rs.Window((-1.0, -1.0), (1.0, 1.0), (4, 4)))
+    assert lib.rs_shoot_staged(0, None, ctypes.byref(g), 0, 4, ctypes.byref(w), ctypes.c_void_p(16), None,
+                               None) == rs.RS_EINVAL
+    parts = (ctypes.c_void_p * 1)(None)
+    assert lib.rs_shoot_staged(1, parts, ctypes.byref(g), 0, 4, ctypes.byref(w), ctypes.c_void_p(16), None,
+                               None) == rs.RS_EINVAL
+    for per_pass in (0, 1000, 3 << 30):
+        assert lib.rs_shoot_streamed(xy, None, 2, 0.0, 0.0, per_pass, ctypes.byref(g), 0, 4, ctypes.byref(w),
+                                     ctypes.c_void_p(16), None, None) == rs.RS_EINVAL
+    bad_xy = (ctypes.c_float * 4)(0.0, float("inf"), 2.0, 3.0)
+    assert lib.rs_shoot_streamed(bad_xy, None, 2, 0.0, 0.0, 1024, ctypes.byref(g), 0, 4, ctypes.byref(w),
+                                 ctypes.c_void_p(16), None, None) == rs.RS_EINVAL
+    assert lib.rs_light_curve_plan_launch(None, None, None, None) == rs.RS_EINVAL
+    assert lib.rs_light_curve_plan_destroy(None) == rs.RS_OK
+    assert lib.rs_set_alloc_failure(-2) == rs.RS_EINVAL
+    assert lib.rs_set_alloc_failure(-1) == rs.RS_OK
+    assert lib.rs_set_staged_state_budget(1000) == rs.RS_EINVAL
