@@ -135,10 +135,16 @@ class ClockSampler:
 # --------------------------------------------------------------------------------------------- helpers
 
 def kernel_source_hash():
+    """Hash of the shoot kernel's source code with comments and blank space removed (a comment edit keeps
+    a profiled traffic figure valid; any code change invalidates it)."""
+    import re
     h = hashlib.sha256()
     for f in ("rs_device.cuh", "rs_shoot.cu"):
-        with open(os.path.join(ROOT, "paper_0905_2453_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, "paper_0905_2453_gb300", "csrc", f)) as fh:
+            src = fh.read()
+        src = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)
+        src = re.sub(r"//[^\n]*", " ", src)
+        h.update(" ".join(src.split()).encode())
     return h.hexdigest()[:16]
 
 

@@ -184,7 +184,7 @@ struct FieldDev {
   int32_t n_lens;
   int32_t has_mass;
   double lam1, lam2;    // (1 - kappa_c) - gamma, (1 - kappa_c) + gamma
-  float lamabs;         // max(|lam1|, |lam2|), for the float64-epilogue term of the error band
+  float lamabs;         // max(|lam1|, |lam2|), for the Eq. 6 rounding term of the error band
   unsigned int* status; // device status word (RS_OK / RS_ETIMEOUT)
 };
 
@@ -540,7 +540,7 @@ __device__ __forceinline__ void deflect_finish(const DeflectAcc<RPT / 2>& acc, f
     float s, sB, b, bB;
     f2_unpack(acc.SS[q], s, sB);
     f2_unpack(acc.AB[q], b, bB);
-    // |alpha| enters through the float64 epilogue rounding (~1e-16 |alpha|): 8e-15 (|hi1| + |hi2|)
+    // |alpha| enters through the rounding of Eq. 6 (~1e-16 |alpha| in float64): 8e-15 (|hi1| + |hi2|)
     sig[2 * q] = kSigmaScale * sqrtf(s) + kSystematicScale * b + 8e-15f * (fabsf(a1h[2 * q]) + fabsf(a2h[2 * q]));
     sig[2 * q + 1] =
         kSigmaScale * sqrtf(sB) + kSystematicScale * bB + 8e-15f * (fabsf(a1h[2 * q + 1]) + fabsf(a2h[2 * q + 1]));
@@ -590,8 +590,9 @@ __device__ __forceinline__ bool deflect(const FieldDev& f, const float (&x1)[RPT
 }
 
 // Half-width of the band around y within which the float32 path cannot decide the pixel: sig (the
-// safety-scaled random-rounding estimate, the coherent term and the alpha part of the float64
-// epilogue rounding) plus the lam x part of that rounding.
+// safety-scaled random-rounding estimate, the coherent term and the alpha part of a float64
+// evaluation of Eq. 6) plus the lam x part of that rounding.  The shoot's float-float epilogue adds
+// its own rounding bound on top (ff_pixel).
 __device__ __forceinline__ float band_halfwidth(float sig, float lamabs, float x1, float x2) {
   return sig + 4e-15f * lamabs * (fabsf(x1) + fabsf(x2));
 }

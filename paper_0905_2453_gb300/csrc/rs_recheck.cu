@@ -3,8 +3,8 @@
 //
 // Each listed ray's deflection (Eq. 2) is summed again over all lenses of its field in
 // float-float ("double-float") arithmetic on the FP32 pipe -- about 2^-44 relative per term,
-// far cheaper on GB300 than float64 -- then mapped (Eq. 6) and binned exactly as in the shoot
-// epilogue.  One warp per listed ray: the lanes split the lens loop (coalesced lens loads) and a
+// far cheaper on GB300 than float64 -- then mapped (Eq. 6) and binned with the float64 arithmetic of
+// the definition.  One warp per listed ray: the lanes split the lens loop (coalesced lens loads) and a
 // fixed reduction tree combines them, so the result is deterministic.
 #include "rs_ff.cuh"
 #include "rs_internal.h"
