@@ -18,8 +18,8 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "librs.so")
-SOURCES = ["rs_api.cu", "rs_shoot.cu", "rs_batch.cu", "rs_recheck.cu", "rs_lightcurve.cu", "rs_cull.cu", "rs_staged.cu"]
-HEADERS = ["rs_device.cuh", "rs_internal.h", "rs_ff.cuh"]
+SOURCES = ["rs_api.cu", "rs_api_batch.cu", "rs_api_staged.cu", "rs_api_lightcurve.cu", "rs_shoot.cu", "rs_batch.cu", "rs_recheck.cu", "rs_lightcurve.cu", "rs_cull.cu", "rs_staged.cu"]
+HEADERS = ["rs_device.cuh", "rs_internal.h", "rs_ff.cuh", "rs_host.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall"]
 

@@ -1,199 +1,23 @@
-// C-ABI layer of librs.so: argument validation, field management, launch shape
-// selection, the batched plan (CUDA graph), and the small elementwise kernels
-// (lens repacking, Eq. 4 normalisation).
+// C-ABI layer of librs.so, core: error reporting, argument validation, fields (static and moving),
+// launch shape selection, the plain, culled and listed-ray shoots, Eq. 4 normalisation, the
+// bounded-wait self-test, and the small elementwise kernels (lens repacking, lens motion, Eq. 4).
+// Batches, lens-partitioned shoots and light curves live in rs_api_batch.cu, rs_api_staged.cu and
+// rs_api_lightcurve.cu.
 #include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
-#include <atomic>
 #include <mutex>
 #include <string>
 #include <vector>
 
-#include "../../include/rs.h"
-#include "rs_internal.h"
+#include "rs_host.h"
 
 using rsdev::FieldDev;
 using rsdev::ShootDesc;
 
-struct rs_field {
-  int device;
-  int64_t n_lens;
-  int64_t n_pad;
-  float4* lens4;
-  float2* mass2;
-  unsigned int* status;
-  double kappa_c, gamma;
-  FieldDev dev;
-  // moving fields: {x1, x2, v1, v2} at t = 0 per lens, bounds of |x| and |v|, current time
-  float4* motion = nullptr;
-  double max_x = 0.0, max_v = 0.0, time = 0.0;
-};
-
-struct rs_batch {
-  int device;
-  int n_fields;
-  // work items of fields without (group 0) and with (group 1) per-lens masses: one persistent
-  // kernel per group, each with its own launch shape
-  int n_items[2];
-  int item_offset[2];
-  int cfg[2];
-  int grid[2];
-  ShootDesc* d_descs;
-  int2* d_items;
-  int* d_counter;
-  uint2* d_rc_list;
-  unsigned int* d_rc_count;
-  unsigned int rc_cap;
-  cudaGraph_t graph;
-  cudaGraphExec_t exec;
-};
-
-struct rs_lc_plan {
-  int device;
-  int n_tracks;
-  int64_t total;
-  int profile;
-  double cut2;
-  float ecut;
-  int grid;
-  rsint::LcTrack* d_table;
-};
-
 namespace {
-
-thread_local std::string g_err;
-// Launch shape per mass mode (index 0: unit masses, 1: per-lens masses).
-int g_cfg[2] = {rsint::kDefaultCfg, rsint::kDefaultCfg};
-// Certified binning (float-float re-evaluation of rays inside their error band of a pixel edge).
-int g_certify = 1;
-// Device memory for the per-ray state of a staged (lens-partitioned) shoot; larger calls run in row blocks.
-size_t g_staged_budget = (size_t)2 << 30;
-
-// Allocation-failure injection (test support): when armed with n >= 0, the n-th following library
-// allocation (0: the next one) reports cudaErrorMemoryAllocation instead of allocating.
-std::atomic<int64_t> g_alloc_fail_in{-1};
-
-bool inject_alloc_failure() {
-  int64_t v = g_alloc_fail_in.load();
-  while (v >= 0)
-    if (g_alloc_fail_in.compare_exchange_weak(v, v - 1)) return v == 0;
-  return false;
-}
-
-template <class T>
-cudaError_t dev_alloc(T** p, size_t bytes) {
-  if (inject_alloc_failure()) {
-    *p = nullptr;
-    return cudaErrorMemoryAllocation;
-  }
-  return cudaMalloc(reinterpret_cast<void**>(p), bytes);
-}
-
-template <class T>
-cudaError_t dev_alloc_async(T** p, size_t bytes, cudaStream_t s) {
-  if (inject_alloc_failure()) {
-    *p = nullptr;
-    return cudaErrorMemoryAllocation;
-  }
-  return cudaMallocAsync(reinterpret_cast<void**>(p), bytes, s);
-}
-
-template <class T>
-cudaError_t host_alloc(T** p, size_t bytes) {
-  if (inject_alloc_failure()) {
-    *p = nullptr;
-    return cudaErrorMemoryAllocation;
-  }
-  return cudaMallocHost(reinterpret_cast<void**>(p), bytes);
-}
-
-int recheck_grid(int device) {
-  int v = 0;
-  if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, device) != cudaSuccess || v < 1) v = 1;
-  return v * 8;
-}
-
-int fail(int code, const char* fmt, ...) {
-  char buf[512];
-  va_list ap;
-  va_start(ap, fmt);
-  vsnprintf(buf, sizeof(buf), fmt, ap);
-  va_end(ap);
-  g_err = buf;
-  return code;
-}
-
-int cuda_fail(cudaError_t e, const char* what) {
-  return fail(e == cudaErrorMemoryAllocation ? RS_ENOMEM : RS_ECUDA, "%s: %s (%s)", what, cudaGetErrorName(e),
-              cudaGetErrorString(e));
-}
-
-constexpr double kCoordLimit = 1e9;
-
-bool finite_coord(double v) { return std::isfinite(v) && std::fabs(v) <= kCoordLimit; }
-
-int check_grid(const rs_ray_grid* g) {
-  if (!g) return fail(RS_EINVAL, "ray grid is NULL");
-  for (int k = 0; k < 2; ++k) {
-    if (!finite_coord(g->origin[k])) return fail(RS_EINVAL, "grid origin[%d] not finite or beyond 1e9", k);
-    if (!(std::isfinite(g->spacing[k]) && g->spacing[k] > 0.0))
-      return fail(RS_EINVAL, "grid spacing[%d] must be finite and > 0", k);
-    if (g->n[k] < 0) return fail(RS_EINVAL, "grid n[%d] < 0", k);
-    const double far = g->origin[k] + (double)(g->n[k] > 0 ? g->n[k] - 1 : 0) * g->spacing[k];
-    if (!finite_coord(far)) return fail(RS_EINVAL, "grid extent along axis %d beyond 1e9", k);
-  }
-  return RS_OK;
-}
-
-int check_window(const rs_window* w) {
-  if (!w) return fail(RS_EINVAL, "window is NULL");
-  for (int k = 0; k < 2; ++k) {
-    if (!(std::isfinite(w->lo[k]) && std::isfinite(w->hi[k]) && w->hi[k] > w->lo[k]))
-      return fail(RS_EINVAL, "window axis %d: need finite lo < hi", k);
-    if (w->npix[k] < 1) return fail(RS_EINVAL, "window npix[%d] < 1", k);
-    if (w->npix[k] > (1 << 22)) return fail(RS_EINVAL, "window npix[%d] > 2^22", k);
-    const double sc = (double)w->npix[k] / (w->hi[k] - w->lo[k]);
-    if (!(std::isfinite(sc) && sc > 0.0)) return fail(RS_EINVAL, "window axis %d: degenerate pixel scale", k);
-  }
-  if ((int64_t)w->npix[0] * (int64_t)w->npix[1] > (int64_t)1 << 40)
-    return fail(RS_EOVERFLOW, "window has more than 2^40 pixels");
-  return RS_OK;
-}
-
-struct DeviceGuard {
-  int prev = -1;
-  bool changed = false;
-  explicit DeviceGuard(int dev) {
-    if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) {
-      changed = cudaSetDevice(dev) == cudaSuccess;
-    }
-  }
-  ~DeviceGuard() {
-    if (changed) cudaSetDevice(prev);
-  }
-};
-
-// The arguments every shoot call shares: grid, row range, window and the counts buffer.
-int check_call(const rs_ray_grid* g, int64_t row_begin, int64_t row_end, const rs_window* w, const uint32_t* d_counts) {
-  int rc;
-  if ((rc = check_grid(g)) != RS_OK) return rc;
-  if ((rc = check_window(w)) != RS_OK) return rc;
-  if (!d_counts) return fail(RS_EINVAL, "d_counts is NULL");
-  if (row_begin < 0 || row_end < row_begin || row_end > g->n[1])
-    return fail(RS_EINVAL, "row range [%lld, %lld) outside [0, %lld]", (long long)row_begin, (long long)row_end,
-                (long long)g->n[1]);
-  return RS_OK;
-}
-
-int check_field_device(const rs_field* f) {
-  int cur = -1;
-  cudaError_t e = cudaGetDevice(&cur);
-  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
-  if (cur != f->device) return fail(RS_EINVAL, "field lives on device %d but device %d is current", f->device, cur);
-  return RS_OK;
-}
 
 __global__ void pack_lenses_kernel(const float* __restrict__ xy, const float* __restrict__ m, int64_t n, int64_t n_pad,
                                    float4* __restrict__ lens4, float2* __restrict__ mass2) {
@@ -266,6 +90,98 @@ __global__ void selftest_wait_kernel(uint64_t limit_ns, unsigned int* out) {
   if (threadIdx.x == 0) *out = ok ? 0u : rsdev::kStatusTimeout;
 }
 
+}  // namespace
+
+namespace rshost {
+
+thread_local std::string g_err;
+// Launch shape per mass mode (index 0: unit masses, 1: per-lens masses).
+int g_cfg[2] = {rsint::kDefaultCfg, rsint::kDefaultCfg};
+// Certified binning (float-float re-evaluation of rays inside their error band of a pixel edge).
+int g_certify = 1;
+// Device memory for the per-ray state of a staged (lens-partitioned) shoot; larger calls run in row blocks.
+size_t g_staged_budget = (size_t)2 << 30;
+
+// Allocation-failure injection (test support): when armed with n >= 0, the n-th following library
+// allocation (0: the next one) reports cudaErrorMemoryAllocation instead of allocating.
+std::atomic<int64_t> g_alloc_fail_in{-1};
+
+bool inject_alloc_failure() {
+  int64_t v = g_alloc_fail_in.load();
+  while (v >= 0)
+    if (g_alloc_fail_in.compare_exchange_weak(v, v - 1)) return v == 0;
+  return false;
+}
+
+int recheck_grid(int device) {
+  int v = 0;
+  if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, device) != cudaSuccess || v < 1) v = 1;
+  return v * 8;
+}
+
+int fail(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return code;
+}
+
+int cuda_fail(cudaError_t e, const char* what) {
+  return fail(e == cudaErrorMemoryAllocation ? RS_ENOMEM : RS_ECUDA, "%s: %s (%s)", what, cudaGetErrorName(e),
+              cudaGetErrorString(e));
+}
+
+int check_grid(const rs_ray_grid* g) {
+  if (!g) return fail(RS_EINVAL, "ray grid is NULL");
+  for (int k = 0; k < 2; ++k) {
+    if (!finite_coord(g->origin[k])) return fail(RS_EINVAL, "grid origin[%d] not finite or beyond 1e9", k);
+    if (!(std::isfinite(g->spacing[k]) && g->spacing[k] > 0.0))
+      return fail(RS_EINVAL, "grid spacing[%d] must be finite and > 0", k);
+    if (g->n[k] < 0) return fail(RS_EINVAL, "grid n[%d] < 0", k);
+    const double far = g->origin[k] + (double)(g->n[k] > 0 ? g->n[k] - 1 : 0) * g->spacing[k];
+    if (!finite_coord(far)) return fail(RS_EINVAL, "grid extent along axis %d beyond 1e9", k);
+  }
+  return RS_OK;
+}
+
+int check_window(const rs_window* w) {
+  if (!w) return fail(RS_EINVAL, "window is NULL");
+  for (int k = 0; k < 2; ++k) {
+    if (!(std::isfinite(w->lo[k]) && std::isfinite(w->hi[k]) && w->hi[k] > w->lo[k]))
+      return fail(RS_EINVAL, "window axis %d: need finite lo < hi", k);
+    if (w->npix[k] < 1) return fail(RS_EINVAL, "window npix[%d] < 1", k);
+    if (w->npix[k] > (1 << 22)) return fail(RS_EINVAL, "window npix[%d] > 2^22", k);
+    const double sc = (double)w->npix[k] / (w->hi[k] - w->lo[k]);
+    if (!(std::isfinite(sc) && sc > 0.0)) return fail(RS_EINVAL, "window axis %d: degenerate pixel scale", k);
+  }
+  if ((int64_t)w->npix[0] * (int64_t)w->npix[1] > (int64_t)1 << 40)
+    return fail(RS_EOVERFLOW, "window has more than 2^40 pixels");
+  return RS_OK;
+}
+
+// The arguments every shoot call shares: grid, row range, window and the counts buffer.
+int check_call(const rs_ray_grid* g, int64_t row_begin, int64_t row_end, const rs_window* w, const uint32_t* d_counts) {
+  int rc;
+  if ((rc = check_grid(g)) != RS_OK) return rc;
+  if ((rc = check_window(w)) != RS_OK) return rc;
+  if (!d_counts) return fail(RS_EINVAL, "d_counts is NULL");
+  if (row_begin < 0 || row_end < row_begin || row_end > g->n[1])
+    return fail(RS_EINVAL, "row range [%lld, %lld) outside [0, %lld]", (long long)row_begin, (long long)row_end,
+                (long long)g->n[1]);
+  return RS_OK;
+}
+
+int check_field_device(const rs_field* f) {
+  int cur = -1;
+  cudaError_t e = cudaGetDevice(&cur);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+  if (cur != f->device) return fail(RS_EINVAL, "field lives on device %d but device %d is current", f->device, cur);
+  return RS_OK;
+}
+
 int num_sms(int device) {
   int v = 0;
   if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) return 1;
@@ -313,107 +229,15 @@ int fill_desc(const rs_field* f, const rs_ray_grid* g, int64_t row_begin, int64_
   return RS_OK;
 }
 
-// Validated light-curve launch parameters: the per-track descriptor table (tracks with samples, in
-// output order), the number of samples and the profile constants.
-struct LcPlan {
-  std::vector<rsint::LcTrack> table;
-  int64_t total = 0;
-  int profile = 0;
-  double cut2 = 0.0;
-  float ecut = 0.f;
-};
-
-int lc_prepare(int n_maps, const float* const* d_mu, const rs_window* windows, int profile, double s,
-               int n_tracks, const rs_track* tracks, LcPlan* plan) {
-  if (profile != RS_PROFILE_GAUSSIAN && profile != RS_PROFILE_DISC)
-    return fail(RS_EINVAL, "profile must be RS_PROFILE_GAUSSIAN or RS_PROFILE_DISC");
-  if (!(std::isfinite(s) && s > 0.0)) return fail(RS_EINVAL, "profile size s must be finite and > 0");
-  if (n_tracks < 0) return fail(RS_EINVAL, "n_tracks < 0");
-  if (n_tracks > 0 && !tracks) return fail(RS_EINVAL, "tracks is NULL");
-  int64_t total = 0;
-  for (int t = 0; t < n_tracks; ++t) {
-    if (tracks[t].n < 0) return fail(RS_EINVAL, "track %d: n < 0", t);
-    total += tracks[t].n;
-    if (total > ((int64_t)1 << 40)) return fail(RS_EOVERFLOW, "more than 2^40 samples in one call");
-  }
-  plan->total = total;
-  plan->profile = profile;
-  if (total == 0) return RS_OK;
-  if (n_maps < 1 || !d_mu || !windows) return fail(RS_EINVAL, "n_maps >= 1 with non-NULL d_mu and windows needed");
-  // profile support radius and the exponent scale: Gaussian E = d^2 / (2 s^2) cut at (6 s)^2 (the device
-  // works with E log2(e), so that the weight is one base-2 exponential), disc E = d^2 / s^2 cut at 1
-  const double R = profile == RS_PROFILE_GAUSSIAN ? 6.0 * s : s;
-  const double cut2 = profile == RS_PROFILE_GAUSSIAN ? (6.0 * s) * (6.0 * s) : s * s;
-  const double kLog2e = 1.4426950408889634;
-  const double escale = profile == RS_PROFILE_GAUSSIAN ? kLog2e / (2.0 * s * s) : 1.0 / (s * s);
-  const double ecut_d = profile == RS_PROFILE_GAUSSIAN ? 18.0 * kLog2e : 1.0;
-  const float ecut = (float)ecut_d;
-  if (!(std::isfinite(cut2) && cut2 > 0.0 && std::isfinite(escale))) return fail(RS_EINVAL, "profile size s out of range");
-  std::vector<rsint::LcTrack>& table = plan->table;
-  table.reserve(n_tracks);
-  int64_t off = 0;
-  for (int t = 0; t < n_tracks; ++t) {
-    const rs_track& tr = tracks[t];
-    if (tr.n == 0) continue;
-    if (tr.map < 0 || tr.map >= n_maps) return fail(RS_EINVAL, "track %d: map %d outside [0, %d)", t, tr.map, n_maps);
-    const rs_window* w = &windows[tr.map];
-    int rc;
-    if ((rc = check_window(w)) != RS_OK) return rc;
-    if (!d_mu[tr.map]) return fail(RS_EINVAL, "map %d is NULL", tr.map);
-    rsint::LcTrack d{};
-    d.mu = d_mu[tr.map];
-    d.np0 = w->npix[0];
-    d.np1 = w->npix[1];
-    double pix[2], rp[2];
-    for (int k = 0; k < 2; ++k) {
-      if (w->npix[k] > (1 << 24)) return fail(RS_EINVAL, "map %d: light curves need npix[%d] <= 2^24", tr.map, k);
-      pix[k] = (w->hi[k] - w->lo[k]) / (double)w->npix[k];
-      if (std::max(std::fabs(w->lo[k]), std::fabs(w->hi[k])) / pix[k] > 1073741824.0)
-        return fail(RS_EINVAL, "map %d axis %d: max(|lo|, |hi|) / pixel must be <= 2^30", tr.map, k);
-      rp[k] = R / pix[k];
-      if (!(rp[k] <= 1048576.0)) return fail(RS_EINVAL, "profile spans more than 2^20 pixels along axis %d of map %d", k, tr.map);
-      const double last = tr.y0[k] + (double)(tr.n - 1) * tr.step[k];
-      if (!finite_coord(tr.y0[k]) || !std::isfinite(tr.step[k]) || !finite_coord(last))
-        return fail(RS_EINVAL, "track %d: samples must be finite with |y| <= 1e9", t);
-    }
-    d.lo0 = w->lo[0];
-    d.lo1 = w->lo[1];
-    d.pix0 = pix[0];
-    d.pix1 = pix[1];
-    d.y00 = tr.y0[0];
-    d.y01 = tr.y0[1];
-    d.st0 = tr.step[0];
-    d.st1 = tr.step[1];
-    d.t00 = (tr.y0[0] - w->lo[0]) / pix[0] - 0.5;
-    d.t01 = (tr.y0[1] - w->lo[1]) / pix[1] - 0.5;
-    d.d0 = tr.step[0] / pix[0];
-    d.d1 = tr.step[1] / pix[1];
-    d.rp0 = rp[0];
-    d.rp1 = rp[1];
-    d.a0 = (float)(pix[0] * pix[0] * escale);
-    d.a1 = (float)(pix[1] * pix[1] * escale);
-    d.inv_a0 = 1.0f / d.a0;
-    if (!(d.a0 > 0.f && d.a1 > 0.f && std::isfinite(d.a0) && std::isfinite(d.a1) && std::isfinite(d.inv_a0)))
-      return fail(RS_EINVAL, "map %d: pixel / profile size ratio outside the float32 range", tr.map);
-    // the float32 exponent is within ~8u ((R + pix0)^2 + (R + pix1)^2) escale + 4u E of the exact one
-    // (offsets in pixel units carry u (|offset| + 1)); the band takes 2^-16 of that scale (~30x margin)
-    d.band = (float)(std::ldexp((std::pow(R + pix[0], 2) + std::pow(R + pix[1], 2)) * escale + ecut_d, -16));
-    d.n = tr.n;
-    d.out_off = off;
-    off += tr.n;
-    table.push_back(d);
-  }
-  plan->cut2 = cut2;
-  plan->ecut = ecut;
-  return RS_OK;
+cudaError_t launch_pack_lenses(const float* xy, const float* m, int64_t n, int64_t n_pad, float4* lens4,
+                               float2* mass2, int blocks, cudaStream_t s) {
+  pack_lenses_kernel<<<blocks, 256, 0, s>>>(xy, m, n, n_pad, lens4, mass2);
+  return cudaGetLastError();
 }
 
-int lc_grid(int device, int64_t total) {
-  const int64_t want = (total + 255) / 256;
-  return (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)num_sms(device) * 8));
-}
+}  // namespace rshost
 
-}  // namespace
+using namespace rshost;
 
 extern "C" {
 
@@ -751,231 +575,6 @@ int rs_shoot_culled(rs_field_t f, const rs_ray_grid* g, int64_t row_begin, int64
   return RS_OK;
 }
 
-int rs_shoot_staged(int n_parts, const rs_field_t* parts, const rs_ray_grid* g, int64_t row_begin, int64_t row_end,
-                    const rs_window* w, uint32_t* d_counts, uint64_t* d_out_of_window, void* stream) {
-  if (n_parts < 1 || !parts) return fail(RS_EINVAL, "need n_parts >= 1 lens partitions");
-  for (int p = 0; p < n_parts; ++p) {
-    if (!parts[p]) return fail(RS_EINVAL, "partition %d is NULL", p);
-    const rs_field* a = parts[p];
-    const rs_field* b = parts[0];
-    if (a->device != b->device || a->dev.has_mass != b->dev.has_mass || a->kappa_c != b->kappa_c ||
-        a->gamma != b->gamma)
-      return fail(RS_EINVAL, "partition %d differs from partition 0 in device, mass mode, kappa_c or gamma", p);
-    if (p + 1 < n_parts && a->n_lens % rsdev::kRenorm != 0)
-      return fail(RS_EINVAL, "partition %d holds %lld lenses: all but the last must hold a multiple of %d", p,
-                  (long long)a->n_lens, rsdev::kRenorm);
-  }
-  int rc;
-  if ((rc = check_call(g, row_begin, row_end, w, d_counts)) != RS_OK) return rc;
-  if ((rc = check_field_device(parts[0])) != RS_OK) return rc;
-  ShootDesc d;
-  if ((rc = fill_desc(parts[0], g, row_begin, row_end, w, d_counts, d_out_of_window, &d)) != RS_OK) return rc;
-  if (d.n_rows == 0 || d.n0 == 0) return RS_OK;
-  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  // ray blocks whose carried state fits the budget (the state is 24 bytes per ray, padded to tiles)
-  const size_t budget = g_staged_budget;
-  const size_t per4 = rsint::staged_state_bytes(4, d.n0);
-  const int64_t rows_blk = std::max<int64_t>(4, (int64_t)(budget / per4) * 4);
-  const int64_t rows_max = std::min<int64_t>(rows_blk, d.n_rows);
-  const size_t state_bytes = rsint::staged_state_bytes(rows_max, d.n0);
-  const unsigned cap = g_certify ? rsint::recheck_capacity(rows_max * d.n0) : 0u;
-  const size_t list_off = (state_bytes + 255) / 256 * 256;
-  const size_t ff_off = list_off + 16 + sizeof(uint2) * (size_t)cap;
-  void* ws = nullptr;
-  cudaError_t e = dev_alloc_async(&ws, ff_off + sizeof(float4) * (size_t)cap, s);
-  if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync (staged-shoot workspace)");
-  char* base = reinterpret_cast<char*>(ws);
-  uint64_t* state = reinterpret_cast<uint64_t*>(base);
-  float4* ff = reinterpret_cast<float4*>(base + ff_off);
-  if (g_certify) {
-    d.rc_cap = cap;
-    d.rc_count = reinterpret_cast<unsigned int*>(base + list_off);
-    d.rc_list = reinterpret_cast<uint2*>(base + list_off + 16);
-  }
-  const int rgrid = recheck_grid(parts[0]->device);
-  for (int64_t r0 = 0; r0 < d.n_rows && e == cudaSuccess; r0 += rows_blk) {
-    ShootDesc db = d;
-    db.j_begin = d.j_begin + r0;
-    db.n_rows = std::min<int64_t>(rows_blk, d.n_rows - r0);
-    if (g_certify) e = cudaMemsetAsync(db.rc_count, 0, sizeof(unsigned int), s);
-    for (int p = 0; p < n_parts && e == cudaSuccess; ++p) {
-      db.f = parts[p]->dev;
-      e = rsint::launch_staged(db, state, p == 0, p == n_parts - 1, s);
-    }
-    if (g_certify) {
-      for (int p = 0; p < n_parts && e == cudaSuccess; ++p) {
-        db.f = parts[p]->dev;
-        e = rsint::launch_recheck_part(db, db.rc_list, db.rc_count, db.rc_cap, ff, p == 0, rgrid, s);
-      }
-      if (e == cudaSuccess) e = rsint::launch_recheck_bin(db, db.rc_list, db.rc_count, db.rc_cap, ff, rgrid, s);
-    }
-  }
-  cudaError_t e2 = cudaFreeAsync(ws, s);
-  if (e == cudaSuccess) e = e2;
-  if (e != cudaSuccess) return cuda_fail(e, "staged shoot launch");
-  return RS_OK;
-}
-
-int rs_shoot_streamed(const float* h_lens_xy, const float* h_masses, int64_t n_lens, double kappa_c, double gamma,
-                      int64_t lenses_per_pass, const rs_ray_grid* g, int64_t row_begin, int64_t row_end,
-                      const rs_window* w, uint32_t* d_counts, uint64_t* d_out_of_window, void* stream) {
-  if (n_lens < 0) return fail(RS_EINVAL, "n_lens < 0");
-  if (n_lens > 0 && !h_lens_xy) return fail(RS_EINVAL, "h_lens_xy is NULL");
-  if (lenses_per_pass < rsdev::kLensPad || lenses_per_pass % rsdev::kLensPad != 0 || lenses_per_pass > ((int64_t)1 << 30))
-    return fail(RS_EINVAL, "lenses_per_pass must be a multiple of %d in [%d, 2^30]", rsdev::kLensPad, rsdev::kLensPad);
-  if (!std::isfinite(kappa_c) || !std::isfinite(gamma)) return fail(RS_EINVAL, "kappa_c and gamma must be finite");
-  for (int64_t i = 0; i < 2 * n_lens; ++i)
-    if (!finite_coord((double)h_lens_xy[i])) return fail(RS_EINVAL, "lens coordinate %lld not finite or beyond 1e9", (long long)i);
-  if (h_masses)
-    for (int64_t i = 0; i < n_lens; ++i)
-      if (!(std::isfinite(h_masses[i]) && h_masses[i] >= 0.f)) return fail(RS_EINVAL, "mass %lld not finite or negative", (long long)i);
-  int rc;
-  if ((rc = check_call(g, row_begin, row_end, w, d_counts)) != RS_OK) return rc;
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
-  const bool mass = h_masses != nullptr;
-  const int64_t P = lenses_per_pass;
-  const int64_t n_parts = std::max<int64_t>(1, (n_lens + P - 1) / P);
-  // a partition buffer's descriptor; the lens arrays are filled pass by pass
-  rs_field proto{};
-  proto.device = dev;
-  proto.kappa_c = kappa_c;
-  proto.gamma = gamma;
-  proto.dev.has_mass = mass ? 1 : 0;
-  proto.dev.lam1 = (1.0 - kappa_c) - gamma;
-  proto.dev.lam2 = (1.0 - kappa_c) + gamma;
-  proto.dev.lamabs = std::nextafter((float)std::max(std::fabs(proto.dev.lam1), std::fabs(proto.dev.lam2)), INFINITY);
-  ShootDesc d;
-  if ((rc = fill_desc(&proto, g, row_begin, row_end, w, d_counts, d_out_of_window, &d)) != RS_OK) return rc;
-  if (d.n_rows == 0 || d.n0 == 0) return RS_OK;
-  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  // resources: two device partition buffers {raw xy, raw m, packed lens4, packed mass2}, two pinned
-  // staging buffers, a copy stream, events, the status word, the state and re-evaluation workspace
-  struct Res {
-    char* dbuf[2] = {nullptr, nullptr};
-    char* hbuf[2] = {nullptr, nullptr};
-    unsigned int* status = nullptr;
-    void* ws = nullptr;
-    cudaStream_t cs = nullptr;
-    cudaEvent_t ready[2] = {nullptr, nullptr}, freed[2] = {nullptr, nullptr}, copied[2] = {nullptr, nullptr};
-    ~Res() {
-      if (cs) cudaStreamSynchronize(cs);
-      for (int b = 0; b < 2; ++b) {
-        if (dbuf[b]) cudaFree(dbuf[b]);
-        if (hbuf[b]) cudaFreeHost(hbuf[b]);
-        if (ready[b]) cudaEventDestroy(ready[b]);
-        if (freed[b]) cudaEventDestroy(freed[b]);
-        if (copied[b]) cudaEventDestroy(copied[b]);
-      }
-      if (status) cudaFree(status);
-      if (ws) cudaFree(ws);
-      if (cs) cudaStreamDestroy(cs);
-    }
-  } r;
-  const size_t raw_xy = sizeof(float) * 2 * (size_t)P, raw_m = mass ? sizeof(float) * (size_t)P : 0;
-  const size_t off_m = raw_xy, off_l4 = (off_m + raw_m + 255) / 256 * 256;
-  const size_t off_m2 = off_l4 + sizeof(float4) * (size_t)P, dbytes = off_m2 + (mass ? sizeof(float2) * (size_t)P : 0);
-  for (int b = 0; b < 2 && e == cudaSuccess; ++b) {
-    if ((e = dev_alloc(&r.dbuf[b], dbytes)) != cudaSuccess) break;
-    if ((e = host_alloc(&r.hbuf[b], raw_xy + raw_m)) != cudaSuccess) break;
-    if ((e = cudaEventCreateWithFlags(&r.ready[b], cudaEventDisableTiming)) != cudaSuccess) break;
-    if ((e = cudaEventCreateWithFlags(&r.freed[b], cudaEventDisableTiming)) != cudaSuccess) break;
-    e = cudaEventCreateWithFlags(&r.copied[b], cudaEventDisableTiming);
-  }
-  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&r.cs, cudaStreamNonBlocking);
-  if (e == cudaSuccess) e = dev_alloc(&r.status, sizeof(unsigned int));
-  if (e == cudaSuccess) e = cudaMemset(r.status, 0, sizeof(unsigned int));
-  // state and re-evaluation workspace, as rs_shoot_staged
-  const int64_t rows_blk = std::max<int64_t>(4, (int64_t)(g_staged_budget / rsint::staged_state_bytes(4, d.n0)) * 4);
-  const int64_t rows_max = std::min<int64_t>(rows_blk, d.n_rows);
-  const size_t state_bytes = rsint::staged_state_bytes(rows_max, d.n0);
-  const unsigned cap = g_certify ? rsint::recheck_capacity(rows_max * d.n0) : 0u;
-  const size_t list_off = (state_bytes + 255) / 256 * 256;
-  const size_t ff_off = list_off + 16 + sizeof(uint2) * (size_t)cap;
-  if (e == cudaSuccess) e = dev_alloc(&r.ws, ff_off + sizeof(float4) * (size_t)cap);
-  if (e != cudaSuccess) return cuda_fail(e, "streamed-shoot resources");
-  char* base = reinterpret_cast<char*>(r.ws);
-  uint64_t* state = reinterpret_cast<uint64_t*>(base);
-  float4* ff = reinterpret_cast<float4*>(base + ff_off);
-  if (g_certify) {
-    d.rc_cap = cap;
-    d.rc_count = reinterpret_cast<unsigned int*>(base + list_off);
-    d.rc_list = reinterpret_cast<uint2*>(base + list_off + 16);
-  }
-  FieldDev fdev[2];
-  for (int b = 0; b < 2; ++b) {
-    fdev[b] = proto.dev;
-    fdev[b].lens4 = reinterpret_cast<const float4*>(r.dbuf[b] + off_l4);
-    fdev[b].mass2 = mass ? reinterpret_cast<const float2*>(r.dbuf[b] + off_m2) : nullptr;
-    fdev[b].status = r.status;
-  }
-  const int threads = 256;
-  const int pblocks = (int)std::min<int64_t>((P + threads - 1) / threads, (int64_t)num_sms(dev) * 16);
-  const int rgrid = recheck_grid(dev);
-  bool used[2] = {false, false};
-  // One sweep over the partitions: partition p goes through pinned buffer p % 2 (host copy once the
-  // previous copy out of it finished), then to device buffer p % 2 (once the kernel that read it
-  // finished) and is packed there; `pass` enqueues the kernel that consumes it on the caller's stream.
-  auto sweep = [&](auto pass) -> cudaError_t {
-    cudaError_t ee = cudaSuccess;
-    for (int64_t p = 0; p < n_parts && ee == cudaSuccess; ++p) {
-      const int b = (int)(p & 1);
-      const int64_t a0 = p * P, np = std::min<int64_t>(P, n_lens - a0);
-      if (used[b] && (ee = cudaEventSynchronize(r.copied[b])) != cudaSuccess) break;
-      if (np > 0) {
-        std::memcpy(r.hbuf[b], h_lens_xy + 2 * a0, sizeof(float) * 2 * (size_t)np);
-        if (mass) std::memcpy(r.hbuf[b] + raw_xy, h_masses + a0, sizeof(float) * (size_t)np);
-      }
-      if (used[b] && (ee = cudaStreamWaitEvent(r.cs, r.freed[b], 0)) != cudaSuccess) break;
-      if (np > 0 && (ee = cudaMemcpyAsync(r.dbuf[b], r.hbuf[b], raw_xy + raw_m, cudaMemcpyHostToDevice, r.cs)) !=
-                        cudaSuccess)
-        break;
-      if ((ee = cudaEventRecord(r.copied[b], r.cs)) != cudaSuccess) break;
-      pack_lenses_kernel<<<pblocks, threads, 0, r.cs>>>(
-          np > 0 ? reinterpret_cast<const float*>(r.dbuf[b]) : nullptr,
-          mass ? reinterpret_cast<const float*>(r.dbuf[b] + off_m) : nullptr, np, P,
-          reinterpret_cast<float4*>(r.dbuf[b] + off_l4), mass ? reinterpret_cast<float2*>(r.dbuf[b] + off_m2) : nullptr);
-      if ((ee = cudaGetLastError()) != cudaSuccess) break;
-      if ((ee = cudaEventRecord(r.ready[b], r.cs)) != cudaSuccess) break;
-      if ((ee = cudaStreamWaitEvent(s, r.ready[b], 0)) != cudaSuccess) break;
-      FieldDev fd = fdev[b];
-      fd.n_lens = (int32_t)np;
-      if ((ee = pass(fd, p == 0, p == n_parts - 1)) != cudaSuccess) break;
-      if ((ee = cudaEventRecord(r.freed[b], s)) != cudaSuccess) break;
-      used[b] = true;
-    }
-    return ee;
-  };
-  for (int64_t r0 = 0; r0 < d.n_rows && e == cudaSuccess; r0 += rows_blk) {
-    ShootDesc db = d;
-    db.j_begin = d.j_begin + r0;
-    db.n_rows = std::min<int64_t>(rows_blk, d.n_rows - r0);
-    if (g_certify) e = cudaMemsetAsync(db.rc_count, 0, sizeof(unsigned int), s);
-    if (e == cudaSuccess)
-      e = sweep([&](const FieldDev& fd, bool first, bool last) {
-        ShootDesc dp = db;
-        dp.f = fd;
-        return rsint::launch_staged(dp, state, first, last, s);
-      });
-    if (e == cudaSuccess && g_certify) {
-      e = sweep([&](const FieldDev& fd, bool first, bool) {
-        ShootDesc dp = db;
-        dp.f = fd;
-        return rsint::launch_recheck_part(dp, db.rc_list, db.rc_count, db.rc_cap, ff, first, rgrid, s);
-      });
-      if (e == cudaSuccess) e = rsint::launch_recheck_bin(db, db.rc_list, db.rc_count, db.rc_cap, ff, rgrid, s);
-    }
-  }
-  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-  if (e != cudaSuccess) return cuda_fail(e, "streamed shoot");
-  unsigned int st = 0;
-  if ((e = cudaMemcpy(&st, r.status, sizeof(st), cudaMemcpyDeviceToHost)) != cudaSuccess)
-    return cuda_fail(e, "cudaMemcpy (status)");
-  if (st != 0) return fail(RS_ETIMEOUT, "a bounded wait for a lens tile gave up");
-  return RS_OK;
-}
-
 int rs_shoot(rs_field_t f, const rs_ray_grid* g, const rs_window* w, uint32_t* d_counts, uint64_t* d_out_of_window,
              void* stream) {
   if (!g) return fail(RS_EINVAL, "ray grid is NULL");
@@ -1041,12 +640,6 @@ int rs_set_alloc_failure(int64_t n) {
   return RS_OK;
 }
 
-int rs_set_staged_state_budget(uint64_t bytes) {
-  if (bytes < ((uint64_t)1 << 20)) return fail(RS_EINVAL, "the staged state budget must be at least 1 MiB");
-  g_staged_budget = (size_t)bytes;
-  return RS_OK;
-}
-
 int rs_get_certified_binning(int* enabled) {
   if (!enabled) return fail(RS_EINVAL, "enabled is NULL");
   *enabled = g_certify;
@@ -1072,270 +665,6 @@ int rs_magnification(const uint32_t* d_counts, const rs_ray_grid* g, const rs_wi
                                                                                         (float)(1.0 / n_av), vec);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "magnification kernel launch");
-  return RS_OK;
-}
-
-// ------------------------------------------------------------------------------------------------ light curves
-
-int rs_light_curves(int n_maps, const float* const* d_mu, const rs_window* windows, int profile, double s,
-                    int n_tracks, const rs_track* tracks, double* d_mu_out, double* d_dm_out, void* stream) {
-  LcPlan plan;
-  int rc = lc_prepare(n_maps, d_mu, windows, profile, s, n_tracks, tracks, &plan);
-  if (rc != RS_OK || plan.total == 0) return rc;
-  if (!d_mu_out) return fail(RS_EINVAL, "d_mu_out is NULL");
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
-  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-  rsint::LcTrack* d_table = nullptr;
-  const size_t bytes = plan.table.size() * sizeof(rsint::LcTrack);
-  if ((e = dev_alloc_async(&d_table, bytes, st)) != cudaSuccess)
-    return cuda_fail(e, "cudaMallocAsync (track table)");
-  e = cudaMemcpyAsync(d_table, plan.table.data(), bytes, cudaMemcpyHostToDevice, st);
-  if (e == cudaSuccess)
-    e = rsint::launch_light_curves(plan.profile, d_table, (int)plan.table.size(), plan.total, plan.cut2, plan.ecut,
-                                   d_mu_out, d_dm_out, lc_grid(dev, plan.total), st);
-  cudaFreeAsync(d_table, st);
-  if (e != cudaSuccess) return cuda_fail(e, "light-curve kernel");
-  return RS_OK;
-}
-
-int rs_light_curve_plan_create(int n_maps, const float* const* d_mu, const rs_window* windows, int profile,
-                               double s, int n_tracks, const rs_track* tracks, rs_lc_plan_t* out) {
-  if (!out) return fail(RS_EINVAL, "out is NULL");
-  *out = nullptr;
-  LcPlan plan;
-  int rc = lc_prepare(n_maps, d_mu, windows, profile, s, n_tracks, tracks, &plan);
-  if (rc != RS_OK) return rc;
-  rs_lc_plan* p = new (std::nothrow) rs_lc_plan{};
-  if (!p) return fail(RS_ENOMEM, "host allocation failed");
-  cudaError_t e = cudaGetDevice(&p->device);
-  if (e != cudaSuccess) {
-    delete p;
-    return cuda_fail(e, "cudaGetDevice");
-  }
-  p->n_tracks = (int)plan.table.size();
-  p->total = plan.total;
-  p->profile = plan.profile;
-  p->cut2 = plan.cut2;
-  p->ecut = plan.ecut;
-  p->grid = lc_grid(p->device, plan.total);
-  if (p->n_tracks > 0) {
-    const size_t bytes = plan.table.size() * sizeof(rsint::LcTrack);
-    if ((e = dev_alloc(&p->d_table, bytes)) != cudaSuccess) {
-      delete p;
-      return cuda_fail(e, "cudaMalloc (track table)");
-    }
-    if ((e = cudaMemcpy(p->d_table, plan.table.data(), bytes, cudaMemcpyHostToDevice)) != cudaSuccess) {
-      cudaFree(p->d_table);
-      delete p;
-      return cuda_fail(e, "cudaMemcpy (track table)");
-    }
-  }
-  *out = p;
-  return RS_OK;
-}
-
-int rs_light_curve_plan_samples(rs_lc_plan_t p, int64_t* n_samples) {
-  if (!p || !n_samples) return fail(RS_EINVAL, "NULL argument");
-  *n_samples = p->total;
-  return RS_OK;
-}
-
-int rs_light_curve_plan_launch(rs_lc_plan_t p, double* d_mu_out, double* d_dm_out, void* stream) {
-  if (!p) return fail(RS_EINVAL, "plan is NULL");
-  if (p->total == 0) return RS_OK;
-  if (!d_mu_out) return fail(RS_EINVAL, "d_mu_out is NULL");
-  int cur = -1;
-  cudaError_t e = cudaGetDevice(&cur);
-  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
-  if (cur != p->device) return fail(RS_EINVAL, "plan lives on device %d but device %d is current", p->device, cur);
-  e = rsint::launch_light_curves(p->profile, p->d_table, p->n_tracks, p->total, p->cut2, p->ecut, d_mu_out, d_dm_out,
-                                 p->grid, reinterpret_cast<cudaStream_t>(stream));
-  if (e != cudaSuccess) return cuda_fail(e, "light-curve kernel");
-  return RS_OK;
-}
-
-int rs_light_curve_plan_destroy(rs_lc_plan_t p) {
-  if (!p) return RS_OK;
-  int prev = -1;
-  cudaGetDevice(&prev);
-  cudaSetDevice(p->device);
-  cudaDeviceSynchronize();
-  if (p->d_table) cudaFree(p->d_table);
-  if (prev >= 0) cudaSetDevice(prev);
-  delete p;
-  return RS_OK;
-}
-
-// ------------------------------------------------------------------------------------------------ batch
-
-int rs_batch_create(int n_fields, const rs_field_t* fields, const rs_ray_grid* grids, const rs_window* windows,
-                    uint32_t* const* d_counts, uint64_t* d_out_of_window, rs_batch_t* out) {
-  if (!out) return fail(RS_EINVAL, "out is NULL");
-  *out = nullptr;
-  if (n_fields <= 0) return fail(RS_EINVAL, "n_fields must be >= 1");
-  if (!fields || !grids || !windows || !d_counts) return fail(RS_EINVAL, "NULL array argument");
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
-  int rc;
-  std::vector<ShootDesc> descs(n_fields);
-  struct Item {
-    double cost;
-    int field;
-    int tile;
-  };
-  std::vector<Item> items[2];
-  for (int k = 0; k < n_fields; ++k) {
-    if (!fields[k]) return fail(RS_EINVAL, "fields[%d] is NULL", k);
-    if (fields[k]->device != dev) return fail(RS_EINVAL, "fields[%d] lives on another device", k);
-    if ((rc = check_grid(&grids[k])) != RS_OK) return rc;
-    if ((rc = check_window(&windows[k])) != RS_OK) return rc;
-    if (!d_counts[k]) return fail(RS_EINVAL, "d_counts[%d] is NULL", k);
-    if ((rc = fill_desc(fields[k], &grids[k], 0, grids[k].n[1], &windows[k], d_counts[k],
-                        d_out_of_window ? d_out_of_window + k : nullptr, &descs[k])) != RS_OK)
-      return rc;
-    const int grp = fields[k]->dev.has_mass ? 1 : 0;
-    const int warps = rsint::kCfgs[g_cfg[grp]].block / 32;
-    const int64_t seg = 32 * (int64_t)rsint::kCfgs[g_cfg[grp]].rpt;
-    const int64_t n0 = descs[k].n0, nr = descs[k].n_rows;
-    if (n0 == 0 || nr == 0) continue;
-    const int64_t ncol = (n0 + seg - 1) / seg;
-    const int64_t nt = ((nr + warps - 1) / warps) * ncol;
-    if ((int64_t)(items[0].size() + items[1].size()) + nt >= ((int64_t)1 << 31))
-      return fail(RS_EOVERFLOW, "too many work items");
-    for (int64_t t = 0; t < nt; ++t) {
-      const int64_t trow = t / ncol, tcol = t - trow * ncol;
-      const int64_t rows = std::min<int64_t>(warps, nr - trow * warps);
-      const int64_t cols = std::min<int64_t>(seg, n0 - tcol * seg);
-      // per-ray cost: one interaction per lens plus a fixed epilogue (~ 64 interactions)
-      const double cost = (double)(rows * cols) * ((double)fields[k]->n_lens + 64.0);
-      items[grp].push_back({cost, k, (int)t});
-    }
-  }
-  std::vector<int2> h_items;
-  rs_batch* b = new (std::nothrow) rs_batch();
-  if (!b) return fail(RS_ENOMEM, "host allocation failed");
-  b->device = dev;
-  b->n_fields = n_fields;
-  for (int grp = 0; grp < 2; ++grp) {
-    std::stable_sort(items[grp].begin(), items[grp].end(),
-                     [](const Item& x, const Item& y) { return x.cost > y.cost; });
-    b->item_offset[grp] = (int)h_items.size();
-    b->n_items[grp] = (int)items[grp].size();
-    for (const Item& it : items[grp]) h_items.push_back(make_int2(it.field, it.tile));
-    b->cfg[grp] = g_cfg[grp];
-    int bps = 0;
-    if (rsint::batch_blocks_per_sm(b->cfg[grp], grp == 1, &bps) != cudaSuccess || bps < 1) bps = 1;
-    b->grid[grp] = num_sms(dev) * bps;
-  }
-  auto cleanup = [&]() {
-    if (b->exec) cudaGraphExecDestroy(b->exec);
-    if (b->graph) cudaGraphDestroy(b->graph);
-    cudaFree(b->d_descs);
-    cudaFree(b->d_items);
-    cudaFree(b->d_counter);
-    cudaFree(b->d_rc_list);
-    cudaFree(b->d_rc_count);
-    delete b;
-  };
-  if (g_certify) {
-    int64_t total = 0;
-    for (int k = 0; k < n_fields; ++k) total += descs[k].n_rows * descs[k].n0;
-    b->rc_cap = rsint::recheck_capacity(total);
-  }
-  if ((e = dev_alloc(&b->d_descs, sizeof(ShootDesc) * n_fields)) != cudaSuccess ||
-      (e = dev_alloc(&b->d_items, sizeof(int2) * std::max<size_t>(1, h_items.size()))) != cudaSuccess ||
-      (e = dev_alloc(&b->d_counter, 2 * sizeof(int))) != cudaSuccess ||
-      (b->rc_cap > 0 && (e = dev_alloc(&b->d_rc_list, sizeof(uint2) * (size_t)b->rc_cap)) != cudaSuccess) ||
-      (b->rc_cap > 0 && (e = dev_alloc(&b->d_rc_count, sizeof(unsigned int))) != cudaSuccess)) {
-    rc = cuda_fail(e, "cudaMalloc (batch)");
-    cleanup();
-    return rc;
-  }
-  for (int k = 0; k < n_fields; ++k) {
-    descs[k].field_id = k;
-    descs[k].rc_list = b->d_rc_list;
-    descs[k].rc_count = b->d_rc_count;
-    descs[k].rc_cap = b->rc_cap;
-  }
-  if ((e = cudaMemcpy(b->d_descs, descs.data(), sizeof(ShootDesc) * n_fields, cudaMemcpyHostToDevice)) != cudaSuccess ||
-      (!h_items.empty() &&
-       (e = cudaMemcpy(b->d_items, h_items.data(), sizeof(int2) * h_items.size(), cudaMemcpyHostToDevice)) != cudaSuccess)) {
-    rc = cuda_fail(e, "cudaMemcpy (batch descriptors)");
-    cleanup();
-    return rc;
-  }
-  // Capture: zero every map and counter, then the persistent kernel.
-  cudaStream_t cs;
-  if ((e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking)) != cudaSuccess) {
-    rc = cuda_fail(e, "cudaStreamCreate");
-    cleanup();
-    return rc;
-  }
-  e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
-  if (e == cudaSuccess) {
-    for (int k = 0; k < n_fields && e == cudaSuccess; ++k)
-      e = cudaMemsetAsync(d_counts[k], 0, sizeof(uint32_t) * (size_t)windows[k].npix[0] * (size_t)windows[k].npix[1], cs);
-    if (e == cudaSuccess && d_out_of_window) e = cudaMemsetAsync(d_out_of_window, 0, sizeof(uint64_t) * n_fields, cs);
-    if (e == cudaSuccess) e = cudaMemsetAsync(b->d_counter, 0, 2 * sizeof(int), cs);
-    if (e == cudaSuccess && b->rc_cap > 0) e = cudaMemsetAsync(b->d_rc_count, 0, sizeof(unsigned int), cs);
-    for (int grp = 1; grp >= 0 && e == cudaSuccess; --grp)
-      if (b->n_items[grp] > 0)
-        e = rsint::launch_batch(b->cfg[grp], grp == 1, b->d_descs, b->d_items + b->item_offset[grp], b->n_items[grp],
-                                b->d_counter + grp, b->grid[grp], cs);
-    if (e == cudaSuccess && b->rc_cap > 0)
-      e = rsint::launch_recheck(nullptr, b->d_descs, b->d_rc_list, b->d_rc_count, b->rc_cap, recheck_grid(dev), cs);
-    cudaError_t e2 = cudaStreamEndCapture(cs, &b->graph);
-    if (e == cudaSuccess) e = e2;
-  }
-  if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, b->graph, 0);
-  cudaStreamDestroy(cs);
-  if (e != cudaSuccess) {
-    rc = cuda_fail(e, "batch graph capture");
-    cleanup();
-    return rc;
-  }
-  *out = b;
-  return RS_OK;
-}
-
-int rs_batch_launch(rs_batch_t b, void* stream) {
-  if (!b) return fail(RS_EINVAL, "batch is NULL");
-  int cur = -1;
-  cudaGetDevice(&cur);
-  if (cur != b->device) return fail(RS_EINVAL, "batch lives on device %d but device %d is current", b->device, cur);
-  cudaError_t e = cudaGraphLaunch(b->exec, reinterpret_cast<cudaStream_t>(stream));
-  if (e != cudaSuccess) return cuda_fail(e, "cudaGraphLaunch");
-  return RS_OK;
-}
-
-int rs_batch_destroy(rs_batch_t b) {
-  if (!b) return RS_OK;
-  DeviceGuard g(b->device);
-  cudaDeviceSynchronize();
-  if (b->exec) cudaGraphExecDestroy(b->exec);
-  if (b->graph) cudaGraphDestroy(b->graph);
-  cudaFree(b->d_descs);
-  cudaFree(b->d_items);
-  cudaFree(b->d_counter);
-  cudaFree(b->d_rc_list);
-  cudaFree(b->d_rc_count);
-  delete b;
-  return RS_OK;
-}
-
-int rs_shoot_batch(int n_fields, const rs_field_t* fields, const rs_ray_grid* grids, const rs_window* windows,
-                   uint32_t* const* d_counts, uint64_t* d_out_of_window, void* stream) {
-  rs_batch_t b = nullptr;
-  int rc = rs_batch_create(n_fields, fields, grids, windows, d_counts, d_out_of_window, &b);
-  if (rc != RS_OK) return rc;
-  rc = rs_batch_launch(b, stream);
-  cudaError_t e = cudaStreamSynchronize(reinterpret_cast<cudaStream_t>(stream));
-  rs_batch_destroy(b);
-  if (rc != RS_OK) return rc;
-  if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize (batch)");
   return RS_OK;
 }
 
@@ -1408,3 +737,4 @@ extern "C" int rs_shoot_rows_noalloc(rs_field_t f, const rs_ray_grid* g, int64_t
   if (e != cudaSuccess) return cuda_fail(e, "shoot launch (no-allocation variant)");
   return RS_OK;
 }
+
