@@ -232,7 +232,7 @@ int rs_trace_certified(rs_field_t f, const rs_ray_grid* g, const int64_t* d_ray_
  * binned from that; the maps then agree with a float64 evaluation except for rays within ~1e-12
  * of an edge.  rs_shoot allocates the list of such rays stream-ordered (cudaMallocAsync,
  * capacity max(4096, rays/32), at most 2^24 entries); rays beyond the capacity keep their
- * float32 decision.  Batches own their list.
+ * float32 decision and the field's status records RS_EOVERFLOW (rs_field_status).  Batches own their list.
  * rs_set_certified_binning(0) turns it off for calls (and batches planned) afterwards.
  */
 int rs_set_certified_binning(int enabled);
@@ -274,9 +274,11 @@ int rs_shoot_batch(int n_fields, const rs_field_t* fields, const rs_ray_grid* gr
                    void* stream);
 
 /*
- * rs_field_status -- synchronise the field's device and report whether a
- * kernel that used it gave up a bounded wait: *status = RS_OK or RS_ETIMEOUT.
- * clear != 0 resets the flag.
+ * rs_field_status -- synchronise the field's device and report what kernels that used it
+ * recorded: *status = RS_ETIMEOUT if a bounded wait gave up; else RS_EOVERFLOW if the list of
+ * rays to re-evaluate (certified binning) of some call was full, so that some rays kept their
+ * float32 decision (shoot fewer rows per call); else RS_OK.  For staged shoots the last
+ * partition's field records the list state.  clear != 0 resets the flags.
  */
 int rs_field_status(rs_field_t f, int clear, int* status);
 

@@ -489,7 +489,7 @@ int rs_field_status(rs_field_t f, int clear, int* status) {
   unsigned int v = 0;
   if ((e = cudaMemcpy(&v, f->status, sizeof(v), cudaMemcpyDeviceToHost)) != cudaSuccess)
     return cuda_fail(e, "cudaMemcpy (status)");
-  *status = v == 0 ? RS_OK : (int)v;
+  *status = (v & 0xffu) == rsdev::kStatusTimeout ? RS_ETIMEOUT : (v & rsdev::kStatusListFull) ? RS_EOVERFLOW : RS_OK;
   if (clear && v != 0) {
     if ((e = cudaMemset(f->status, 0, sizeof(unsigned int))) != cudaSuccess) return cuda_fail(e, "cudaMemset (status)");
   }

@@ -240,7 +240,10 @@ int rs_shoot_streamed(const float* h_lens_xy, const float* h_masses, int64_t n_l
   unsigned int st = 0;
   if ((e = cudaMemcpy(&st, r.status, sizeof(st), cudaMemcpyDeviceToHost)) != cudaSuccess)
     return cuda_fail(e, "cudaMemcpy (status)");
-  if (st != 0) return fail(RS_ETIMEOUT, "a bounded wait for a lens tile gave up");
+  if ((st & 0xffu) == rsdev::kStatusTimeout) return fail(RS_ETIMEOUT, "a bounded wait for a lens tile gave up");
+  if (st & rsdev::kStatusListFull)
+    return fail(RS_EOVERFLOW, "the certified-binning list overflowed: some rays kept their float32 decision "
+                              "(shoot fewer rows per call)");
   return RS_OK;
 }
 

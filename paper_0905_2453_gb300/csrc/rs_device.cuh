@@ -45,7 +45,8 @@ constexpr int kGroup = 64;                 // lenses per float32 partial sum (fi
 constexpr int kRenorm = 256;               // (hi, lo) renormalised after every 256 lenses (fixed: arithmetic)
 constexpr int kLensPad = 1024;             // device lens arrays are padded to a multiple of this
 constexpr uint64_t kWaitLimitNs = 1000000000ull;  // bounded mbarrier wait: 1 s
-constexpr unsigned kStatusTimeout = 5u;    // == RS_ETIMEOUT
+constexpr unsigned kStatusTimeout = 5u;    // == RS_ETIMEOUT (low byte of the status word)
+constexpr unsigned kStatusListFull = 0x100u;  // a certified-binning list overflowed (bit 8)
 
 // ----------------------------------------------------------------------------------------------
 // Packed f32x2 arithmetic (sm_100+): a uint64_t holds {lo = ray A, hi = ray B}.
@@ -517,7 +518,7 @@ __device__ __forceinline__ bool deflect_accumulate(const FieldDev& f, const uint
   if (!ok) {
     // Record the timeout and drain this CTA's copies still in flight (bounded) before leaving:
     // tile t (its parity was already flipped above) and tile t + 1 if it was issued.
-    if (threadIdx.x == 0) atomicExch(f.status, kStatusTimeout);
+    if (threadIdx.x == 0) atomicOr(f.status, kStatusTimeout);
     (void)mbar_wait_bounded(&sm.bar[t & 1], ps.parity[t & 1] ^ 1u);
     if (t + 1 < ntiles) (void)mbar_wait_bounded(&sm.bar[(t + 1) & 1], ps.parity[(t + 1) & 1]);
     return false;
@@ -690,8 +691,9 @@ __device__ __forceinline__ void bin_rays(const ShootDesc& d, const float (&x1)[R
             const int64_t i = i_base + STRIDE * k;
             d.rc_list[slot] = make_uint2((unsigned)d.field_id, (unsigned)(jrel * d.n0 + i));
             bin_now = false;  // counted by the float-float re-evaluation
+          } else {
+            atomicOr(d.f.status, kStatusListFull);  // list full: the ray keeps its float32 decision
           }
-          // list full: the ray keeps its float32 decision
         }
       }
     }

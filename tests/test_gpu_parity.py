@@ -308,3 +308,26 @@ def test_far_from_origin_certified_map():
     ref, oref = oracle.shoot_field(f)
     assert counts.sum() > 0
     assert np.array_equal(counts, ref) and oow == oref
+
+
+def test_certified_list_overflow_is_reported():
+    """Pixels far narrower than the rays' error bands make nearly every in-window ray uncertain, so the
+    re-evaluation list (rays / 32 entries) overflows: the field's status reports RS_EOVERFLOW (those rays
+    kept their float32 decision); after clearing, a normal shoot reports RS_OK."""
+    m = rs()
+    xy, _ = ri.disc_lenses(50, 5.0, seed=9)
+    g = ri.RayGrid(origin=(-1.0 + 1 / 1024, -1.0 + 1 / 1024), spacing=(1 / 512, 1 / 512), n=(1024, 1024))
+    thin = ri.Window(lo=(-0.5, -2.0), hi=(0.5, 2.0), npix=(1 << 22, 1))
+    normal = ri.Window(lo=(-2.0, -2.0), hi=(2.0, 2.0), npix=(64, 64))
+    f = m.Field(xy)
+    try:
+        c = torch.zeros((1, 1 << 22), dtype=torch.int32, device=dev())
+        o = torch.zeros(1, dtype=torch.int64, device=dev())
+        f.shoot(g, thin, c, o)
+        assert f.status(clear=True) == m.RS_EOVERFLOW
+        assert int(c.sum().item()) + int(o.item()) == g.n_rays        # every ray still counted once
+        assert f.status() == m.RS_OK
+        f.shoot(g, normal)
+        assert f.status() == m.RS_OK
+    finally:
+        f.close()
