@@ -56,7 +56,9 @@ def workload_config(spec, name):
     return {
         "workload": spec.name,
         "n_lens": spec.n_lens,
-        "masses": "per-lens float32" if spec.masses is not None else "unit (equal-mass kernels)",
+        "masses": ("unit (equal-mass kernels)" if spec.masses is None else
+                   "float32, all 1 (stored; equal-mass kernels)" if bool(np.all(spec.masses == 1.0)) else
+                   "per-lens float32"),
         "kappa_star": round(spec.kappa_star, 6), "kappa_c": spec.kappa_c, "gamma": spec.gamma,
         "ray_grid": list(spec.grid.n), "map": list(spec.window.npix),
         "rays_per_step": spec.grid.n_rays,
@@ -274,7 +276,7 @@ def run_ours(args):
     from paper_0905_2453_gb300 import tune
     if args.launch_shape:
         b_, r_ = (int(v) for v in args.launch_shape.split("x"))
-        rs.rs_set_launch_config(spec.masses is not None, b_, r_)
+        rs.rs_set_launch_config(field.info()[1], b_, r_)
         shape = (b_, r_, {})
     else:
         shape = tune.autotune(field, spec.grid, spec.window, stream=stream)
@@ -657,7 +659,7 @@ def run_section(args):
         spec = workload(args.workload, seed=0)
         if args.launch_shape:
             b_, r_ = (int(v) for v in args.launch_shape.split("x"))
-            rs.rs_set_launch_config(spec.masses is not None, b_, r_)
+            rs.rs_set_launch_config(spec.masses is not None and not bool(np.all(spec.masses == 1.0)), b_, r_)
         out = {"zoom": run_zoom(rs, torch, device, stream, spec),
                "culled_full_map": run_zoom(rs, torch, device, stream, spec, factor=1, quarter=False)}
     elif args.section == "batch-small":
@@ -665,6 +667,10 @@ def run_section(args):
     elif args.section == "staged":
         spec = workload(args.workload, seed=0)
         out = {"staged": run_staged(rs, torch, device, stream, spec)}
+    elif args.section == "configs":
+        names = [v for v in args.configs.split(",") if v]
+        out = {"configs": run_configs(rs, torch, device, stream, names, cpu=not args.no_cpu_baseline,
+                                      launch_shape=args.launch_shape)}
     elif args.section == "frames":
         spec = workload(args.workload, seed=0)
         out = {"frames": run_frames(rs, torch, device, stream, spec)}
@@ -772,6 +778,103 @@ def run_staged(rs, torch, device, stream, spec, parts=4, reps=3):
     return out
 
 
+def oracle_trace_rate(spec, n_rays: int, seed: int = 11):
+    """The FP64 oracle on a random subset of the grid's rays (per-ray evaluation): interactions/s."""
+    import oracle
+    oracle.build()
+    rng = np.random.default_rng(seed)
+    ij = np.stack([rng.integers(0, int(spec.grid.n[0]), n_rays), rng.integers(0, int(spec.grid.n[1]), n_rays)], 1)
+    t = time.perf_counter()
+    oracle.trace_field(spec, ij)
+    dt = time.perf_counter() - t
+    return {"value": n_rays * spec.n_lens / dt, "unit": METRIC, "seconds": dt, "cores": oracle.num_threads(),
+            "kind": "oracle", "sample": f"{n_rays} random rays of the grid, all {spec.n_lens} lenses"}
+
+
+def run_configs(rs, torch, device, stream, names, cpu=True, full_limit=2e12, max_sample=2e13, launch_shape=None):
+    """Throughput of the shoot on every workload configuration (1 GPU).
+
+    Grids of up to full_limit interactions are shot whole.  Larger ones are timed on two blocks of
+    central rows, k and 2k units of rows that hold a whole number of waves of the tuned launch shape
+    (a multiple of 2 x SMs CTAs: whole waves at one or two resident CTAs per SM, every launch shape
+    here).  The rate of the larger block is the sample rate; the difference of the two (the work of
+    k units over the difference of the times) is the steady-state rate of the full grid, whose ragged
+    end of the last CTAs -- up to one CTA time, seconds with 1e8 lenses -- the difference cancels.
+    """
+    from paper_0905_2453_gb300 import tune
+    sms = torch.cuda.get_device_properties(device).multi_processor_count
+    peak = fp32_peak_tflops(sms, 2070) * 1e12
+
+    def pct(rate):
+        return 100.0 * rate * FLOPS_PER_INTERACTION / peak
+
+    out = {}
+    for name in names:
+        spec = workload(name, seed=0)
+        f = rs.Field.from_spec(spec, stream)
+        n_lens, weighted = f.info()
+        if launch_shape:
+            b, r = (int(v) for v in launch_shape.split("x"))
+            rs.rs_set_launch_config(weighted, b, r)
+        else:
+            b, r, _ = tune.autotune(f, spec.grid, spec.window, stream=stream)
+        n0, n1 = int(spec.grid.n[0]), int(spec.grid.n[1])
+        npix = (int(spec.window.npix[1]), int(spec.window.npix[0]))
+        c = torch.zeros(npix, dtype=torch.int32, device=device)
+        o = torch.zeros(1, dtype=torch.int64, device=device)
+        clocks = ClockSampler(device.index or 0)
+        clocks.start()
+
+        def timed(r0, r1, warm=True):
+            if warm:
+                rs.rs_shoot_rows(f.handle, spec.grid, r0, r1, spec.window, c, o, stream)
+            torch.cuda.synchronize(device)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            rs.rs_shoot_rows(f.handle, spec.grid, r0, r1, spec.window, c, o, stream)
+            e1.record(stream)
+            torch.cuda.synchronize(device)
+            return e0.elapsed_time(e1)
+
+        entry = {"workload": spec.name, "n_lens": n_lens, "weighted_kernels": bool(weighted),
+                 "launch_shape": f"{b}x{r}", "full_grid_interactions": spec.interactions}
+        if spec.interactions <= full_limit:
+            ms = timed(0, n1)
+            rate = spec.interactions / (ms / 1e3)
+            entry.update({"sample": "whole grid", "rows": [0, n1], "ms": ms, "interactions_per_s": rate,
+                          "pct_fp32_peak_2070mhz": pct(rate)})
+        else:
+            warps, seg = b // 32, 32 * r
+            cpr = -(-n0 // seg)                             # CTAs per group of `warps` rows
+            unit = (2 * sms) // math.gcd(2 * sms, cpr) * warps
+            per_unit = unit * n0 * n_lens
+            k = max(1, min(n1 // (2 * unit), int(max_sample // (2 * per_unit))))
+            blocks = []
+            for rows in (k * unit, 2 * k * unit):
+                r0 = (n1 - rows) // 2 // warps * warps
+                ms = timed(r0, r0 + rows, warm=not blocks)
+                blocks.append({"rows": [r0, r0 + rows], "ctas": cpr * (rows // warps), "ms": ms,
+                               "interactions_per_s": rows * n0 * n_lens / (ms / 1e3)})
+            steady = k * per_unit / ((blocks[1]["ms"] - blocks[0]["ms"]) / 1e3)
+            entry.update({"sample": f"central row blocks of {k} and {2 * k} x {unit} rows ({blocks[0]['ctas']} and "
+                                    f"{blocks[1]['ctas']} CTAs of {b} threads on {sms} SMs)",
+                          "blocks": blocks, "interactions_per_s": steady, "pct_fp32_peak_2070mhz": pct(steady),
+                          "sample_interactions_per_s": blocks[1]["interactions_per_s"],
+                          "sample_pct_fp32_peak_2070mhz": pct(blocks[1]["interactions_per_s"])})
+        entry["clocks"] = clocks.stop()
+        entry["full_grid_seconds_at_this_rate"] = spec.interactions / entry["interactions_per_s"]
+        entry["status"] = f.status()
+        f.close()
+        if cpu:
+            n_rays = max(16, min(100_000, int(3e9 / max(1, n_lens))))
+            entry["cpu_baseline"] = oracle_trace_rate(spec, n_rays)
+        out[name] = entry
+        log(f"config {name}: {json.dumps(entry)}")
+        del c, o
+        torch.cuda.empty_cache()
+    return out
+
+
 def args_workload_name(spec):
     return getattr(spec, "name", "field")
 
@@ -789,7 +892,10 @@ def main():
     ap.add_argument("--no-zoom", action="store_true")
     ap.add_argument("--no-frames", action="store_true")
     ap.add_argument("--no-staged", action="store_true")
-    ap.add_argument("--section", choices=["zoom", "light-curves", "frames", "staged", "batch-small"], default=None,
+    ap.add_argument("--configs", default="tiny,n1e4,n1e6,n1e8",
+                    help="workloads of --section configs (comma-separated: tiny, n1e4, n1e6, n1e8)")
+    ap.add_argument("--section", choices=["zoom", "light-curves", "frames", "staged", "batch-small", "configs"],
+                    default=None,
                     help="run one secondary measurement alone and print its JSON object (for profiling)")
     ap.add_argument("--batch-reps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -89,7 +89,10 @@ typedef struct {
  * rs_create_field -- upload a lens realisation (Eq. 2 lenses, Eq. 6 macro-model).
  *   lens_xy  : float[2*n_lens], interleaved (x1, x2) per lens.  May be NULL if n_lens == 0.
  *   masses   : float[n_lens] (finite, >= 0), or NULL for unit masses.  With NULL the
- *              equal-mass kernels are used (no mass is stored or read, Section 3.2).
+ *              equal-mass kernels are used (no mass is stored or read, Section 3.2).  Masses
+ *              that are all exactly 1 also select the equal-mass kernels; they are still stored
+ *              (the field may then be a lens partition next to weighted ones).  With device
+ *              inputs that test is a reduction read back before the call returns.
  *   n_lens   : >= 0 and < 2^31.  n_lens == 0 gives the undeflected (macro-only) map.
  *   kappa_c  : smooth convergence sigma_c of Eq. 6; gamma: external shear (finite).
  *   inputs_on_device : 0 = lens_xy/masses are host pointers, 1 = device pointers.
@@ -102,8 +105,23 @@ typedef struct {
 int rs_create_field(const float* lens_xy, const float* masses, int64_t n_lens, double kappa_c,
                     double gamma, int inputs_on_device, void* stream, rs_field_t* out);
 
-/* rs_destroy_field -- release a field (synchronises its device first).  NULL is a no-op. */
+/* rs_destroy_field -- release a field (synchronises its device first).  NULL is a no-op.
+ * RS_EINVAL (nothing released) while lens-range views of the field are alive. */
 int rs_destroy_field(rs_field_t f);
+
+/*
+ * rs_create_field_view -- a field made of lenses [lens_begin, lens_begin + n_lens) of `parent`,
+ * reading the parent's device arrays (no copy; the view owns only its status word).  Uses: the
+ * deflection of a subset of the lenses (Eq. 2 is a sum, so views of disjoint ranges superpose),
+ * resident lens partitions for rs_shoot_staged, and short proxy runs on a prefix of a very large
+ * field (the autotuner).  lens_begin must be a multiple of 256 (lens tiles and the summation
+ * schedule start there, so views cut at multiples of 256 give rs_shoot_staged the parent's results
+ * bit for bit).  The view takes the parent's kappa_c, gamma and mass mode, and sees the parent's
+ * current lens positions (a view of a moving field moves with it; rs_field_set_time applies to
+ * the parent only).  The parent cannot be destroyed while views are alive.  0 <= n_lens,
+ * lens_begin + n_lens <= the parent's lens count.  Errors: RS_EINVAL, RS_ENOMEM, RS_ECUDA.
+ */
+int rs_create_field_view(rs_field_t parent, int64_t lens_begin, int64_t n_lens, rs_field_t* out);
 
 /*
  * Moving lenses (Section 4: the stars move, so the caustic network and the map change with time;
@@ -124,7 +142,9 @@ int rs_create_moving_field(const float* lens_xy, const float* vel_xy, const floa
 int rs_field_set_time(rs_field_t f, double t, void* stream);
 int rs_field_time(rs_field_t f, double* t);
 
-/* Number of lenses, and whether the field carries per-lens masses (1) or unit masses (0). */
+/* Number of lenses, and whether the field's kernels weigh lenses by their masses (1: masses given
+ * and not all exactly 1) or take unit masses (0).  The launch shape of rs_set_launch_config's mass
+ * mode has_masses applies to the field. */
 int rs_field_info(rs_field_t f, int64_t* n_lens, int* has_masses);
 
 /*
@@ -170,7 +190,9 @@ int rs_shoot_culled(rs_field_t f, const rs_ray_grid* g, int64_t row_begin, int64
  * partially deflected rays carried in device memory between the passes, and the rays are mapped
  * and binned after the last partition).  For fields of 2^31 lenses or more, or lenses held as
  * shards.  The lens order is partition 0's lenses, then partition 1's, ...; every partition but
- * the last must hold a multiple of 256 lenses, and all share device, mass mode, kappa_c and gamma.
+ * the last must hold a multiple of 256 lenses, and all share device, kappa_c, gamma and whether
+ * masses were given (masses given to all or to none; if any partition's masses are not all 1, every
+ * partition runs the weighted kernels).
  * The carried state is the shoot kernel's own accumulator set (24 bytes per ray, stream-ordered
  * allocation; rays are processed in row blocks of at most 2 GiB of state), so the float32
  * deflections, error bands and counts equal those of one rs_shoot_rows over a single field
@@ -184,7 +206,8 @@ int rs_shoot_staged(int n_parts, const rs_field_t* parts, const rs_ray_grid* g, 
 /*
  * rs_shoot_streamed -- rs_shoot_staged for lenses held in HOST memory (out-of-core: more lenses than
  * fit the device, or than one field may hold).  The lenses (h_lens_xy: float[2*n_lens] interleaved,
- * h_masses: float[n_lens] or NULL for unit masses, n_lens may exceed 2^31) stream through the device
+ * h_masses: float[n_lens] or NULL for unit masses -- masses all exactly 1 count as unit masses and
+ * are not uploaded --, n_lens may exceed 2^31) stream through the device
  * in passes of lenses_per_pass lenses (a multiple of 1024, at most 2^30) via two pinned staging
  * buffers and two device buffers: the host copy and upload of the next partition overlap the pass
  * over the current one on the GPU.  With certified binning on, a second sweep streams the lenses

@@ -33,7 +33,7 @@ __all__ = [
     "rs_selftest_bounded_wait", "rs_shoot_rows_noalloc", "rs_light_curves", "rs_shoot_culled",
     "rs_create_moving_field", "rs_field_set_time", "rs_field_time", "rs_shoot_staged", "rs_shoot_streamed",
     "rs_set_staged_state_budget", "rs_set_alloc_failure", "rs_light_curve_plan_create", "rs_light_curve_plan_samples",
-    "rs_light_curve_plan_launch", "rs_light_curve_plan_destroy",
+    "rs_light_curve_plan_launch", "rs_light_curve_plan_destroy", "rs_create_field_view",
 ]
 
 RS_OK, RS_EINVAL, RS_ENOMEM, RS_ECUDA, RS_EOVERFLOW, RS_ETIMEOUT = 0, 1, 2, 3, 4, 5
@@ -48,7 +48,7 @@ EXPORTED_SYMBOLS = (
     "rs_create_moving_field", "rs_field_set_time", "rs_field_time", "rs_shoot_staged", "rs_shoot_streamed",
     "rs_set_staged_state_budget", "rs_set_alloc_failure",
     "rs_light_curve_plan_create", "rs_light_curve_plan_samples", "rs_light_curve_plan_launch",
-    "rs_light_curve_plan_destroy",
+    "rs_light_curve_plan_destroy", "rs_create_field_view",
 )
 
 
@@ -128,6 +128,7 @@ def load():
         "rs_field_set_time": ([vp, dbl, vp], i32),
         "rs_field_time": ([vp, ctypes.POINTER(dbl)], i32),
         "rs_destroy_field": ([vp], i32),
+        "rs_create_field_view": ([vp, i64, i64, ctypes.POINTER(vp)], i32),
         "rs_field_info": ([vp, ctypes.POINTER(i64), ctypes.POINTER(i32)], i32),
         "rs_shoot": ([vp, gp, wp, vp, vp, vp], i32),
         "rs_shoot_rows": ([vp, gp, i64, i64, wp, vp, vp, vp], i32),
@@ -294,6 +295,13 @@ def rs_field_time(handle: int) -> float:
 
 def rs_destroy_field(handle: int) -> None:
     _check(load().rs_destroy_field(handle), "rs_destroy_field")
+
+
+def rs_create_field_view(handle: int, lens_begin: int, n_lens: int) -> int:
+    """A field of lenses [lens_begin, lens_begin + n_lens) of the field `handle` (no copy)."""
+    h = ctypes.c_void_p()
+    _check(load().rs_create_field_view(handle, int(lens_begin), int(n_lens), ctypes.byref(h)), "rs_create_field_view")
+    return h.value
 
 
 def rs_field_info(handle: int):
@@ -613,6 +621,15 @@ class Field:
 
     def info(self):
         return rs_field_info(self.handle)
+
+    def view(self, lens_begin: int, n_lens: int) -> "Field":
+        """The lenses [lens_begin, lens_begin + n_lens) of this field as a field of their own, reading
+        this field's device arrays (lens_begin a multiple of 256).  Close views before this field."""
+        v = Field.__new__(Field)
+        v.handle = rs_create_field_view(self.handle, lens_begin, n_lens)
+        v.kappa_c, v.gamma = self.kappa_c, self.gamma
+        v._parent = self  # keeps the parent alive while the view is
+        return v
 
     def shoot(self, grid, window, counts=None, out_of_window=None, stream=None, rows=None, culled=False,
               rays_shot=None):

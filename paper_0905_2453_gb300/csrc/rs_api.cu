@@ -36,6 +36,14 @@ __global__ void pack_lenses_kernel(const float* __restrict__ xy, const float* __
   }
 }
 
+// *flag |= 1 if some mass is not exactly 1 (NaN included): such a field needs the weighted kernels.
+__global__ void mass_check_kernel(const float* __restrict__ m, int64_t n, unsigned int* __restrict__ flag) {
+  bool weighted = false;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    weighted |= !(m[i] == 1.0f);
+  if (__syncthreads_or(weighted) && threadIdx.x == 0) atomicOr(flag, 1u);
+}
+
 // Moving fields: {x1, x2, v1, v2} per lens at t = 0.
 __global__ void motion_pack_kernel(const float* __restrict__ xy, const float* __restrict__ v, int64_t n,
                                    float4* __restrict__ motion) {
@@ -276,12 +284,17 @@ int rs_create_field(const float* lens_xy, const float* masses, int64_t n_lens, d
   if (n_lens >= ((int64_t)1 << 31) - rsdev::kLensPad) return fail(RS_EOVERFLOW, "n_lens must be < 2^31 - 1024");
   if (n_lens > 0 && !lens_xy) return fail(RS_EINVAL, "lens_xy is NULL");
   if (!std::isfinite(kappa_c) || !std::isfinite(gamma)) return fail(RS_EINVAL, "kappa_c and gamma must be finite");
+  // masses that are all exactly 1 select the unit-mass kernels, as NULL does (the masses are still
+  // stored, so such a field can be a lens partition next to weighted ones)
+  bool unit_masses = true;
   if (!inputs_on_device) {
     for (int64_t i = 0; i < 2 * n_lens; ++i)
       if (!finite_coord((double)lens_xy[i])) return fail(RS_EINVAL, "lens coordinate %lld not finite or beyond 1e9", (long long)i);
     if (masses)
-      for (int64_t i = 0; i < n_lens; ++i)
+      for (int64_t i = 0; i < n_lens; ++i) {
         if (!(std::isfinite(masses[i]) && masses[i] >= 0.f)) return fail(RS_EINVAL, "mass %lld not finite or negative", (long long)i);
+        unit_masses = unit_masses && masses[i] == 1.0f;
+      }
   }
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   rs_field* f = new (std::nothrow) rs_field();
@@ -339,6 +352,22 @@ int rs_create_field(const float* lens_xy, const float* masses, int64_t n_lens, d
     cleanup();
     return rc;
   }
+  if (has_mass && inputs_on_device && n_lens > 0) {
+    // unit-mass test of device inputs: the status word serves as the flag, read back and cleared
+    unsigned int weighted = 0;
+    const int blocks = (int)std::min<int64_t>((n_lens + 255) / 256, (int64_t)num_sms(f->device) * 8);
+    mass_check_kernel<<<blocks, 256, 0, s>>>(masses, n_lens, f->status);
+    if ((e = cudaGetLastError()) != cudaSuccess ||
+        (e = cudaMemcpyAsync(&weighted, f->status, sizeof(unsigned int), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(s)) != cudaSuccess ||
+        (e = cudaMemsetAsync(f->status, 0, sizeof(unsigned int), s)) != cudaSuccess) {
+      int rc = cuda_fail(e, "mass check");
+      cudaStreamSynchronize(s);
+      cleanup();
+      return rc;
+    }
+    unit_masses = weighted == 0u;
+  }
   {
     const int threads = 256;
     const int64_t want = (f->n_pad + threads - 1) / threads;
@@ -366,7 +395,7 @@ int rs_create_field(const float* lens_xy, const float* masses, int64_t n_lens, d
   f->dev.lens4 = f->lens4;
   f->dev.mass2 = has_mass ? f->mass2 : nullptr;
   f->dev.n_lens = (int32_t)n_lens;
-  f->dev.has_mass = has_mass ? 1 : 0;
+  f->dev.has_mass = (has_mass && !unit_masses) ? 1 : 0;
   f->dev.lam1 = (1.0 - kappa_c) - gamma;
   f->dev.lam2 = (1.0 - kappa_c) + gamma;
   f->dev.lamabs = std::nextafter((float)std::max(std::fabs(f->dev.lam1), std::fabs(f->dev.lam2)), INFINITY);
@@ -377,13 +406,58 @@ int rs_create_field(const float* lens_xy, const float* masses, int64_t n_lens, d
 
 int rs_destroy_field(rs_field_t f) {
   if (!f) return RS_OK;
+  if (f->views > 0) return fail(RS_EINVAL, "the field has %d live lens-range views: destroy them first", f->views);
   DeviceGuard g(f->device);
   cudaDeviceSynchronize();
   cudaFree(f->lens4);
   cudaFree(f->mass2);
   cudaFree(f->status);
   cudaFree(f->motion);
+  if (f->parent) --f->parent->views;
   delete f;
+  return RS_OK;
+}
+
+static_assert(rsdev::kRenorm % rsint::kTile == 0 && rsdev::kLensPad % rsint::kTile == 0,
+              "view ranges start on lens-tile boundaries");
+
+int rs_create_field_view(rs_field_t parent, int64_t lens_begin, int64_t n_lens, rs_field_t* out) {
+  if (!out) return fail(RS_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!parent) return fail(RS_EINVAL, "parent field is NULL");
+  if (lens_begin < 0 || n_lens < 0 || lens_begin > parent->n_lens || n_lens > parent->n_lens - lens_begin)
+    return fail(RS_EINVAL, "lens range [%lld, %lld + %lld) not within the field's %lld lenses", (long long)lens_begin,
+                (long long)lens_begin, (long long)n_lens, (long long)parent->n_lens);
+  if (lens_begin % rsdev::kRenorm != 0) return fail(RS_EINVAL, "lens_begin must be a multiple of %d", rsdev::kRenorm);
+  DeviceGuard g(parent->device);
+  rs_field* f = new (std::nothrow) rs_field();
+  if (!f) return fail(RS_ENOMEM, "host allocation failed");
+  cudaError_t e = dev_alloc(&f->status, sizeof(unsigned int));
+  if (e == cudaSuccess) e = cudaMemset(f->status, 0, sizeof(unsigned int));
+  if (e != cudaSuccess) {
+    int rc = cuda_fail(e, "view status word");
+    cudaFree(f->status);
+    delete f;
+    return rc;
+  }
+  f->device = parent->device;
+  f->n_lens = n_lens;
+  f->n_pad = (n_lens + rsdev::kLensPad - 1) / rsdev::kLensPad * rsdev::kLensPad;
+  f->kappa_c = parent->kappa_c;
+  f->gamma = parent->gamma;
+  f->lens4 = nullptr;  // not owned
+  f->mass2 = nullptr;
+  f->dev = parent->dev;
+  // full lens tiles past the range stay inside the parent's padded arrays: lens_begin is a multiple
+  // of the tile and the parent's padding reaches the next multiple of kLensPad
+  f->dev.lens4 = parent->dev.lens4 + lens_begin;
+  f->dev.mass2 = parent->dev.mass2 ? parent->dev.mass2 + lens_begin : nullptr;
+  f->dev.n_lens = (int32_t)n_lens;
+  f->dev.status = f->status;
+  f->time = parent->time;
+  f->parent = parent;
+  ++parent->views;
+  *out = f;
   return RS_OK;
 }
 

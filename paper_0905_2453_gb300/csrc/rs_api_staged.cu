@@ -26,13 +26,17 @@ int rs_shoot_staged(int n_parts, const rs_field_t* parts, const rs_ray_grid* g, 
     if (!parts[p]) return fail(RS_EINVAL, "partition %d is NULL", p);
     const rs_field* a = parts[p];
     const rs_field* b = parts[0];
-    if (a->device != b->device || a->dev.has_mass != b->dev.has_mass || a->kappa_c != b->kappa_c ||
+    if (a->device != b->device || (a->dev.mass2 != nullptr) != (b->dev.mass2 != nullptr) || a->kappa_c != b->kappa_c ||
         a->gamma != b->gamma)
-      return fail(RS_EINVAL, "partition %d differs from partition 0 in device, mass mode, kappa_c or gamma", p);
+      return fail(RS_EINVAL, "partition %d differs from partition 0 in device, stored masses, kappa_c or gamma", p);
     if (p + 1 < n_parts && a->n_lens % rsdev::kRenorm != 0)
       return fail(RS_EINVAL, "partition %d holds %lld lenses: all but the last must hold a multiple of %d", p,
                   (long long)a->n_lens, rsdev::kRenorm);
   }
+  // one kernel for every partition: the weighted one if any partition has masses other than 1 (all
+  // partitions then store masses)
+  int weighted = 0;
+  for (int p = 0; p < n_parts; ++p) weighted |= parts[p]->dev.has_mass;
   int rc;
   if ((rc = check_call(g, row_begin, row_end, w, d_counts)) != RS_OK) return rc;
   if ((rc = check_field_device(parts[0])) != RS_OK) return rc;
@@ -68,11 +72,13 @@ int rs_shoot_staged(int n_parts, const rs_field_t* parts, const rs_ray_grid* g, 
     if (g_certify) e = cudaMemsetAsync(db.rc_count, 0, sizeof(unsigned int), s);
     for (int p = 0; p < n_parts && e == cudaSuccess; ++p) {
       db.f = parts[p]->dev;
+      db.f.has_mass = weighted;
       e = rsint::launch_staged(db, state, p == 0, p == n_parts - 1, s);
     }
     if (g_certify) {
       for (int p = 0; p < n_parts && e == cudaSuccess; ++p) {
         db.f = parts[p]->dev;
+        db.f.has_mass = weighted;
         e = rsint::launch_recheck_part(db, db.rc_list, db.rc_count, db.rc_cap, ff, p == 0, rgrid, s);
       }
       if (e == cudaSuccess) e = rsint::launch_recheck_bin(db, db.rc_list, db.rc_count, db.rc_cap, ff, rgrid, s);
@@ -94,15 +100,18 @@ int rs_shoot_streamed(const float* h_lens_xy, const float* h_masses, int64_t n_l
   if (!std::isfinite(kappa_c) || !std::isfinite(gamma)) return fail(RS_EINVAL, "kappa_c and gamma must be finite");
   for (int64_t i = 0; i < 2 * n_lens; ++i)
     if (!finite_coord((double)h_lens_xy[i])) return fail(RS_EINVAL, "lens coordinate %lld not finite or beyond 1e9", (long long)i);
+  bool unit_masses = true;
   if (h_masses)
-    for (int64_t i = 0; i < n_lens; ++i)
+    for (int64_t i = 0; i < n_lens; ++i) {
       if (!(std::isfinite(h_masses[i]) && h_masses[i] >= 0.f)) return fail(RS_EINVAL, "mass %lld not finite or negative", (long long)i);
+      unit_masses = unit_masses && h_masses[i] == 1.0f;
+    }
   int rc;
   if ((rc = check_call(g, row_begin, row_end, w, d_counts)) != RS_OK) return rc;
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
-  const bool mass = h_masses != nullptr;
+  const bool mass = h_masses != nullptr && !unit_masses;  // masses all 1: the unit-mass kernels, none copied
   const int64_t P = lenses_per_pass;
   const int64_t n_parts = std::max<int64_t>(1, (n_lens + P - 1) / P);
   // a partition buffer's descriptor; the lens arrays are filled pass by pass

@@ -22,6 +22,10 @@ struct rs_field {
   // moving fields: {x1, x2, v1, v2} at t = 0 per lens, bounds of |x| and |v|, current time
   float4* motion = nullptr;
   double max_x = 0.0, max_v = 0.0, time = 0.0;
+  // lens-range views: the field a view reads (views own only their status word), and the number
+  // of live views of a field (it cannot be destroyed while any is left)
+  rs_field* parent = nullptr;
+  int views = 0;
 };
 
 namespace rshost {

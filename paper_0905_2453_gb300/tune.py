@@ -6,7 +6,10 @@ results, so the choice only affects speed.  ``autotune`` times every shape on a
 proxy run (a block of the workload's own grid rows) with CUDA events, selects the
 fastest with ``rs_set_launch_config`` and caches the choice in a JSON file keyed
 by (GPU name, library version, mass mode, lens-count bucket, row-length bucket).  This replaces the
-paper's occupancy-calculator choice of 128 or 256 threads (Section 2.2).
+paper's occupancy-calculator choice of 128 or 256 threads (Section 2.2).  Fields of more than
+``max_proxy_lenses`` lenses are timed on a view of their first lenses: past a few lens tiles the cost
+per interaction no longer depends on the lens count, and a proxy over all 1e8 lenses of a large field
+would take minutes per shape.
 """
 from __future__ import annotations
 
@@ -42,8 +45,9 @@ def _load(path):
 
 
 def autotune(field, grid, window, min_rays: float = 8e6, max_interactions: float = 3e11, reps: int = 3,
-             cache_path: str = None, force: bool = False, stream=None):
-    """Pick and set the fastest launch shape for this (field, grid); returns (block, rpt, timings_ms)."""
+             cache_path: str = None, force: bool = False, stream=None, max_proxy_lenses: int = 1 << 16):
+    """Pick and set the fastest launch shape for this (field, grid); returns (block, rpt, timings_ms)
+    with each shape's time for its own (largest) proxy block of rows."""
     cache_path = cache_path or os.environ.get("RS_TUNE_CACHE", DEFAULT_CACHE)
     n_lens, has_mass = field.info()
     key = cache_key(field, grid)
@@ -52,30 +56,59 @@ def autotune(field, grid, window, min_rays: float = 8e6, max_interactions: float
         b, r = cache[key]["block"], cache[key]["rpt"]
         rs_set_launch_config(has_mass, b, r)
         return b, r, cache[key].get("ms", {})
-    # proxy: enough rays for several full waves of the largest CTA tile on every SM (a partial wave
-    # would favour shapes with more, smaller CTAs), capped in work
+    # proxy: blocks of the grid's rows, capped in work; very large fields through a view of their
+    # first lenses.  Where the grid allows, each shape shoots k and 2k units of rows holding a whole
+    # number of waves (a multiple of 2 x SMs CTAs: whole waves at one or two resident CTAs per SM) and
+    # is rated by the difference, k units over the difference of the times: the steady state of a
+    # large grid, without the ragged end of the last CTAs that would favour shapes with more, smaller
+    # CTAs.  Small grids are timed whole, as they will run.
+    proxy = field.view(0, max_proxy_lenses) if n_lens > max_proxy_lenses else field
+    n_proxy = max(1, min(n_lens, max_proxy_lenses))
     n0, n1 = int(grid.n[0]), int(grid.n[1])
     rows = max(64, int(min_rays // max(1, n0)))
-    rows = min(rows, max(64, int(max_interactions // max(1, n0 * max(1, n_lens)))))
+    rows = min(rows, max(64, int(max_interactions // max(1, n0 * n_proxy))))
     rows = min(rows, n1)
     dev = torch.device("cuda", torch.cuda.current_device())
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
     counts = torch.zeros((int(window.npix[1]), int(window.npix[0])), dtype=torch.int32, device=dev)
     st = torch.cuda.current_stream(dev) if stream is None else stream
-    timings = {}
-    for block, rpt in rs_launch_configs():
-        rs_set_launch_config(has_mass, block, rpt)
-        rs_shoot_rows(field.handle, grid, 0, rows, window, counts, None, st)
+
+    def timed(nrows):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(st)
         for _ in range(reps):
-            rs_shoot_rows(field.handle, grid, 0, rows, window, counts, None, st)
+            rs_shoot_rows(proxy.handle, grid, 0, nrows, window, counts, None, st)
         e1.record(st)
         e1.synchronize()
-        timings[f"{block}x{rpt}"] = e0.elapsed_time(e1) / reps
-    best = min(timings, key=timings.get)
+        return e0.elapsed_time(e1) / reps
+
+    timings, rates, shape_rows = {}, {}, {}
+    try:
+        for block, rpt in rs_launch_configs():
+            warps, seg = block // 32, 32 * rpt
+            cpr = -(-n0 // seg)  # CTAs per group of `warps` rows
+            unit = (2 * sms) // math.gcd(2 * sms, cpr) * warps
+            k = min(max(1, round(rows / unit)), n1 // (2 * unit))
+            name = f"{block}x{rpt}"
+            rs_set_launch_config(has_mass, block, rpt)
+            if rows < n1 and k >= 1 and unit * n0 * n_proxy <= 4 * max_interactions:
+                rs_shoot_rows(proxy.handle, grid, 0, k * unit, window, counts, None, st)  # warm-up
+                t1, t2 = timed(k * unit), timed(2 * k * unit)
+                timings[name], shape_rows[name] = t2, [k * unit, 2 * k * unit]
+                per = k * unit * n0 * n_proxy
+                rates[name] = per / max(t2 - t1, 1e-6) * 1e3 if t2 > t1 else 2 * per / max(t2, 1e-6) * 1e3
+            else:
+                rs_shoot_rows(proxy.handle, grid, 0, rows, window, counts, None, st)  # warm-up
+                timings[name], shape_rows[name] = timed(rows), [rows]
+                rates[name] = rows * n0 * n_proxy / max(timings[name], 1e-6) * 1e3
+    finally:
+        if proxy is not field:
+            proxy.close()
+    best = max(rates, key=rates.get)
     b, r = (int(t) for t in best.split("x"))
     rs_set_launch_config(has_mass, b, r)
-    cache[key] = {"block": b, "rpt": r, "ms": timings, "proxy_rows": rows}
+    cache[key] = {"block": b, "rpt": r, "ms": timings, "rows": shape_rows, "interactions_per_s": rates,
+                  "proxy_lenses": n_proxy}
     try:
         os.makedirs(os.path.dirname(cache_path), exist_ok=True)
         tmp = cache_path + f".tmp{os.getpid()}"

@@ -226,3 +226,5 @@ def test_widening_entry_points_validate_before_cuda(rs):
     assert lib.rs_set_alloc_failure(-2) == rs.RS_EINVAL
     assert lib.rs_set_alloc_failure(-1) == rs.RS_OK
     assert lib.rs_set_staged_state_budget(1000) == rs.RS_EINVAL
+    assert lib.rs_create_field_view(None, 0, 0, ctypes.byref(h)) == rs.RS_EINVAL
+    assert lib.rs_create_field_view(None, 0, 0, None) == rs.RS_EINVAL
