@@ -135,7 +135,7 @@ int rs_create_field_view(rs_field_t parent, int64_t lens_begin, int64_t n_lens, 
  *   work on other streams must be ordered by the caller.  Batches that include the field read its
  *   lenses at launch, so a planned batch of moving fields can be replayed after each time step.
  *   Errors: RS_EINVAL (not a moving field, t not finite, or |x| + |v| |t| beyond 1e9).
- * rs_field_time -- the field's current time.
+ * rs_field_time -- the field's current time (a lens-range view: its parent's).
  */
 int rs_create_moving_field(const float* lens_xy, const float* vel_xy, const float* masses, int64_t n_lens,
                            double kappa_c, double gamma, int inputs_on_device, void* stream, rs_field_t* out);

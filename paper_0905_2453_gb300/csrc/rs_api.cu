@@ -454,7 +454,6 @@ int rs_create_field_view(rs_field_t parent, int64_t lens_begin, int64_t n_lens, 
   f->dev.mass2 = parent->dev.mass2 ? parent->dev.mass2 + lens_begin : nullptr;
   f->dev.n_lens = (int32_t)n_lens;
   f->dev.status = f->status;
-  f->time = parent->time;
   f->parent = parent;
   ++parent->views;
   *out = f;
@@ -544,7 +543,7 @@ int rs_field_set_time(rs_field_t f, double t, void* stream) {
 
 int rs_field_time(rs_field_t f, double* t) {
   if (!f || !t) return fail(RS_EINVAL, "NULL argument");
-  *t = f->time;
+  *t = f->parent ? f->parent->time : f->time;  // a view moves with its parent
   return RS_OK;
 }
 

@@ -101,6 +101,7 @@ def test_view_validation_and_moving_parent():
             with pytest.raises(m.RSError):
                 v.set_time(1.0)                      # views follow their parent's time
             parent.set_time(3.0)
+            assert v.time == 3.0
             moved = oracle.lens_positions(spec.lens_xy, vel, 3.0)
             sub = ri.Field("vm", moved[256:], None, spec.kappa_c, spec.gamma, spec.grid, spec.window)
             got = _shoot(m, v, spec)
