@@ -5,9 +5,9 @@
 // so the warp's loads of neighbouring pixels fall in the same L1 lines and every per-sample
 // float64 step (position, box, quotient) is paid once per thread, not once per pixel.  A thread
 // walks the rows of the box that bounds its profile's support and, per row, the chord of the
-// support (half a pixel of margin each side).  With E = (di)^2 a0 + (dj)^2 a1 the float32 exponent of
+// support (a margin of ~2^-10 pixel each side).  With E = (di)^2 a0 + (dj)^2 a1 the float32 exponent of
 // the pixel offset (di, dj) in pixel units, the chord's interior (E below the cut by more than a
-// guard band, half a pixel of margin) is summed without tests; at the rim membership is decided from
+// guard band, same margin) is summed without tests; at the rim membership is decided from
 // E, and pixels whose E lies within the guard band repeat the float64 test
 // ((lo + (i + 0.5) pix) - y)^2 + (...)^2 <= cut^2 (no fused multiply-add), so the covered pixel set
 // is exactly that of a float64 evaluation.
@@ -65,11 +65,19 @@ __device__ __forceinline__ void rim_pixel(const LcTrack& T, int64_t k, int i, in
   }
 }
 
+// Gaussian weights are separable: 2^-(ex + ey) = 2^-ex 2^-ey.  A thread whose support box spans at most
+// kLcCols columns keeps the column factors 2^-ex of its sample in shared memory (thread-private slots,
+// conflict-free: slot c of thread t at c * 256 + t) and the untested chord interiors cost a load and a
+// fused multiply-add per pixel; each row's interior sums are scaled by 2^-ey once.
+constexpr int kLcThreads = 256;
+constexpr int kLcCols = 32;
+
 template <int PROFILE>
-__global__ void __launch_bounds__(256) light_curve_kernel(const LcTrack* __restrict__ tracks, int n_tracks,
-                                                          int64_t n_samples, double cut2, float ecut,
-                                                          double* __restrict__ mu_out,
-                                                          double* __restrict__ dm_out) {
+__global__ void __launch_bounds__(kLcThreads) light_curve_kernel(const LcTrack* __restrict__ tracks, int n_tracks,
+                                                                 int64_t n_samples, double cut2, float ecut,
+                                                                 double* __restrict__ mu_out,
+                                                                 double* __restrict__ dm_out) {
+  __shared__ float s_wx[PROFILE == 0 ? kLcCols * kLcThreads : 1];
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < n_samples; g += stride) {
     // the track holding sample g: the last one whose first output position is <= g
@@ -94,21 +102,31 @@ __global__ void __launch_bounds__(256) light_curve_kernel(const LcTrack* __restr
       const int j_lo = max(jt + (int)ceilf(fy - rpy) - 1, 0), j_hi = min(jt + (int)floorf(fy + rpy) + 1, T.np1 - 1);
       const float a0 = T.a0, a1 = T.a1, band = T.band;
       const float lim_hi = ecut + band, lim_lo = ecut - band;
+      const bool sep = PROFILE == 0 && i_hi - i_lo < kLcCols;
+      if (sep) {
+        for (int i = i_lo; i <= i_hi; ++i) {
+          const float dxp = __fsub_rn((float)(i - it), fx);
+          s_wx[(i - i_lo) * kLcThreads + threadIdx.x] = ex2_neg(__fmul_rn(__fmul_rn(dxp, dxp), a0));
+        }
+      }
       for (int j = j_lo; j <= j_hi; ++j) {
         const float dyp = __fsub_rn((float)(j - jt), fy);
         const float ey = __fmul_rn(__fmul_rn(dyp, dyp), a1);
         const float rem_hi = lim_hi - ey;
         if (!(rem_hi >= 0.f)) continue;
-        // chord of the support on this row (E <= cut + band), half a pixel of margin each side; float32
-        // errors of the half-chord are ~2^-24 of the support radius, far inside the guard band
-        const float h_out = sqrt_approx(rem_hi * T.inv_a0) + 0.5f;
+        // chord of the support on this row (E <= cut + band) with a margin of 2^-10 + 2^-16 h pixels each
+        // side: the float32 half-chord h is within a few 2^-24 h of its exact value (the guard band of the
+        // exponent already covers the rounding of ey, a0 and the pixel offsets)
+        const float hq_out = sqrt_approx(rem_hi * T.inv_a0);
+        const float h_out = hq_out + fmaf(hq_out, 0x1p-16f, 0x1p-10f);
         const int c_lo = max(it + (int)ceilf(fx - h_out), i_lo);
         const int c_hi = min(it + (int)floorf(fx + h_out), i_hi);
-        // interior of the chord (E <= cut - band, half a pixel of margin): inside for certain, no test
+        // interior of the chord (E <= cut - band, same margin): inside for certain, no test
         int n_lo = c_hi + 1, n_hi = c_hi;
         const float rem_lo = lim_lo - ey;
         if (rem_lo > 0.f) {
-          const float h_in = sqrt_approx(rem_lo * T.inv_a0) - 0.5f;
+          const float hq_in = sqrt_approx(rem_lo * T.inv_a0);
+          const float h_in = hq_in - fmaf(hq_in, 0x1p-16f, 0x1p-10f);
           if (h_in >= 0.f) {
             n_lo = max(it + (int)ceilf(fx - h_in), c_lo);
             n_hi = min(it + (int)floorf(fx + h_in), c_hi);
@@ -122,7 +140,21 @@ __global__ void __launch_bounds__(256) light_curve_kernel(const LcTrack* __restr
         float rw = 0.f, rm = 0.f;  // this row's partial sums (at most 2 R / pix + 3 terms)
         // rim pixels on the low side: float32 test, float64 test inside the guard band
         for (int i = c_lo; i < n_lo; ++i) rim_pixel<PROFILE>(T, k, i, j, it, fx, a0, ey, ecut, band, cut2, row, rw, rm);
-        if (PROFILE == 0) {
+        if (PROFILE == 0 && sep) {
+          float iw = 0.f, im = 0.f;
+          const float* wx = s_wx + threadIdx.x - i_lo * kLcThreads;
+#pragma unroll 4
+          for (int i = n_lo; i <= n_hi; ++i) {
+            const float w = wx[i * kLcThreads];
+            iw = __fadd_rn(iw, w);
+            im = fmaf(w, __ldg(row + i), im);
+          }
+          if (n_lo <= n_hi) {
+            const float wy = ex2_neg(ey);
+            rw = fmaf(wy, iw, rw);
+            rm = fmaf(wy, im, rm);
+          }
+        } else if (PROFILE == 0) {
           float kx = (float)(n_lo - it);
 #pragma unroll 4
           for (int i = n_lo; i <= n_hi; ++i) {
@@ -166,9 +198,9 @@ namespace rsint {
 cudaError_t launch_light_curves(int profile, const LcTrack* tracks, int n_tracks, int64_t n_samples, double cut2,
                                 float ecut, double* mu_out, double* dm_out, int grid, cudaStream_t s) {
   if (profile == 0)
-    light_curve_kernel<0><<<grid, 256, 0, s>>>(tracks, n_tracks, n_samples, cut2, ecut, mu_out, dm_out);
+    light_curve_kernel<0><<<grid, kLcThreads, 0, s>>>(tracks, n_tracks, n_samples, cut2, ecut, mu_out, dm_out);
   else
-    light_curve_kernel<1><<<grid, 256, 0, s>>>(tracks, n_tracks, n_samples, cut2, ecut, mu_out, dm_out);
+    light_curve_kernel<1><<<grid, kLcThreads, 0, s>>>(tracks, n_tracks, n_samples, cut2, ecut, mu_out, dm_out);
   return cudaGetLastError();
 }
 

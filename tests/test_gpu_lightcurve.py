@@ -8,7 +8,10 @@ weight error delta_p changes the weighted mean by at most sum_p w_p delta_p |mu_
 units known to u (1 + |offset|), a = pix^2 / (2 s^2); the float64 sample position adds ~2^-53 of
 its pixel index, negligible for these maps), the scaling by log2(e) one more rounding of E, the
 hardware base-2 exponential at most 2^-21 relative: delta_p = u (8 E + 8 sqrt(a E) + 16) covers
-these with room.  Both sums are positive; each row of the support (at most n_r = 2 R / pix + 3
+these with room.  Where the device takes the weight as the product of the column and row factors
+2^-ex 2^-ey (separable Gaussian, chord interiors), each factor's exponent carries the same kinds of
+rounding over a smaller magnitude and the two exponentials stay within 2^-20 = 16 u together; the
+product's own rounding enters the row sum (one more term in its budget).  Both sums are positive; each row of the support (at most n_r = 2 R / pix + 3
 pixels) is summed in float32 with fused multiply-adds, relative error <= (n_r + 1) u, and the rows
 are folded into compensated pairs whose float-float quotient adds ~2u: (2 n_r + 10) u |mu| covers
 the sums.  The tests allow twice the resulting first-order bound.

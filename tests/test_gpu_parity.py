@@ -203,6 +203,36 @@ def test_batch_equals_plain_launches_bitwise():
             fl.close()
 
 
+def test_batch_workload_full_size_vs_oracle():
+    """The 64-field batch at full size, one persistent launch as the benchmark times it: every field's
+    counts conserve its rays and equal its plain launch bit for bit, and the eight smallest fields
+    (1.3e8 - 3.3e8 interactions each) equal the oracle's maps exactly (certified binning)."""
+    m = rs()
+    specs = ri.batch_fields(64)
+    fields = [m.Field.from_spec(s) for s in specs]
+    try:
+        b = m.Batch(fields, [s.grid for s in specs], [s.window for s in specs])
+        try:
+            b.launch()
+            torch.cuda.synchronize()
+            got = [(b.counts[k].cpu().numpy().view(np.uint32).copy(), int(b.out_of_window[k].item()))
+                   for k in range(len(specs))]
+        finally:
+            b.close()
+        assert all(f.status() == m.RS_OK for f in fields)
+    finally:
+        for fl in fields:
+            fl.close()
+    for k, s in enumerate(specs):
+        c, o = got[k]
+        assert int(c.sum(dtype=np.int64)) + o == s.grid.n_rays, k
+        ref, oref = shoot_gpu(s)
+        assert np.array_equal(c, ref) and o == oref, k
+    for k in sorted(range(len(specs)), key=lambda k: specs[k].interactions)[:8]:
+        ref, oref = oracle.shoot_field(specs[k])
+        assert np.array_equal(got[k][0], ref) and got[k][1] == oref, k
+
+
 def test_n1e4_full_size_sampled_rays():
     """1e4 lenses on the 4096^2 grid in the benchmark's launch shape: 20000 sampled rays vs the oracle."""
     f = ri.n1e4_field()
