@@ -28,7 +28,7 @@ __device__ __forceinline__ void acc_two_sum(float& s, float& c, float x) {
 }
 
 // sqrt(x) for x >= 0 from the hardware reciprocal square root (a few ulp; used for chord bounds
-// that carry half a pixel of margin)
+// that carry a margin of 2^-10 + 2^-16 h pixels, h the half-chord)
 __device__ __forceinline__ float sqrt_approx(float x) { return x > 0.f ? x * rsqrtf(x) : 0.f; }
 
 __device__ __forceinline__ float ex2_neg(float e) {
