@@ -222,12 +222,15 @@ constexpr float kSigmaScale = 5.9604645e-08f * 8.0f * kSigmaSafety;
 // upper-bounds |alpha| and tracks sum_i |t_i| for a far field of many lenses.
 constexpr float kSystematicScale = 2.0f * 5.9604645e-08f;
 
+constexpr int kMaxSeg = 256;  // grid columns of one CTA tile: 32 lanes x at most 8 rays per thread
+
 template <int TILE, int ROWS = 1>
 struct __align__(16) LensSmem {
   float4 lens4[2][TILE];     // double-buffered lens tiles {x1, x1, x2, x2}
   float2 mass2[2][TILE];     // {m, m}
   float4 rowtab[ROWS][TILE]; // per CTA row r and lens l of the current tile: {d2, d2, d2^2, d2^2}
   float x2row[ROWS];         // x2 of the CTA's rows
+  float x1col[kMaxSeg];      // x1 of the CTA's columns (shoot_tile)
   uint64_t bar[2];
 };
 
@@ -718,25 +721,38 @@ template <int WARPS, int RPT, int TILE, bool MASS>
 __device__ __forceinline__ bool shoot_tile(const ShootDesc& d, int64_t tile, LensSmem<TILE, WARPS>& sm,
                                            PipeState& ps) {
   constexpr int SEG = 32 * RPT;
+  static_assert(SEG <= kMaxSeg, "tile columns fit the shared coordinate row");
   const int64_t ncol = (d.n0 + SEG - 1) / SEG;
   const int64_t trow = tile / ncol;
   const int64_t tcol = tile - trow * ncol;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t jrel = trow * WARPS + warp;
   const bool row_ok = jrel < d.n_rows;
-  const int64_t j = d.j_begin + (row_ok ? jrel : d.n_rows - 1);
-  const float x2r = ray_coord(j, d.sp1, d.or1);
+  // Ray coordinates (float64 fma rounded to float, as the header defines them) of the tile's SEG
+  // columns and WARPS rows, each formed once per CTA rather than once per warp: the float64 pipe is
+  // narrow, and on small fields these conversions would otherwise delay every tile's start.
+  for (int c = threadIdx.x; c < SEG + WARPS; c += WARPS * 32) {
+    if (c < SEG) {
+      int64_t i = tcol * SEG + c;
+      if (i >= d.n0) i = d.n0 - 1;
+      sm.x1col[c] = ray_coord(i, d.sp0, d.or0);
+    } else {
+      int64_t jr = trow * WARPS + (c - SEG);
+      if (jr >= d.n_rows) jr = d.n_rows - 1;
+      sm.x2row[c - SEG] = ray_coord(d.j_begin + jr, d.sp1, d.or1);  // also read by build_row_table
+    }
+  }
+  __syncthreads();
+  const float x2r = sm.x2row[warp];
   float x1[RPT], x2[RPT];
   bool valid[RPT];
 #pragma unroll
   for (int k = 0; k < RPT; ++k) {
-    int64_t i = tcol * SEG + lane + 32 * k;
+    const int64_t i = tcol * SEG + lane + 32 * k;
     valid[k] = row_ok && i < d.n0;
-    if (i >= d.n0) i = d.n0 - 1;
-    x1[k] = ray_coord(i, d.sp0, d.or0);
+    x1[k] = sm.x1col[lane + 32 * k];
     x2[k] = x2r;
   }
-  if (lane == 0) sm.x2row[warp] = x2r;  // read by build_row_table after the first tile barrier
   float a1h[RPT], a1l[RPT], a2h[RPT], a2l[RPT], sig[RPT];
   if (!deflect_pairs<RPT, TILE, MASS, true, WARPS>(d.f, x1, x2, a1h, a1l, a2h, a2l, sig, sm, ps)) return false;
   bin_rays<RPT, 32>(d, x1, x2, a1h, a1l, a2h, a2l, sig, valid, jrel, tcol * SEG + lane, lane);
