@@ -20,7 +20,6 @@ from __future__ import annotations
 import argparse
 import hashlib
 import json
-import math
 import os
 import statistics
 import subprocess
@@ -854,9 +853,8 @@ def run_configs(rs, torch, device, stream, names, cpu=True, full_limit=2e12, max
             entry.update({"sample": "whole grid", "rows": [0, n1], "ms": ms, "interactions_per_s": rate,
                           "pct_fp32_peak_2070mhz": pct(rate)})
         else:
-            warps, seg = b // 32, 32 * r
-            cpr = -(-n0 // seg)                             # CTAs per group of `warps` rows
-            unit = (2 * sms) // math.gcd(2 * sms, cpr) * warps
+            warps, cpr = b // 32, -(-n0 // (32 * r))       # rows and CTAs per row group
+            unit = tune.wave_rows(n0, b, r, sms)
             per_unit = unit * n0 * n_lens
             k = max(1, min(n1 // (2 * unit), int(max_sample // (2 * per_unit))))
             blocks = []

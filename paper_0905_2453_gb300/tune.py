@@ -36,6 +36,15 @@ def cache_key(field, grid) -> str:
             f"|n0=2^{_bucket(int(grid.n[0]))}")
 
 
+def wave_rows(n0: int, block: int, rpt: int, sms: int) -> int:
+    """The smallest number of grid rows whose CTAs (of `block` threads x `rpt` rays per thread, one warp per
+    row and 32 x rpt columns per CTA) fill whole waves of 2 x sms CTAs: whole waves at one or two resident
+    CTAs per SM (every launch shape of the library)."""
+    warps, seg = block // 32, 32 * rpt
+    cpr = -(-int(n0) // seg)  # CTAs per group of `warps` rows
+    return (2 * sms) // math.gcd(2 * sms, cpr) * warps
+
+
 def _load(path):
     try:
         with open(path) as fh:
@@ -85,9 +94,7 @@ def autotune(field, grid, window, min_rays: float = 8e6, max_interactions: float
     timings, rates, shape_rows = {}, {}, {}
     try:
         for block, rpt in rs_launch_configs():
-            warps, seg = block // 32, 32 * rpt
-            cpr = -(-n0 // seg)  # CTAs per group of `warps` rows
-            unit = (2 * sms) // math.gcd(2 * sms, cpr) * warps
+            unit = wave_rows(n0, block, rpt, sms)
             k = min(max(1, round(rows / unit)), n1 // (2 * unit))
             name = f"{block}x{rpt}"
             rs_set_launch_config(has_mass, block, rpt)
