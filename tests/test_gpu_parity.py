@@ -147,8 +147,9 @@ def test_row_sharding_accumulates_bitwise():
 
 
 def test_ragged_sizes_and_edge_cases():
-    """Lens counts around the group (32) and tile (512) sizes, one ray, rays off the tile size."""
-    for n_lens in (1, 31, 32, 33, 511, 512, 513, 1025):
+    """Lens counts around the float32 group (64 lenses), the lens pair, the lens tile and renormalisation
+    period (256) and the padding (1024), one ray, rays off the tile size."""
+    for n_lens in (1, 2, 3, 63, 64, 65, 127, 255, 256, 257, 511, 513, 1023, 1024, 1025, 1279):
         f = ri.disc_field(f"rag{n_lens}", n_lens, 0.3, 0.0, 0.1, 37, 16, seed=n_lens, mass="salpeter")
         ij = all_rays(f.grid)
         _check_per_ray(f, ij, f"ragged N={n_lens}")
