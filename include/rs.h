@@ -46,7 +46,7 @@
  *   - Binning (the definition, float64): u_k = (y_k - lo_k) * (npix_k / (hi_k - lo_k));
  *     a ray is in the window iff 0 <= u_k < npix_k on both axes (NaN fails),
  *     pixel p_k = floor(u_k).  With certified binning (below) the counts follow
- *     this definition applied to the exact deflection.  Counts are uint32, row-major [p2][p1].  A ray that
+ *     this definition applied to the exact deflection (within the scope stated there).  Counts are uint32, row-major [p2][p1].  A ray that
  *     hits a lens exactly has a non-finite deflection and is out of window.
  */
 #ifndef RS_H
@@ -253,7 +253,10 @@ int rs_trace_certified(rs_field_t f, const rs_ray_grid* g, const int64_t* d_ray_
  * approximate reciprocal).  A ray whose source position lies within that band of a pixel or window edge is
  * not binned by the float32 result but re-evaluated with rs_trace_certified's arithmetic and
  * binned from that; the maps then agree with a float64 evaluation except for rays within ~1e-12
- * of an edge.  rs_shoot allocates the list of such rays stream-ordered (cudaMallocAsync,
+ * of an edge and rays whose float32 error exceeds the band: the band is an estimate from the group
+ * partials, and a ray between near lenses whose terms cancel inside one group can exceed it (seen
+ * on fields of a few lenses; on fields of 100 lenses and more every checked ray stayed inside).
+ * rs_shoot allocates the list of such rays stream-ordered (cudaMallocAsync,
  * capacity max(4096, rays/32), at most 2^24 entries); rays beyond the capacity keep their
  * float32 decision and the field's status records RS_EOVERFLOW (rs_field_status).  Batches own their list.
  * rs_set_certified_binning(0) turns it off for calls (and batches planned) afterwards.
