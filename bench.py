@@ -1,19 +1,22 @@
 #!/usr/bin/env python3
 """Benchmark of the GB300 inverse ray-shooting path (one JSON line on stdout).
 
-Workload (default): 1e4 equal-mass point lenses uniform in a disc (kappa_* = 0.45,
-kappa_c = 0, gamma = 0.4), a 4096 x 4096 regular ray grid, a 1024 x 1024 uint32
-source map.  One step = one magnification map: zero the counts, shoot every ray
-(deflection over all lenses, lens map, binning: one kernel), normalise to mu
-(one kernel).  Metric: lens-ray interactions per second (rays x lenses / time),
-and the same as a fraction of the FP32 peak with the paper's 10 flops per
-interaction.
+Workload (default, the largest single-GPU configuration): 1e8 equal-mass point lenses
+(float32 masses of 1) uniform in a disc (kappa_* = 0.5, kappa_c = 0, gamma = 0.5), an
+8192 x 8192 regular ray grid, a 4096 x 4096 uint32 source map.  A whole map takes about
+20 minutes, so one step shoots a central block of grid rows that fills whole waves of
+CTAs: zero the counts, shoot the block (deflection over all 1e8 lenses, lens map,
+binning: one kernel, plus the certified re-evaluation), normalise to mu (one kernel).
+Metric: lens-ray interactions per second (rays x lenses / time), and the same as a
+fraction of the FP32 peak with the paper's 10 flops per interaction.  The other
+configurations (100, 1e4 and 1e6 lenses, the 64-field batch) are reported as
+sub-objects with their own roofline.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload NAME]
 
---impl reference times the FP64 CPU oracle (the reference arm) on bounded row
-samples of the same workload.  Under torchrun every rank shoots its own lens
-realisation of the workload (weak scaling, no collective on the data path).
+--impl reference times the FP64 CPU oracle (the reference arm) on bounded samples of
+the same workload.  Under torchrun every rank shoots its own lens realisation of the
+workload (weak scaling, no collective on the data path).
 """
 from __future__ import annotations
 
@@ -208,33 +211,49 @@ def oracle_rate(spec, target_s: float, max_rows=None):
 
 
 def run_reference(args):
+    """The reference arm: the FP64 oracle on the host cores, each step a bounded sample of the workload
+    (central grid rows when a row is cheap enough, else random rays of the grid, new ones every step)."""
     world, rank, _ = dist_env()
     if rank != 0:
         return
+    import oracle
+    oracle.build()
     spec = workload(args.workload, seed=0)
     per_step = min(1.0, 150.0 / max(1, args.steps + args.warmup))
-    calib = oracle_rate(spec, per_step)
-    rows = calib["rows"]
-    import oracle
-    for _ in range(args.warmup):
-        oracle.shoot_field(spec, rows=(0, rows))
+    n0, n1 = int(spec.grid.n[0]), int(spec.grid.n[1])
+    if n0 * spec.n_lens <= 2.5e8 * per_step / 4:
+        calib = oracle_rate(spec, per_step)
+        rows, cores = calib["rows"], calib["cores"]
+
+        def one(k):
+            j0 = (k * rows) % max(1, n1 - rows + 1)
+            oracle.shoot_field(spec, rows=(j0, j0 + rows))
+            return rows * n0
+
+        sample = f"{rows} grid rows ({rows * n0} rays) x {spec.n_lens} lenses per step"
+    else:
+        cal = oracle_trace_rate(spec, 8, seed=5)
+        n_rays, cores = max(8, int(per_step / max(cal["seconds"] / 8, 1e-9))), cal["cores"]
+
+        def one(k):
+            oracle.trace_field(spec, ri.sample_rays(spec.grid, n_rays, seed=1000 + k))
+            return n_rays
+
+        sample = f"{n_rays} random rays of the {n0} x {n1} grid x {spec.n_lens} lenses per step (new rays each step)"
+    for k in range(args.warmup):
+        one(-1 - k)
     t0 = time.perf_counter()
-    for k in range(args.steps):
-        j0 = (k * rows) % max(1, int(spec.grid.n[1]) - rows + 1)
-        oracle.shoot_field(spec, rows=(j0, j0 + rows))
+    rays = sum(one(k) for k in range(args.steps))
     dt = time.perf_counter() - t0
-    inter = rows * int(spec.grid.n[0]) * spec.n_lens * args.steps
-    value = inter / dt
-    sample = (f"{rows} grid rows ({rows * int(spec.grid.n[0])} rays) x {spec.n_lens} lenses per step, "
-              f"FP64 oracle, OpenMP over rays")
+    value = rays * spec.n_lens / dt
     cfg = workload_config(spec, args.workload)
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "interactions/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": cfg,
-        "cpu_baseline": {"value": value, "unit": "interactions/s", "cores": calib["cores"], "kind": "oracle",
-                         "sample": sample},
+        "cpu_baseline": {"value": value, "unit": "interactions/s", "cores": cores, "kind": "oracle",
+                         "sample": sample + ", FP64 oracle, OpenMP over rays"},
         "e2e": {"value": value, "unit": "interactions/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
         "gflops_equiv": value * FLOPS_PER_INTERACTION / 1e9,
     }
@@ -242,6 +261,72 @@ def run_reference(args):
 
 
 # --------------------------------------------------------------------------------------------- our arm
+
+FULL_LIMIT = 2e12  # grids of at most this many interactions are shot whole per step
+
+
+def headline_rows(rs, spec, field, sms, stream, launch_shape=None):
+    """Rows [r0, r1) one step shoots, the launch shape and a description.
+
+    Grids of at most FULL_LIMIT interactions are shot whole.  Larger ones are shot as the central block of
+    the fewest rows that fill whole waves of CTAs (every CTA of the block runs at once, so the block's rate
+    is the full grid's steady state); the launch shape is the tuned best or, among the shapes within 1 % of
+    its rate, the one whose whole wave takes the fewest rows (every shape gives bitwise the same counts)."""
+    from paper_0905_2453_gb300 import tune
+    n_lens, weighted = field.info()
+    if launch_shape:
+        b, r = (int(v) for v in launch_shape.split("x"))
+        rs.rs_set_launch_config(weighted, b, r)
+        rates = {}
+    else:
+        b, r, _ = tune.autotune(field, spec.grid, spec.window, stream=stream)
+        rates = tune.shape_rates(field, spec.grid)
+    n0, n1 = int(spec.grid.n[0]), int(spec.grid.n[1])
+    if spec.interactions <= FULL_LIMIT:
+        return 0, n1, (b, r), "whole grid"
+
+    def unit_of(shape):
+        occ = rs.rs_launch_occupancy(weighted, *shape)
+        return tune.wave_rows(n0, shape[0], shape[1], sms, occ), occ
+
+    best = rates.get(f"{b}x{r}")
+    cands = [(b, r)]
+    if best:
+        cands += [tuple(int(v) for v in k.split("x")) for k, v in rates.items() if v >= 0.99 * best]
+    b, r = min(cands, key=lambda sh: (unit_of(sh)[0], cands.index(sh)))
+    rs.rs_set_launch_config(weighted, b, r)
+    unit, occ = unit_of((b, r))
+    warps = b // 32
+    r0 = (n1 - unit) // 2 // warps * warps
+    ctas = -(-n0 // (32 * r)) * (unit // warps)
+    note = (f"central rows [{r0}, {r0 + unit}) of the {n0} x {n1} grid: {ctas} CTAs of {b} threads = "
+            f"{ctas // (occ * sms)} whole wave(s) of {occ} CTAs x {sms} SMs")
+    return r0, r0 + unit, (b, r), note
+
+
+def oracle_sample_rate(spec, target_s: float):
+    """The FP64 oracle on a bounded sample of the workload: whole central grid rows when one row takes at
+    most target_s / 4, else random rays of the grid (per-ray evaluation), sized to about target_s."""
+    one_row = int(spec.grid.n[0]) * spec.n_lens
+    if one_row <= 2.5e8 * target_s / 4:
+        r = oracle_rate(spec, target_s)
+        r["sample"] = (f"{r['rows']} central grid rows ({r['rays']} rays) x {spec.n_lens} lenses, "
+                       f"{r['seconds']:.1f} s, FP64 OpenMP over rays")
+        return r
+    cal = oracle_trace_rate(spec, 16, seed=5)
+    n = max(16, int(target_s / max(cal["seconds"] / 16, 1e-9)))
+    r = oracle_trace_rate(spec, n)
+    r["sample"] = (f"{n} random rays of the {spec.grid.n[0]} x {spec.grid.n[1]} grid x {spec.n_lens} lenses, "
+                   f"{r['seconds']:.1f} s, FP64 OpenMP over rays")
+    return r
+
+
+def roofline_entry(interactions, seconds, sms, max_mhz, traffic=None):
+    peak = fp32_peak_tflops(sms, max_mhz)
+    achieved = interactions * FLOPS_PER_INTERACTION / seconds / 1e12
+    return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "traffic": traffic}
+
 
 def run_ours(args):
     import torch
@@ -272,23 +357,23 @@ def run_ours(args):
     spec = workload(args.workload, seed=rank)
     stream = torch.cuda.current_stream(device)
     field = rs.Field.from_spec(spec, stream)
-    from paper_0905_2453_gb300 import tune
-    if args.launch_shape:
-        b_, r_ = (int(v) for v in args.launch_shape.split("x"))
-        rs.rs_set_launch_config(field.info()[1], b_, r_)
-        shape = (b_, r_, {})
-    else:
-        shape = tune.autotune(field, spec.grid, spec.window, stream=stream)
+    sms, max_mhz = peaks(local)
+    r0, r1, shape, rows_note = headline_rows(rs, spec, field, sms, stream, args.launch_shape)
     npix = (int(spec.window.npix[1]), int(spec.window.npix[0]))
     counts = torch.zeros(npix, dtype=torch.int32, device=device)
     oow = torch.zeros(1, dtype=torch.int64, device=device)
     mu = torch.empty(npix, dtype=torch.float32, device=device)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=device)
+    inter_step = (r1 - r0) * int(spec.grid.n[0]) * spec.n_lens
+    rays_step = (r1 - r0) * int(spec.grid.n[0])
+
+    def shoot():
+        rs.rs_shoot_rows(field.handle, spec.grid, r0, r1, spec.window, counts, oow, stream)
 
     def step():
         counts.zero_()
         oow.zero_()
-        rs.rs_shoot(field.handle, spec.grid, spec.window, counts, oow, stream)
+        shoot()
         rs.rs_magnification(counts, spec.grid, spec.window, mu, stream)
 
     for _ in range(args.warmup):
@@ -307,7 +392,7 @@ def run_ours(args):
         counts.zero_()
         oow.zero_()
         e[1].record(stream)
-        rs.rs_shoot(field.handle, spec.grid, spec.window, counts, oow, stream)
+        shoot()
         e[2].record(stream)
         rs.rs_magnification(counts, spec.grid, spec.window, mu, stream)
         e[3].record(stream)
@@ -322,7 +407,7 @@ def run_ours(args):
     status = field.status()
     if status != rs.RS_OK:
         raise SystemExit(f"device reported status {status}")
-    inter_step = spec.interactions
+    conserved = int(counts.sum(dtype=torch.int64).item()) + int(oow.item()) == rays_step
     value = inter_step * args.steps * world / total_s
 
     # ---------------- end to end through the public API with host buffers
@@ -337,7 +422,7 @@ def run_ours(args):
             f = rs.Field(h_xy.numpy(), None if h_m is None else h_m.numpy(), spec.kappa_c, spec.gamma, stream)
             counts.zero_()
             oow.zero_()
-            rs.rs_shoot(f.handle, spec.grid, spec.window, counts, oow, stream)
+            rs.rs_shoot_rows(f.handle, spec.grid, r0, r1, spec.window, counts, oow, stream)
             rs.rs_magnification(counts, spec.grid, spec.window, mu, stream)
             h_mu.copy_(mu, non_blocking=True)
             h_oow.copy_(oow, non_blocking=True)
@@ -345,7 +430,7 @@ def run_ours(args):
             f.close()
 
         e2e_step()
-        n_e2e = max(3, min(args.steps, 20))
+        n_e2e = max(3, min(args.steps, 20 if inter_step <= FULL_LIMIT else 3))
         barrier()
         torch.cuda.synchronize(device)
         t0 = time.perf_counter()
@@ -356,7 +441,20 @@ def run_ours(args):
         d2h = h_mu.numel() * 4 + 8
         e2e = {"value": inter_step * n_e2e * world / dt, "unit": "interactions/s", "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h, "steps": n_e2e,
-               "includes": "field upload + repack, shoot, normalise, D2H of mu and out-of-window, field release"}
+               "includes": "field upload from pinned host memory + validation + repack, shoot of the step's rows, "
+                           "normalise, D2H of mu and the out-of-window count, field release"}
+    field.close()
+    del counts, oow, mu
+    torch.cuda.empty_cache()
+
+    side = workload("n1e4", seed=0) if args.workload != "n1e4" else spec
+
+    # ---------------- the other configurations (one GPU), each with its roofline
+    configs = None
+    if not args.no_configs and world == 1:
+        names = [v for v in args.configs.split(",") if v and v != args.workload]
+        configs = run_configs(rs, torch, device, stream, names, cpu=not args.no_cpu_baseline,
+                              launch_shape=args.launch_shape, max_sample=args.max_sample)
 
     # ---------------- batched maps/s vs plain launches (64 fields)
     batched = None
@@ -369,58 +467,64 @@ def run_ours(args):
     if not args.no_light_curves and world == 1:
         light = run_light_curves(rs, torch, device, stream, cpu_baseline=not args.no_cpu_baseline)
 
-    # ---------------- zoom into the map (culled shooting) vs plain shooting of the finer grid
+    # ---------------- zoom into the 1e4-lens map (culled shooting) vs plain shooting of the finer grid
     zoom = None
     if not args.no_zoom and world == 1:
-        zoom = run_zoom(rs, torch, device, stream, spec)
-        zoom["culled_full_map"] = run_zoom(rs, torch, device, stream, spec, factor=1, quarter=False)
+        zoom = run_zoom(rs, torch, device, stream, side)
+        zoom["culled_full_map"] = run_zoom(rs, torch, device, stream, side, factor=1, quarter=False)
 
     # ---------------- a time series of maps with moving lenses (one batch launch per 16 steps)
     frames = None
     if not args.no_frames and world == 1:
-        frames = run_frames(rs, torch, device, stream, spec)
+        frames = run_frames(rs, torch, device, stream, side)
 
     # ---------------- lens-partitioned shooting: device shards and host-streamed lenses
     staged = None
     if not args.no_staged and world == 1:
-        staged = run_staged(rs, torch, device, stream, spec)
+        staged = run_staged(rs, torch, device, stream, side)
 
     # ---------------- CPU baseline (oracle, bounded sample)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        r = oracle_rate(spec, args.cpu_seconds)
+        r = oracle_sample_rate(spec, args.cpu_seconds)
         cpu = {"value": r["value"], "unit": "interactions/s", "cores": r["cores"], "kind": "oracle",
-               "sample": f"{r['rows']} central grid rows ({r['rays']} rays) x {spec.n_lens} lenses, "
-                         f"{r['seconds']:.1f} s, FP64 OpenMP over rays"}
+               "sample": r["sample"]}
 
-    field.close()
     if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
         return
-    sms, max_mhz = peaks(local)
-    peak = fp32_peak_tflops(sms, max_mhz)
-    achieved = inter_step * FLOPS_PER_INTERACTION / shoot_avg_s / 1e12
+    rl = roofline_entry(inter_step, shoot_avg_s, sms, max_mhz, profiled_traffic(args.workload))
     med = clk.get("sm_mhz")
     cfg = workload_config(spec, args.workload)
+    cfg["rows_per_step"] = [r0, r1]
+    cfg["rays_per_step"] = rays_step
+    cfg["interactions_per_step"] = inter_step
+    cfg["sample"] = rows_note
+    cfg["l2"] = ("inputs larger than L2 (lenses: %.2f GB on the device); L2 also flushed between steps (512 MiB "
+                 "write)" % (spec.n_lens * (24 if spec.masses is not None else 16) / 1e9)
+                 if spec.n_lens * 16 > (129 << 20) else "flushed between timed steps (512 MiB write)")
     cfg["launch_shape"] = f"{shape[0]} threads x {shape[1]} rays/thread" + ("" if args.launch_shape else " (autotuned)")
     cfg["certified_binning"] = rs.rs_get_certified_binning()
+    rl.update({"kernel": "shoot_kernel (span of rs_shoot_rows: list reset, shoot, certified re-evaluation)",
+               "kernel_ms": shoot_avg_s * 1e3,
+               "peak_basis": f"FP32 FMA: {sms} SMs x 128 lanes x 2 flops x {max_mhz:.0f} MHz (max clock); "
+                             f"10 flops per interaction (paper App. A)"})
     line = {
         "metric": METRIC, "value": value, "unit": "interactions/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_s / args.steps * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": cfg,
-        "pct_fp32_peak": 100.0 * achieved / peak,
-        "pct_fp32_peak_at_measured_clock": (100.0 * achieved / fp32_peak_tflops(sms, med)) if med else None,
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak, "traffic": profiled_traffic(args.workload),
-                     "kernel": "shoot_kernel (span of rs_shoot: list reset, shoot, certified re-evaluation)",
-                     "kernel_ms": shoot_avg_s * 1e3,
-                     "peak_basis": f"FP32 FMA: {sms} SMs x 128 lanes x 2 flops x {max_mhz:.0f} MHz (max clock); "
-                                   f"10 flops per interaction (paper App. A)"},
+        "pct_fp32_peak": 100.0 * rl["frac"],
+        "pct_fp32_peak_at_measured_clock": (100.0 * rl["achieved"] / fp32_peak_tflops(sms, med)) if med else None,
+        "roofline": rl,
         "clocks": {"sm_mhz": med, "sm_max_mhz": clk.get("sm_max_mhz"), "reasons": clk.get("reasons"),
                    "samples": clk.get("samples")},
         "e2e": e2e,
         "gpu_launches": (3 if rs.rs_get_certified_binning() else 2) * args.steps,
+        "rays_conserved": conserved,
         "cpu_baseline": cpu,
+        "configs": configs,
         "batched": batched,
         "light_curves": light,
         "zoom": zoom,
@@ -477,7 +581,7 @@ def run_batched_small(rs, torch, device, stream, n_fields=256, reps=5):
             "interactions_per_s": inter / t_batch, "bitwise_equal": bool(same), "reps": reps}
 
 
-def run_batched(rs, torch, device, stream, reps=3):
+def run_batched(rs, torch, device, stream, reps=10):
     from paper_0905_2453_gb300 import tune
     specs = ri.batch_fields(64)
     fields = [rs.Field.from_spec(s, stream) for s in specs]
@@ -501,27 +605,33 @@ def run_batched(rs, torch, device, stream, reps=3):
     torch.cuda.synchronize(device)
     same = all(torch.equal(b.counts[k], counts_plain[k]) for k in range(len(specs))) and \
         torch.equal(b.out_of_window, oow_plain)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(reps):
+    # alternate the two so that both see the same clock and temperature history; every repetition timed
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(reps)]
+    for e in ev:
+        e[0].record(stream)
         b.launch(stream)
-    e1.record(stream)
-    torch.cuda.synchronize(device)
-    t_batch = e0.elapsed_time(e1) / 1e3 / reps
-    e0.record(stream)
-    for _ in range(reps):
+        e[1].record(stream)
+        e[2].record(stream)
         plain()
-    e1.record(stream)
+        e[3].record(stream)
     torch.cuda.synchronize(device)
-    t_plain = e0.elapsed_time(e1) / 1e3 / reps
+    tb = [e[0].elapsed_time(e[1]) / 1e3 for e in ev]
+    tp = [e[2].elapsed_time(e[3]) / 1e3 for e in ev]
+    t_batch, t_plain = statistics.median(tb), statistics.median(tp)
+    ratios = sorted(p / q for p, q in zip(tp, tb))
     inter = sum(s.interactions for s in specs)
     b.close()
     for f in fields:
         f.close()
+    sms = torch.cuda.get_device_properties(device).multi_processor_count
     return {"workload": "64 Salpeter fields, N* log-uniform [1e2,1e5], rays 1024^2-4096^2, maps 512^2-1024^2",
             "maps_per_s": len(specs) / t_batch, "plain_maps_per_s": len(specs) / t_plain,
-            "speedup": t_plain / t_batch, "interactions_per_s": inter / t_batch, "bitwise_equal": bool(same),
-            "reps": reps}
+            "speedup": t_plain / t_batch,
+            "speedup_per_rep": {"min": ratios[0], "median": statistics.median(ratios), "max": ratios[-1]},
+            "batch_ms": {"median": t_batch * 1e3, "min": min(tb) * 1e3, "max": max(tb) * 1e3},
+            "plain_ms": {"median": t_plain * 1e3, "min": min(tp) * 1e3, "max": max(tp) * 1e3},
+            "interactions_per_s": inter / t_batch, "bitwise_equal": bool(same), "reps": reps,
+            "roofline": roofline_entry(inter, t_batch, sms, 2070.0)}
 
 
 def support_pixels(wins, tracks, R):
@@ -870,6 +980,7 @@ def run_configs(rs, torch, device, stream, names, cpu=True, full_limit=2e12, max
                           "sample_interactions_per_s": blocks[1]["interactions_per_s"],
                           "sample_pct_fp32_peak_2070mhz": pct(blocks[1]["interactions_per_s"])})
         entry["clocks"] = clocks.stop()
+        entry["roofline"] = roofline_entry(1.0, 1.0 / entry["interactions_per_s"], sms, 2070.0, profiled_traffic(name))
         entry["full_grid_seconds_at_this_rate"] = spec.interactions / entry["interactions_per_s"]
         entry["status"] = f.status()
         f.close()
@@ -893,7 +1004,7 @@ def main():
     ap.add_argument("--steps", type=int, default=60)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", default="n1e4")
+    ap.add_argument("--workload", default="n1e8")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-light-curves", action="store_true")
@@ -902,12 +1013,14 @@ def main():
     ap.add_argument("--no-staged", action="store_true")
     ap.add_argument("--max-sample", type=float, default=2e13,
                     help="interactions of the larger row block of a sampled configuration (--section configs)")
-    ap.add_argument("--configs", default="tiny,n1e4,n1e6,n1e8",
-                    help="workloads of --section configs (comma-separated: tiny, n1e4, n1e6, n1e8)")
+    ap.add_argument("--configs", default="tiny,n1e4,n1e6",
+                    help="workloads of the configs sub-object (comma-separated: tiny, n1e4, n1e6, n1e8; the "
+                         "headline workload is left out)")
+    ap.add_argument("--no-configs", action="store_true")
     ap.add_argument("--section", choices=["zoom", "light-curves", "frames", "staged", "batch-small", "configs"],
                     default=None,
                     help="run one secondary measurement alone and print its JSON object (for profiling)")
-    ap.add_argument("--batch-reps", type=int, default=3)
+    ap.add_argument("--batch-reps", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--launch-shape", default=None, help="fix the launch shape, e.g. 128x8 (skips the autotuner)")

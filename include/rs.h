@@ -193,7 +193,7 @@ int rs_shoot_culled(rs_field_t f, const rs_ray_grid* g, int64_t row_begin, int64
  * the last must hold a multiple of 256 lenses, and all share device, kappa_c, gamma and whether
  * masses were given (masses given to all or to none; if any partition's masses are not all 1, every
  * partition runs the weighted kernels).
- * The carried state is the shoot kernel's own accumulator set (24 bytes per ray, stream-ordered
+ * The carried state is the shoot kernel's own accumulator set (28 bytes per ray, stream-ordered
  * allocation; rays are processed in row blocks of at most 2 GiB of state), so the float32
  * deflections, error bands and counts equal those of one rs_shoot_rows over a single field
  * holding all the lenses, bit for bit; with certified binning on, the listed rays are
@@ -231,8 +231,8 @@ int rs_set_staged_state_budget(uint64_t bytes);  /* also used by rs_shoot_stream
  *   d_alpha  : double[2*k] device or NULL, receives (alpha1, alpha2) per ray (Eq. 2).
  *   d_err    : double[2*k] device or NULL, receives per axis the half-width of the band
  *              around y inside which the float32 result cannot decide a pixel (see
- *              certified binning below).
- * The per-ray arithmetic is the one rs_shoot uses, bit for bit.
+ *              certified binning below); asking for it costs one more pass over the lenses.
+ * The per-ray arithmetic is the one rs_shoot uses, bit for bit (the band included).
  */
 int rs_trace(rs_field_t f, const rs_ray_grid* g, const int64_t* d_ray_ij, int64_t k, double* d_y,
              double* d_alpha, double* d_err, void* stream);
@@ -247,15 +247,19 @@ int rs_trace_certified(rs_field_t f, const rs_ray_grid* g, const int64_t* d_ray_
 
 /*
  * Certified binning (on by default).  The float32 shoot attaches to every ray an error band:
- * 10 u sqrt(64 sum_g (P1_g^2 + P2_g^2)) + 2 u sum_g (|P1_g| + |P2_g|) (u = 2^-24, P_g the float32
- * partial sums of its 64-lens groups): the random rounding, plus coherent errors (the far field
+ * 10 u sqrt(64 sum_g (P1_g^2 + P2_g^2)) + 2 u sum_g (|P1_g| + |P2_g|) + 16 u T (u = 2^-24, P_g the
+ * float32 partial sums of its 64-lens groups): the random rounding, coherent errors (the far field
  * sees the ray's coordinate only to the precision of the lens-ray difference; a bias of the
- * approximate reciprocal).  A ray whose source position lies within that band of a pixel or window edge is
- * not binned by the float32 result but re-evaluated with rs_trace_certified's arithmetic and
- * binned from that; the maps then agree with a float64 evaluation except for rays within ~1e-12
- * of an edge and rays whose float32 error exceeds the band: the band is an estimate from the group
- * partials, and a ray between near lenses whose terms cancel inside one group can exceed it (seen
- * on fields of a few lenses; on fields of 100 lenses and more every checked ray stayed inside).
+ * approximate reciprocal), and the rounding of the largest single terms, which a group partial
+ * hides where near lenses' terms cancel inside it: T = max(m_max, max m_i / r_i over the lenses
+ * within r_i <= 1 of the ray), m_max the field's largest mass.  A ray whose source position lies
+ * within that band of a pixel or window edge is not binned by the float32 result but re-evaluated
+ * with rs_trace_certified's arithmetic and binned from that; the maps then agree with a float64
+ * evaluation except for rays within ~1e-12 of an edge and rays whose float32 error exceeds the
+ * band.  The band is an estimate of the error, not a rigorous bound (that bound, 72 u sum_i m_i / r_i,
+ * would need a square root per lens and ray); the tests check that it covers the float32 error of
+ * every ray traced on fields of 1 to 1e8 lenses, few-lens fields included, and that certified maps
+ * of such fields equal the oracle's bit for bit.
  * rs_shoot allocates the list of such rays stream-ordered (cudaMallocAsync,
  * capacity max(4096, rays/32), at most 2^24 entries); rays beyond the capacity keep their
  * float32 decision and the field's status records RS_EOVERFLOW (rs_field_status).  Batches own their list.
@@ -316,10 +320,14 @@ int rs_field_status(rs_field_t f, int clear, int* status);
  * afterwards) for fields without (has_masses = 0) or with per-lens masses.
  * rs_launch_configs lists the compiled shapes: up to `cap` (block, rpt)
  * pairs into `pairs` (int[2*cap]); returns the number available via *count.
+ * rs_launch_occupancy reports how many CTAs of a shape's shoot kernel are
+ * resident per SM on the current device (SMs x that = one wave of CTAs);
+ * RS_EINVAL for a shape that is not compiled.
  */
 int rs_set_launch_config(int has_masses, int block, int rays_per_thread);
 int rs_get_launch_config(int has_masses, int* block, int* rays_per_thread);
 int rs_launch_configs(int* pairs, int cap, int* count);
+int rs_launch_occupancy(int has_masses, int block, int rays_per_thread, int* ctas_per_sm);
 
 /*
  * Light curves (Section 1: a source of finite size moves across the magnification map; the
@@ -403,7 +411,9 @@ int rs_light_curve_plan_destroy(rs_lc_plan_t p);
  *   - at most 2^24 rays per call (one list entry per 32 rays); larger row ranges return
  *     RS_EOVERFLOW without launching anything -- split them over several calls;
  *   - the first call on a device looks up the array's device address (cudaGetSymbolAddress,
- *     with that device current); make that first call before any stream capture;
+ *     with that device current), and so does the first call after the device's context changed
+ *     (a device reset loads the library's device code anew); make such a first call before any
+ *     stream capture;
  *   - every call shares the array and the array keeps the last call's contents; each call
  *     clears the entry counter on its stream.  Calls that overlap on the GPU (different
  *     streams, or different host threads, without ordering between them) race on the array:
@@ -434,6 +444,13 @@ const char* rs_last_error(void);
 
 /* Library version string. */
 const char* rs_version(void);
+
+/*
+ * rs_device_code_version -- the compute capability the library's device code was built for, as
+ * the CUDA runtime reports it for one of its kernels (cudaFuncAttributes::binaryVersion: 103 for
+ * sm_103a).  Needs a device; RS_ECUDA when the code cannot run on the current one.
+ */
+int rs_device_code_version(int* binary_version);
 
 #ifdef __cplusplus
 }

@@ -33,7 +33,7 @@ __all__ = [
     "rs_selftest_bounded_wait", "rs_shoot_rows_noalloc", "rs_light_curves", "rs_shoot_culled",
     "rs_create_moving_field", "rs_field_set_time", "rs_field_time", "rs_shoot_staged", "rs_shoot_streamed",
     "rs_set_staged_state_budget", "rs_set_alloc_failure", "rs_light_curve_plan_create", "rs_light_curve_plan_samples",
-    "rs_light_curve_plan_launch", "rs_light_curve_plan_destroy", "rs_create_field_view",
+    "rs_light_curve_plan_launch", "rs_light_curve_plan_destroy", "rs_create_field_view", "rs_device_code_version", "rs_launch_occupancy",
 ]
 
 RS_OK, RS_EINVAL, RS_ENOMEM, RS_ECUDA, RS_EOVERFLOW, RS_ETIMEOUT = 0, 1, 2, 3, 4, 5
@@ -48,7 +48,7 @@ EXPORTED_SYMBOLS = (
     "rs_create_moving_field", "rs_field_set_time", "rs_field_time", "rs_shoot_staged", "rs_shoot_streamed",
     "rs_set_staged_state_budget", "rs_set_alloc_failure",
     "rs_light_curve_plan_create", "rs_light_curve_plan_samples", "rs_light_curve_plan_launch",
-    "rs_light_curve_plan_destroy", "rs_create_field_view",
+    "rs_light_curve_plan_destroy", "rs_create_field_view", "rs_device_code_version", "rs_launch_occupancy",
 )
 
 
@@ -156,9 +156,11 @@ def load():
         "rs_field_status": ([vp, i32, ctypes.POINTER(i32)], i32),
         "rs_last_error": ([], ctypes.c_char_p),
         "rs_version": ([], ctypes.c_char_p),
+        "rs_device_code_version": ([ctypes.POINTER(i32)], i32),
         "rs_set_launch_config": ([i32, i32, i32], i32),
         "rs_get_launch_config": ([i32, ctypes.POINTER(i32), ctypes.POINTER(i32)], i32),
         "rs_launch_configs": ([ctypes.POINTER(i32), i32, ctypes.POINTER(i32)], i32),
+        "rs_launch_occupancy": ([i32, i32, i32, ctypes.POINTER(i32)], i32),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -221,6 +223,13 @@ def _dptr(t, dtype, name, numel=None):
 
 def rs_version() -> str:
     return load().rs_version().decode()
+
+
+def rs_device_code_version() -> int:
+    """Compute capability the library's device code targets, as the CUDA runtime reports it (103)."""
+    v = ctypes.c_int32(0)
+    _check(load().rs_device_code_version(ctypes.byref(v)), "rs_device_code_version")
+    return int(v.value)
 
 
 def rs_last_error() -> str:
@@ -591,6 +600,14 @@ def rs_launch_configs():
     buf = (ctypes.c_int * 64)()
     _check(load().rs_launch_configs(buf, 32, ctypes.byref(cnt)), "rs_launch_configs")
     return [(buf[2 * i], buf[2 * i + 1]) for i in range(min(cnt.value, 32))]
+
+
+def rs_launch_occupancy(has_masses: bool, block: int, rays_per_thread: int) -> int:
+    """Resident CTAs per SM of a launch shape's shoot kernel on the current device."""
+    v = ctypes.c_int(0)
+    _check(load().rs_launch_occupancy(int(bool(has_masses)), int(block), int(rays_per_thread), ctypes.byref(v)),
+           "rs_launch_occupancy")
+    return int(v.value)
 
 
 # ------------------------------------------------------------------------------------------- objects

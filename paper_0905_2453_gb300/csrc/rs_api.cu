@@ -36,12 +36,17 @@ __global__ void pack_lenses_kernel(const float* __restrict__ xy, const float* __
   }
 }
 
-// *flag |= 1 if some mass is not exactly 1 (NaN included): such a field needs the weighted kernels.
+// flag[0] |= 1 if some mass is not exactly 1 (NaN included): such a field needs the weighted kernels;
+// flag[1] = max of the bit patterns of |m| (the largest |m|: non-negative floats order as their bits).
 __global__ void mass_check_kernel(const float* __restrict__ m, int64_t n, unsigned int* __restrict__ flag) {
   bool weighted = false;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+  unsigned int mx = 0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     weighted |= !(m[i] == 1.0f);
+    mx = max(mx, __float_as_uint(fabsf(m[i])));
+  }
   if (__syncthreads_or(weighted) && threadIdx.x == 0) atomicOr(flag, 1u);
+  atomicMax(flag + 1, mx);
 }
 
 // Moving fields: {x1, x2, v1, v2} per lens at t = 0.
@@ -237,6 +242,11 @@ int fill_desc(const rs_field* f, const rs_ray_grid* g, int64_t row_begin, int64_
   return RS_OK;
 }
 
+float near_cap(int64_t n_lens, float m_max) {
+  // the near radius h is 1: the cap on every term of a lens farther than h is the largest mass itself
+  return n_lens > 0 ? m_max : 0.f;
+}
+
 cudaError_t launch_pack_lenses(const float* xy, const float* m, int64_t n, int64_t n_pad, float4* lens4,
                                float2* mass2, int blocks, cudaStream_t s) {
   pack_lenses_kernel<<<blocks, 256, 0, s>>>(xy, m, n, n_pad, lens4, mass2);
@@ -251,7 +261,16 @@ extern "C" {
 
 const char* rs_last_error(void) { return g_err.c_str(); }
 
-const char* rs_version(void) { return "rs-gb300 0.2 (sm_103a)"; }
+const char* rs_version(void) { return "rs-gb300 0.3 (sm_103a)"; }
+
+int rs_device_code_version(int* binary_version) {
+  if (!binary_version) return fail(RS_EINVAL, "binary_version is NULL");
+  cudaFuncAttributes a;
+  cudaError_t e = cudaFuncGetAttributes(&a, magnification_kernel);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaFuncGetAttributes");
+  *binary_version = a.binaryVersion;
+  return RS_OK;
+}
 
 int rs_set_launch_config(int has_masses, int block, int rays_per_thread) {
   const int c = rsint::find_cfg(block, rays_per_thread);
@@ -264,6 +283,15 @@ int rs_get_launch_config(int has_masses, int* block, int* rays_per_thread) {
   const int c = g_cfg[has_masses ? 1 : 0];
   if (block) *block = rsint::kCfgs[c].block;
   if (rays_per_thread) *rays_per_thread = rsint::kCfgs[c].rpt;
+  return RS_OK;
+}
+
+int rs_launch_occupancy(int has_masses, int block, int rays_per_thread, int* ctas_per_sm) {
+  if (!ctas_per_sm) return fail(RS_EINVAL, "ctas_per_sm is NULL");
+  const int c = rsint::find_cfg(block, rays_per_thread);
+  if (c < 0) return fail(RS_EINVAL, "no compiled launch shape (%d threads, %d rays/thread)", block, rays_per_thread);
+  cudaError_t e = rsint::shoot_blocks_per_sm(c, has_masses != 0, ctas_per_sm);
+  if (e != cudaSuccess) return cuda_fail(e, "occupancy query");
   return RS_OK;
 }
 
@@ -287,14 +315,18 @@ int rs_create_field(const float* lens_xy, const float* masses, int64_t n_lens, d
   // masses that are all exactly 1 select the unit-mass kernels, as NULL does (the masses are still
   // stored, so such a field can be a lens partition next to weighted ones)
   bool unit_masses = true;
+  float m_max = n_lens > 0 ? 1.f : 0.f;  // largest mass (the near-lens band term's cap)
   if (!inputs_on_device) {
     for (int64_t i = 0; i < 2 * n_lens; ++i)
       if (!finite_coord((double)lens_xy[i])) return fail(RS_EINVAL, "lens coordinate %lld not finite or beyond 1e9", (long long)i);
-    if (masses)
+    if (masses) {
+      m_max = 0.f;
       for (int64_t i = 0; i < n_lens; ++i) {
         if (!(std::isfinite(masses[i]) && masses[i] >= 0.f)) return fail(RS_EINVAL, "mass %lld not finite or negative", (long long)i);
         unit_masses = unit_masses && masses[i] == 1.0f;
+        m_max = std::max(m_max, masses[i]);
       }
+    }
   }
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   rs_field* f = new (std::nothrow) rs_field();
@@ -320,9 +352,10 @@ int rs_create_field(const float* lens_xy, const float* masses, int64_t n_lens, d
     cudaFree(tmp_m);
     delete f;
   };
+  // status word, and a second word for the mass check of device inputs
   if ((e = dev_alloc(&f->lens4, sizeof(float4) * f->n_pad)) != cudaSuccess ||
       (has_mass && (e = dev_alloc(&f->mass2, sizeof(float2) * f->n_pad)) != cudaSuccess) ||
-      (e = dev_alloc(&f->status, sizeof(unsigned int))) != cudaSuccess) {
+      (e = dev_alloc(&f->status, 2 * sizeof(unsigned int))) != cudaSuccess) {
     int rc = cuda_fail(e, "cudaMalloc (field)");
     cleanup();
     return rc;
@@ -346,27 +379,29 @@ int rs_create_field(const float* lens_xy, const float* masses, int64_t n_lens, d
     src_xy = tmp_xy;
     src_m = tmp_m;
   }
-  if ((e = cudaMemsetAsync(f->status, 0, sizeof(unsigned int), s)) != cudaSuccess) {
+  if ((e = cudaMemsetAsync(f->status, 0, 2 * sizeof(unsigned int), s)) != cudaSuccess) {
     int rc = cuda_fail(e, "cudaMemsetAsync (status)");
     cudaStreamSynchronize(s);
     cleanup();
     return rc;
   }
   if (has_mass && inputs_on_device && n_lens > 0) {
-    // unit-mass test of device inputs: the status word serves as the flag, read back and cleared
-    unsigned int weighted = 0;
+    // unit-mass test and largest mass of device inputs: the two status words serve as the flag and
+    // the maximum, read back and cleared
+    unsigned int check[2] = {0u, 0u};
     const int blocks = (int)std::min<int64_t>((n_lens + 255) / 256, (int64_t)num_sms(f->device) * 8);
     mass_check_kernel<<<blocks, 256, 0, s>>>(masses, n_lens, f->status);
     if ((e = cudaGetLastError()) != cudaSuccess ||
-        (e = cudaMemcpyAsync(&weighted, f->status, sizeof(unsigned int), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(check, f->status, sizeof(check), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
         (e = cudaStreamSynchronize(s)) != cudaSuccess ||
-        (e = cudaMemsetAsync(f->status, 0, sizeof(unsigned int), s)) != cudaSuccess) {
+        (e = cudaMemsetAsync(f->status, 0, sizeof(check), s)) != cudaSuccess) {
       int rc = cuda_fail(e, "mass check");
       cudaStreamSynchronize(s);
       cleanup();
       return rc;
     }
-    unit_masses = weighted == 0u;
+    unit_masses = check[0] == 0u;
+    std::memcpy(&m_max, &check[1], sizeof(float));
   }
   {
     const int threads = 256;
@@ -399,6 +434,7 @@ int rs_create_field(const float* lens_xy, const float* masses, int64_t n_lens, d
   f->dev.lam1 = (1.0 - kappa_c) - gamma;
   f->dev.lam2 = (1.0 - kappa_c) + gamma;
   f->dev.lamabs = std::nextafter((float)std::max(std::fabs(f->dev.lam1), std::fabs(f->dev.lam2)), INFINITY);
+  f->dev.mcap = near_cap(n_lens, f->dev.has_mass ? m_max : 1.f);
   f->dev.status = f->status;
   *out = f;
   return RS_OK;
@@ -760,20 +796,42 @@ static __device__ __align__(256) unsigned char g_static_recheck[256 + sizeof(uin
 namespace {
 
 constexpr int kMaxDevices = 64;
+constexpr int64_t kStaticMaxRays = (int64_t)kStaticRecheckEntries * 32;  // one list entry per 32 rays: 2^24
 std::mutex g_static_mutex;
 void* g_static_ptr[kMaxDevices] = {};
+void* g_static_ctx[kMaxDevices] = {};
 
-// Device address of g_static_recheck on the current device, looked up once per device.  In host
-// code the array's name only stands in for the device symbol; its address must come from
-// cudaGetSymbolAddress with the device current.
+// The current CUDA context (through the driver entry point, so the library needs no link to the
+// driver library), or nullptr where it cannot be queried.
+void* current_context() {
+  using GetCtx = int (*)(void**);
+  static GetCtx fn = []() -> GetCtx {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      return nullptr;
+    return reinterpret_cast<GetCtx>(p);
+  }();
+  void* ctx = nullptr;
+  if (fn == nullptr || fn(&ctx) != 0) return nullptr;
+  return ctx;
+}
+
+// Device address of g_static_recheck in the current device's context, looked up on the first call
+// on a device and again whenever the context changed (after a device reset the module, and with it
+// the array, is loaded anew).  In host code the array's name only stands in for the device symbol;
+// its address must come from cudaGetSymbolAddress with the device current.
 int static_recheck_ptr(int device, void** out) {
   if (device < 0 || device >= kMaxDevices) return fail(RS_EINVAL, "device index %d beyond %d", device, kMaxDevices);
+  void* ctx = current_context();
   std::lock_guard<std::mutex> lock(g_static_mutex);
-  if (!g_static_ptr[device]) {
+  if (!g_static_ptr[device] || g_static_ctx[device] != ctx) {
     void* p = nullptr;
     cudaError_t e = cudaGetSymbolAddress(&p, g_static_recheck);
     if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress (static re-evaluation list)");
     g_static_ptr[device] = p;
+    g_static_ctx[device] = ctx;
   }
   *out = g_static_ptr[device];
   return RS_OK;
@@ -791,12 +849,12 @@ extern "C" int rs_shoot_rows_noalloc(rs_field_t f, const rs_ray_grid* g, int64_t
   ShootDesc d;
   if ((rc = fill_desc(f, g, row_begin, row_end, w, d_counts, d_out_of_window, &d)) != RS_OK) return rc;
   if (d.n_rows == 0 || d.n0 == 0) return RS_OK;
-  const unsigned int cap = rsint::recheck_capacity(d.n_rows * d.n0);
-  if (cap > kStaticRecheckEntries)
+  if (d.n_rows * d.n0 > kStaticMaxRays)
     return fail(RS_EOVERFLOW,
                 "rs_shoot_rows_noalloc shoots at most 2^24 rays per call (its static re-evaluation list holds %u "
                 "entries, one per 32 rays); got %lld rays: split the rows over several calls",
                 kStaticRecheckEntries, (long long)(d.n_rows * d.n0));
+  const unsigned int cap = rsint::recheck_capacity(d.n_rows * d.n0);
   void* base = nullptr;
   if ((rc = static_recheck_ptr(f->device, &base)) != RS_OK) return rc;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);

@@ -44,7 +44,7 @@ int rs_shoot_staged(int n_parts, const rs_field_t* parts, const rs_ray_grid* g, 
   if ((rc = fill_desc(parts[0], g, row_begin, row_end, w, d_counts, d_out_of_window, &d)) != RS_OK) return rc;
   if (d.n_rows == 0 || d.n0 == 0) return RS_OK;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  // ray blocks whose carried state fits the budget (the state is 24 bytes per ray, padded to tiles)
+  // ray blocks whose carried state fits the budget (the state is 28 bytes per ray, padded to tiles)
   const size_t budget = g_staged_budget;
   const size_t per4 = rsint::staged_state_bytes(4, d.n0);
   const int64_t rows_blk = std::max<int64_t>(4, (int64_t)(budget / per4) * 4);
@@ -101,10 +101,12 @@ int rs_shoot_streamed(const float* h_lens_xy, const float* h_masses, int64_t n_l
   for (int64_t i = 0; i < 2 * n_lens; ++i)
     if (!finite_coord((double)h_lens_xy[i])) return fail(RS_EINVAL, "lens coordinate %lld not finite or beyond 1e9", (long long)i);
   bool unit_masses = true;
+  float m_max = 0.f;
   if (h_masses)
     for (int64_t i = 0; i < n_lens; ++i) {
       if (!(std::isfinite(h_masses[i]) && h_masses[i] >= 0.f)) return fail(RS_EINVAL, "mass %lld not finite or negative", (long long)i);
       unit_masses = unit_masses && h_masses[i] == 1.0f;
+      m_max = std::max(m_max, h_masses[i]);
     }
   int rc;
   if ((rc = check_call(g, row_begin, row_end, w, d_counts)) != RS_OK) return rc;
@@ -123,6 +125,8 @@ int rs_shoot_streamed(const float* h_lens_xy, const float* h_masses, int64_t n_l
   proto.dev.lam1 = (1.0 - kappa_c) - gamma;
   proto.dev.lam2 = (1.0 - kappa_c) + gamma;
   proto.dev.lamabs = std::nextafter((float)std::max(std::fabs(proto.dev.lam1), std::fabs(proto.dev.lam2)), INFINITY);
+  // every pass carries the cap of the whole lens set, as a field of all the lenses would
+  proto.dev.mcap = near_cap(n_lens, mass ? m_max : 1.f);
   ShootDesc d;
   if ((rc = fill_desc(&proto, g, row_begin, row_end, w, d_counts, d_out_of_window, &d)) != RS_OK) return rc;
   if (d.n_rows == 0 || d.n0 == 0) return RS_OK;

@@ -15,14 +15,15 @@ using namespace rsdev;
 template <int WARPS, int RPT, int TILE, bool MASS>
 __global__ void __launch_bounds__(WARPS * 32, WARPS <= 4 ? 2 : 1)
     batch_kernel(const ShootDesc* __restrict__ descs, const int2* __restrict__ items, int n_items, int* counter) {
-  __shared__ LensSmem<TILE, WARPS> sm;
+  extern __shared__ __align__(128) unsigned char rs_smem[];
+  auto& ss = *reinterpret_cast<ShootSmem<WARPS, RPT, TILE>*>(rs_smem);
   __shared__ int s_item;
   // the current item's field descriptor, staged in shared memory once per item so that the tile
   // code reads it as cheaply as the plain kernel reads its kernel-parameter descriptor
   __shared__ __align__(16) ShootDesc s_desc;
   static_assert(sizeof(ShootDesc) % 4 == 0, "descriptor copied as 32-bit words");
   PipeState ps;
-  pipe_init(sm.bar, ps);
+  pipe_init(ss.lens.bar, ps);
   int cur_field = -1;
   for (;;) {
     if (threadIdx.x == 0) s_item = atomicAdd(counter, 1);
@@ -37,28 +38,40 @@ __global__ void __launch_bounds__(WARPS * 32, WARPS <= 4 ? 2 : 1)
       cur_field = w.x;
     }
     __syncthreads();  // s_desc ready; every thread has read s_item
-    const bool ok = shoot_tile<WARPS, RPT, TILE, MASS>(s_desc, (int64_t)w.y, sm, ps);
+    const bool ok = shoot_tile<WARPS, RPT, TILE, MASS>(s_desc, (int64_t)w.y, ss, ps);
     if (!ok) break;
   }
+}
+
+template <int WARPS, int RPT, bool MASS>
+cudaError_t launch_batch_m(const ShootDesc* descs, const int2* items, int n_items, int* counter, int grid,
+                           cudaStream_t s) {
+  constexpr size_t smem = sizeof(ShootSmem<WARPS, RPT, rsint::kTile>);
+  cudaError_t e = rsint::smem_opt_in<batch_kernel<WARPS, RPT, rsint::kTile, MASS>>(smem);
+  if (e != cudaSuccess) return e;
+  batch_kernel<WARPS, RPT, rsint::kTile, MASS><<<grid, WARPS * 32, smem, s>>>(descs, items, n_items, counter);
+  return cudaGetLastError();
 }
 
 template <int WARPS, int RPT>
 cudaError_t launch_batch_t(bool mass, const ShootDesc* descs, const int2* items, int n_items, int* counter, int grid,
                            cudaStream_t s) {
-  if (mass)
-    batch_kernel<WARPS, RPT, rsint::kTile, true><<<grid, WARPS * 32, 0, s>>>(descs, items, n_items, counter);
-  else
-    batch_kernel<WARPS, RPT, rsint::kTile, false><<<grid, WARPS * 32, 0, s>>>(descs, items, n_items, counter);
-  return cudaGetLastError();
+  return mass ? launch_batch_m<WARPS, RPT, true>(descs, items, n_items, counter, grid, s)
+              : launch_batch_m<WARPS, RPT, false>(descs, items, n_items, counter, grid, s);
+}
+
+template <int WARPS, int RPT, bool MASS>
+cudaError_t occ_m(int* blocks) {
+  constexpr size_t smem = sizeof(ShootSmem<WARPS, RPT, rsint::kTile>);
+  cudaError_t e = rsint::smem_opt_in<batch_kernel<WARPS, RPT, rsint::kTile, MASS>>(smem);
+  if (e != cudaSuccess) return e;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, batch_kernel<WARPS, RPT, rsint::kTile, MASS>,
+                                                       WARPS * 32, smem);
 }
 
 template <int WARPS, int RPT>
 cudaError_t occ_t(bool mass, int* blocks) {
-  if (mass)
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, batch_kernel<WARPS, RPT, rsint::kTile, true>,
-                                                         WARPS * 32, 0);
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, batch_kernel<WARPS, RPT, rsint::kTile, false>,
-                                                       WARPS * 32, 0);
+  return mass ? occ_m<WARPS, RPT, true>(blocks) : occ_m<WARPS, RPT, false>(blocks);
 }
 
 }  // namespace

@@ -158,6 +158,7 @@ __global__ void __launch_bounds__(128, 2) shoot_cells_kernel(const ShootDesc d, 
                                                              const unsigned* __restrict__ n_kept) {
   constexpr int RPT = 8;
   __shared__ LensSmem<rsint::kTile, 1> sm;
+  __shared__ NearSmem<rsint::kTile, 4, 128, RPT> ns;  // one near-lens box per warp (its cell)
   PipeState ps;
   pipe_init(sm.bar, ps);
   const unsigned count = *n_kept;
@@ -182,9 +183,18 @@ __global__ void __launch_bounds__(128, 2) shoot_cells_kernel(const ShootDesc d, 
       x1[k] = ray_coord(i, d.sp0, d.or0);
       x2[k] = x2r;
     }
-    float a1h[RPT], a1l[RPT], a2h[RPT], a2l[RPT], sig[RPT];
-    if (!deflect_pairs<RPT, rsint::kTile, MASS, false, 1>(d.f, x1, x2, a1h, a1l, a2h, a2l, sig, sm, ps)) return;
-    bin_rays<RPT, 1>(d, x1, x2, a1h, a1l, a2h, a2l, sig, valid, jrel, i_base, lane);
+    if (lane == 0) {
+      // the cell's ray box (coordinates grow with the grid index)
+      const int64_t ia = cx * kCell, ib = min(ia + kCell, d.n0) - 1;
+      const int64_t ja = cy * kCell, jb = min(ja + kCell, d.n_rows) - 1;
+      near_set_box(ns, warp, ray_coord(ia, d.sp0, d.or0), ray_coord(ib, d.sp0, d.or0),
+                   ray_coord(d.j_begin + ja, d.sp1, d.or1), ray_coord(d.j_begin + jb, d.sp1, d.or1));
+    }
+    __syncthreads();  // every box is set before the first lens tile is searched
+    float a1h[RPT], a1l[RPT], a2h[RPT], a2l[RPT], sig[RPT], tn[RPT];
+    if (!deflect_pairs<RPT, rsint::kTile, MASS, false, 1>(d.f, x1, x2, a1h, a1l, a2h, a2l, sig, tn, sm, ps, &ns))
+      return;
+    bin_rays<RPT, 1>(d, x1, x2, a1h, a1l, a2h, a2l, sig, tn, valid, jrel, i_base, lane);
   }
 }
 

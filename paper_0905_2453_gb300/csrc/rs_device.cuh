@@ -186,6 +186,7 @@ struct FieldDev {
   int32_t has_mass;
   double lam1, lam2;    // (1 - kappa_c) - gamma, (1 - kappa_c) + gamma
   float lamabs;         // max(|lam1|, |lam2|), for the Eq. 6 rounding term of the error band
+  float mcap;           // the largest mass / h: bounds every term of a lens farther than h from a ray (0: no lenses)
   unsigned int* status; // device status word (RS_OK / RS_ETIMEOUT)
 };
 
@@ -223,6 +224,132 @@ constexpr float kSigmaScale = 5.9604645e-08f * 8.0f * kSigmaSafety;
 constexpr float kSystematicScale = 2.0f * 5.9604645e-08f;
 
 constexpr int kMaxSeg = 256;  // grid columns of one CTA tile: 32 lanes x at most 8 rays per thread
+
+// ----------------------------------------------------------------------------------------------
+// Near-lens term of the error band.
+//
+// The band built from the group partials misses one kind of float32 error: where the terms of
+// lenses near a ray cancel inside one 64-lens group, the partial is far smaller than those terms,
+// whose own rounding (a few u of each) it does not show.  Every ray therefore also carries
+//   T = max(mcap, max over lenses with r^2 <= h^2 of m_i / r_i),
+// an upper bound on its largest single term (mcap = largest mass / h bounds the term of every
+// lens farther than h), and its band grows by kNearScale T.  T depends only on the ray and the
+// field (every kernel evaluates the same float32 expression, near_term, and a maximum does not
+// depend on the order).  The shoot kernels find the lenses within h of a CTA's ray box while the
+// lens tiles stream through shared memory, so only those few are evaluated per ray.
+// ----------------------------------------------------------------------------------------------
+constexpr float kNearH2 = 1.0f;          // h^2: h = 1, the Einstein radius of a unit mass
+constexpr double kNearPad = 1.001;       // box widening: > h by a margin covering float32 rounding
+constexpr float kNearScale = 0x1p-20f;   // 16 u
+
+__device__ __forceinline__ float rsqrt_approx(float x) {
+  float r;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
+// m / r of one lens for one ray when the lens lies within h (float32 r^2 <= h^2), else 0.  A ray on
+// the lens gives +inf (its band is then infinite); a massless lens gives NaN, which fmaxf ignores.
+__device__ __forceinline__ float near_term(float x1, float x2, float lx, float ly, float m) {
+  const float d1 = __fsub_rn(x1, lx), d2 = __fsub_rn(x2, ly);
+  const float r2 = __fmaf_rn(d1, d1, __fmul_rn(d2, d2));
+  return r2 <= kNearH2 ? __fmul_rn(m, rsqrt_approx(r2)) : 0.f;
+}
+
+// No near-lens search (listed-ray kernels evaluate T over every lens themselves).
+struct NoNear {
+  static constexpr bool kOn = false;
+  static constexpr int kGroups = 1;
+};
+
+// Near-lens search state of a CTA of BLOCK threads holding RPT rays each, whose rays form NG groups
+// (NG = 1: one box around all rays of the CTA; NG = warps: one box per warp).
+template <int TILE, int NG, int BLOCK, int RPT>
+struct __align__(16) NearSmem {
+  static constexpr bool kOn = true;
+  static constexpr int kGroups = NG;
+  float box[NG][4];        // x1 lo, x1 hi, x2 lo, x2 hi of each group's rays, widened by h (rounded outwards)
+  int n[NG];               // lenses of the current tile inside each box
+  uint16_t idx[NG][TILE];  // their indices within the tile
+  float t[RPT * BLOCK];    // per ray: the largest near term so far (thread x's ray k at k * BLOCK + x)
+};
+
+// Box of the rays [x1a, x1b] x [x2a, x2b] widened by kNearPad: a lens outside it is farther than h
+// from every ray inside, in float32 as well (its rounded d1 or d2 exceeds h).
+template <class NS>
+__device__ __forceinline__ void near_set_box(NS& ns, int g, float x1a, float x1b, float x2a, float x2b) {
+  ns.box[g][0] = __double2float_rd(__dsub_rd((double)x1a, kNearPad));
+  ns.box[g][1] = __double2float_ru(__dadd_ru((double)x1b, kNearPad));
+  ns.box[g][2] = __double2float_rd(__dsub_rd((double)x2a, kNearPad));
+  ns.box[g][3] = __double2float_ru(__dadd_ru((double)x2b, kNearPad));
+  ns.n[g] = 0;
+}
+
+// Lists the lenses of the current tile (cnt lenses at l4) that lie inside each group's box.  All
+// threads of the CTA call it; the lists start empty.
+template <class NS>
+__device__ __forceinline__ void near_gather(NS& ns, const float4* l4, int cnt, int nthreads) {
+  const int lane = threadIdx.x & 31;
+  for (int l0 = 0; l0 < cnt; l0 += nthreads) {  // CTA-uniform trip count
+    const int l = l0 + (int)threadIdx.x;
+    float lx = 0.f, ly = 0.f;
+    if (l < cnt) {
+      const float4 L = l4[l];
+      lx = L.x;
+      ly = L.z;
+    }
+#pragma unroll
+    for (int g = 0; g < NS::kGroups; ++g) {
+      const bool in = l < cnt && lx >= ns.box[g][0] && lx <= ns.box[g][1] && ly >= ns.box[g][2] && ly <= ns.box[g][3];
+      const unsigned mask = __ballot_sync(0xffffffffu, in);
+      if (mask != 0u) {
+        const int leader = __ffs(mask) - 1;
+        int base = 0;
+        if (lane == leader) base = atomicAdd(&ns.n[g], __popc(mask));
+        base = __shfl_sync(0xffffffffu, base, leader);
+        if (in) ns.idx[g][base + __popc(mask & ((1u << lane) - 1u))] = (uint16_t)l;
+      }
+    }
+  }
+}
+
+// Near terms of group g's listed lenses of the current tile for the thread's rays (packed pairs X1,
+// X2), folded into the thread's entries of ns.t.
+template <int NP, bool MASS, class NS>
+__device__ __forceinline__ void near_eval(NS& ns, int g, const float4* l4, const float2* m2,
+                                          const uint64_t (&X1)[NP], const uint64_t (&X2)[NP], int nthreads) {
+  const int n = ns.n[g];
+  if (n == 0) return;
+  float x1[2 * NP], x2[2 * NP], t[2 * NP];
+#pragma unroll
+  for (int q = 0; q < NP; ++q) {
+    f2_unpack(X1[q], x1[2 * q], x1[2 * q + 1]);
+    f2_unpack(X2[q], x2[2 * q], x2[2 * q + 1]);
+  }
+#pragma unroll
+  for (int k = 0; k < 2 * NP; ++k) t[k] = ns.t[k * nthreads + threadIdx.x];
+  for (int e = 0; e < n; ++e) {
+    const int l = ns.idx[g][e];
+    const float4 L = l4[l];
+    const float m = MASS ? m2[l].x : 1.f;
+#pragma unroll
+    for (int k = 0; k < 2 * NP; ++k) t[k] = fmaxf(t[k], near_term(x1[k], x2[k], L.x, L.z, m));
+  }
+#pragma unroll
+  for (int k = 0; k < 2 * NP; ++k) ns.t[k * nthreads + threadIdx.x] = t[k];
+}
+
+// T of one ray over every lens of a field (listed-ray kernels): the same value as the shoot's.
+template <bool MASS>
+__device__ __forceinline__ float near_term_all(const FieldDev& f, float x1, float x2) {
+  float t = f.mcap;
+  for (int l = 0; l < f.n_lens; ++l) {
+    const float4 L = __ldg(f.lens4 + l);
+    const float m = MASS ? __ldg(f.mass2 + l).x : 1.f;
+    t = fmaxf(t, near_term(x1, x2, L.x, L.z, m));
+  }
+  return t;
+}
 
 template <int TILE, int ROWS = 1>
 struct __align__(16) LensSmem {
@@ -412,10 +539,12 @@ struct DeflectAcc {
 // so a field split into parts of multiples of 256 lenses, accumulated part after part, gives
 // bitwise the sums of the whole field.  Returns false if a bounded wait gave up (the CTA must then
 // stop; the status word has been set).
-template <int RPT, int TILE, bool MASS, bool ROW, int ROWS>
+// With a near-lens search (NS::kOn), every tile's lenses inside the group boxes of ns are listed and
+// their near terms folded into ns.t (the caller sets the boxes and the thread's ns.t entries).
+template <int RPT, int TILE, bool MASS, bool ROW, int ROWS, class NS = NoNear>
 __device__ __forceinline__ bool deflect_accumulate(const FieldDev& f, const uint64_t (&X1)[RPT / 2],
                                                    const uint64_t (&X2)[RPT / 2], DeflectAcc<RPT / 2>& acc,
-                                                   LensSmem<TILE, ROWS>& sm, PipeState& ps) {
+                                                   LensSmem<TILE, ROWS>& sm, PipeState& ps, NS* ns = nullptr) {
   static_assert(TILE % kGroup == 0 && kGroup % 8 == 0, "lens tile must hold whole lens groups");
   static_assert(kRenorm % kGroup == 0, "renormalisation falls on group boundaries");
   constexpr int NP = RPT / 2;
@@ -442,13 +571,15 @@ __device__ __forceinline__ bool deflect_accumulate(const FieldDev& f, const uint
       ok = false;
       break;
     }
-    if (ROW) {
-      build_row_table<TILE, ROWS>(sm, b);
-      __syncthreads();
-    }
+    const int cnt = min(TILE, n - t * TILE);
+    if constexpr (NS::kOn) near_gather(*ns, &sm.lens4[b][0], cnt, (int)blockDim.x);
+    if (ROW) build_row_table<TILE, ROWS>(sm, b);
+    if (ROW || NS::kOn) __syncthreads();
+    if constexpr (NS::kOn)
+      near_eval<NP, MASS>(*ns, NS::kGroups == 1 ? 0 : (int)(threadIdx.x >> 5), &sm.lens4[b][0], &sm.mass2[b][0], X1,
+                          X2, (int)blockDim.x);
     const uint32_t lbase = smem_u32(&sm.lens4[b][0]);
     const uint32_t mbase = smem_u32(&sm.mass2[b][0]);
-    const int cnt = min(TILE, n - t * TILE);
     int g = 0;
     for (; g + kGroup <= cnt; g += kGroup) {
       uint64_t P1[NP], P2[NP];
@@ -515,8 +646,12 @@ __device__ __forceinline__ bool deflect_accumulate(const FieldDev& f, const uint
         AB[q] = f2_add_x(AB[q], f2_add_x(f2_abs(P1[q]), f2_abs(P2[q])));
       }
     }
-    __syncthreads();  // every thread is done with buffer b and the row table
-    if (threadIdx.x == 0 && t + 2 < ntiles) issue_lens_tile<TILE, MASS>(f, sm, t + 2, b);
+    __syncthreads();  // every thread is done with buffer b, the row table and the near lists
+    if (threadIdx.x == 0) {
+      if constexpr (NS::kOn)
+        for (int g = 0; g < NS::kGroups; ++g) ns->n[g] = 0;
+      if (t + 2 < ntiles) issue_lens_tile<TILE, MASS>(f, sm, t + 2, b);
+    }
   }
   if (!ok) {
     // Record the timeout and drain this CTA's copies still in flight (bounded) before leaving:
@@ -561,11 +696,13 @@ __device__ __forceinline__ void pack_rays(const float (&x1)[RPT], const float (&
   }
 }
 
-template <int RPT, int TILE, bool MASS, bool ROW, int ROWS>
+// Deflection of the thread's rays and, with a near-lens search (the caller set the boxes), the
+// largest-term bound T of every ray (tn); without one, tn = mcap (the caller adds the near terms).
+template <int RPT, int TILE, bool MASS, bool ROW, int ROWS, class NS = NoNear>
 __device__ __forceinline__ bool deflect_pairs(const FieldDev& f, const float (&x1)[RPT], const float (&x2)[RPT],
                                               float (&a1h)[RPT], float (&a1l)[RPT], float (&a2h)[RPT],
-                                              float (&a2l)[RPT], float (&sig)[RPT], LensSmem<TILE, ROWS>& sm,
-                                              PipeState& ps) {
+                                              float (&a2l)[RPT], float (&sig)[RPT], float (&tn)[RPT],
+                                              LensSmem<TILE, ROWS>& sm, PipeState& ps, NS* ns = nullptr) {
   static_assert(RPT % 2 == 0, "rays per thread must be even (packed pairs)");
   constexpr int NP = RPT / 2;
   uint64_t X1[NP], X2[NP];
@@ -573,18 +710,29 @@ __device__ __forceinline__ bool deflect_pairs(const FieldDev& f, const float (&x
   DeflectAcc<NP> acc;
 #pragma unroll
   for (int q = 0; q < NP; ++q) acc.H1[q] = acc.L1[q] = acc.H2[q] = acc.L2[q] = acc.SS[q] = acc.AB[q] = 0ull;
-  if (!deflect_accumulate<RPT, TILE, MASS, ROW, ROWS>(f, X1, X2, acc, sm, ps)) return false;
+  if constexpr (NS::kOn) {
+#pragma unroll
+    for (int k = 0; k < RPT; ++k) ns->t[k * blockDim.x + threadIdx.x] = 0.f;
+  }
+  if (!deflect_accumulate<RPT, TILE, MASS, ROW, ROWS, NS>(f, X1, X2, acc, sm, ps, ns)) return false;
   deflect_finish<RPT>(acc, a1h, a1l, a2h, a2l, sig);
+#pragma unroll
+  for (int k = 0; k < RPT; ++k) {
+    if constexpr (NS::kOn)
+      tn[k] = fmaxf(ns->t[k * blockDim.x + threadIdx.x], f.mcap);
+    else
+      tn[k] = f.mcap;
+  }
   return true;
 }
 
-// As deflect_pairs, with alpha in float64 (hi + lo, exact).
+// As deflect_pairs without a near-lens search, with alpha in float64 (hi + lo, exact).
 template <int RPT, int TILE, bool MASS, bool ROW, int ROWS>
 __device__ __forceinline__ bool deflect(const FieldDev& f, const float (&x1)[RPT], const float (&x2)[RPT],
                                         double (&a1)[RPT], double (&a2)[RPT], float (&sig)[RPT],
                                         LensSmem<TILE, ROWS>& sm, PipeState& ps) {
-  float a1h[RPT], a1l[RPT], a2h[RPT], a2l[RPT];
-  if (!deflect_pairs<RPT, TILE, MASS, ROW, ROWS>(f, x1, x2, a1h, a1l, a2h, a2l, sig, sm, ps)) return false;
+  float a1h[RPT], a1l[RPT], a2h[RPT], a2l[RPT], tn[RPT];
+  if (!deflect_pairs<RPT, TILE, MASS, ROW, ROWS>(f, x1, x2, a1h, a1l, a2h, a2l, sig, tn, sm, ps)) return false;
 #pragma unroll
   for (int k = 0; k < RPT; ++k) {
     a1[k] = (double)a1h[k] + (double)a1l[k];
@@ -595,10 +743,10 @@ __device__ __forceinline__ bool deflect(const FieldDev& f, const float (&x1)[RPT
 
 // Half-width of the band around y within which the float32 path cannot decide the pixel: sig (the
 // safety-scaled random-rounding estimate, the coherent term and the alpha part of a float64
-// evaluation of Eq. 6) plus the lam x part of that rounding.  The shoot's float-float epilogue adds
-// its own rounding bound on top (ff_pixel).
-__device__ __forceinline__ float band_halfwidth(float sig, float lamabs, float x1, float x2) {
-  return sig + 4e-15f * lamabs * (fabsf(x1) + fabsf(x2));
+// evaluation of Eq. 6), the near-lens term of the ray's largest-term bound tn, and the lam x part of
+// the Eq. 6 rounding.  The shoot's float-float epilogue adds its own rounding bound on top (ff_pixel).
+__device__ __forceinline__ float band_halfwidth(float sig, float tn, float lamabs, float x1, float x2) {
+  return sig + kNearScale * tn + 4e-15f * lamabs * (fabsf(x1) + fabsf(x2));
 }
 
 // ----------------------------------------------------------------------------------------------
@@ -653,8 +801,8 @@ __device__ __forceinline__ int ff_pixel(float x, float lh, float ll, float ah, f
 template <int RPT, int STRIDE>
 __device__ __forceinline__ void bin_rays(const ShootDesc& d, const float (&x1)[RPT], const float (&x2)[RPT],
                                          const float (&a1h)[RPT], const float (&a1l)[RPT], const float (&a2h)[RPT],
-                                         const float (&a2l)[RPT], const float (&sig)[RPT], const bool (&valid)[RPT],
-                                         int64_t jrel, int64_t i_base, int lane) {
+                                         const float (&a2l)[RPT], const float (&sig)[RPT], const float (&tn)[RPT],
+                                         const bool (&valid)[RPT], int64_t jrel, int64_t i_base, int lane) {
   unsigned oow_lane = 0;
 #pragma unroll
   for (int k = 0; k < RPT; ++k) {
@@ -670,7 +818,7 @@ __device__ __forceinline__ void bin_rays(const ShootDesc& d, const float (&x1)[R
       // Certain: the band [u - du, u + du] lies inside one pixel of the window, or outside the window
       // on some axis.  Margins: the band in pixel units, the float-float rounding, and 1e-7 for the
       // float rounding of the fraction.
-      const float band = band_halfwidth(sig[k], d.f.lamabs, x1[k], x2[k]);
+      const float band = band_halfwidth(sig[k], tn[k], d.f.lamabs, x1[k], x2[k]);
       const float m1 = band * d.scf0 + eu1 + 1e-7f, m2 = band * d.scf1 + eu2 + 1e-7f;
       // with u = p + f: u + m < 0 iff p <= -2, or p = -1 and 1 - f > m; u - m >= np iff p > np, or
       // p = np and f >= m (margins below 1/2; wider bands are never certain)
@@ -717,9 +865,18 @@ __host__ __device__ __forceinline__ int64_t shoot_tiles(int64_t n_rows, int64_t 
   return ((n_rows + WARPS - 1) / WARPS) * ((n0 + seg - 1) / seg);
 }
 
+// Shared memory of the shoot kernels: lens tiles and row table, and the near-lens search of the
+// CTA's ray box.
+template <int WARPS, int RPT, int TILE>
+struct ShootSmem {
+  LensSmem<TILE, WARPS> lens;
+  NearSmem<TILE, 1, WARPS * 32, RPT> near;
+};
+
 template <int WARPS, int RPT, int TILE, bool MASS>
-__device__ __forceinline__ bool shoot_tile(const ShootDesc& d, int64_t tile, LensSmem<TILE, WARPS>& sm,
+__device__ __forceinline__ bool shoot_tile(const ShootDesc& d, int64_t tile, ShootSmem<WARPS, RPT, TILE>& ss,
                                            PipeState& ps) {
+  LensSmem<TILE, WARPS>& sm = ss.lens;
   constexpr int SEG = 32 * RPT;
   static_assert(SEG <= kMaxSeg, "tile columns fit the shared coordinate row");
   const int64_t ncol = (d.n0 + SEG - 1) / SEG;
@@ -742,6 +899,13 @@ __device__ __forceinline__ bool shoot_tile(const ShootDesc& d, int64_t tile, Len
       sm.x2row[c - SEG] = ray_coord(d.j_begin + jr, d.sp1, d.or1);  // also read by build_row_table
     }
   }
+  if (threadIdx.x == 0) {
+    // the tile's ray box: coordinates grow with the grid index
+    const int64_t ia = tcol * SEG, ib = min(ia + SEG, d.n0) - 1;
+    const int64_t ja = trow * WARPS, jb = min(ja + WARPS, d.n_rows) - 1;
+    near_set_box(ss.near, 0, ray_coord(ia, d.sp0, d.or0), ray_coord(ib, d.sp0, d.or0),
+                 ray_coord(d.j_begin + ja, d.sp1, d.or1), ray_coord(d.j_begin + jb, d.sp1, d.or1));
+  }
   __syncthreads();
   const float x2r = sm.x2row[warp];
   float x1[RPT], x2[RPT];
@@ -753,9 +917,10 @@ __device__ __forceinline__ bool shoot_tile(const ShootDesc& d, int64_t tile, Len
     x1[k] = sm.x1col[lane + 32 * k];
     x2[k] = x2r;
   }
-  float a1h[RPT], a1l[RPT], a2h[RPT], a2l[RPT], sig[RPT];
-  if (!deflect_pairs<RPT, TILE, MASS, true, WARPS>(d.f, x1, x2, a1h, a1l, a2h, a2l, sig, sm, ps)) return false;
-  bin_rays<RPT, 32>(d, x1, x2, a1h, a1l, a2h, a2l, sig, valid, jrel, tcol * SEG + lane, lane);
+  float a1h[RPT], a1l[RPT], a2h[RPT], a2l[RPT], sig[RPT], tn[RPT];
+  if (!deflect_pairs<RPT, TILE, MASS, true, WARPS>(d.f, x1, x2, a1h, a1l, a2h, a2l, sig, tn, sm, ps, &ss.near))
+    return false;
+  bin_rays<RPT, 32>(d, x1, x2, a1h, a1l, a2h, a2l, sig, tn, valid, jrel, tcol * SEG + lane, lane);
   return true;
 }
 

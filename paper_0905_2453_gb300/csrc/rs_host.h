@@ -102,6 +102,8 @@ int recheck_grid(int device);
 // The launch descriptor of a shoot call over rows [row_begin, row_end) (RS_EOVERFLOW beyond 2^32 - 1 rays).
 int fill_desc(const rs_field* f, const rs_ray_grid* g, int64_t row_begin, int64_t row_end, const rs_window* w,
               uint32_t* d_counts, uint64_t* d_oow, rsdev::ShootDesc* d);
+// The field's cap on the term m / r of any lens farther than the near radius from a ray (0 without lenses).
+float near_cap(int64_t n_lens, float m_max);
 // Repack n lenses (xy interleaved, m or null) into the padded layout of n_pad entries.
 cudaError_t launch_pack_lenses(const float* xy, const float* m, int64_t n, int64_t n_pad, float4* lens4,
                                float2* mass2, int blocks, cudaStream_t s);

@@ -2,6 +2,7 @@
 // translation units (rs_shoot.cu, rs_batch.cu).  Not part of the public ABI.
 #pragma once
 
+#include <atomic>
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -22,6 +23,21 @@ constexpr int kNumCfg = 6;
 constexpr KernelCfg kCfgs[kNumCfg] = {{64, 8}, {128, 4}, {128, 8}, {256, 4}, {256, 8}, {256, 6}};
 constexpr int kDefaultCfg = 2;
 
+// Dynamic shared memory beyond 48 KiB per CTA needs a one-time opt-in per kernel and device.
+template <auto Kernel>
+cudaError_t smem_opt_in(size_t bytes) {
+  if (bytes <= ((size_t)48 << 10)) return cudaSuccess;
+  static std::atomic<unsigned long long> done{0};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  const unsigned long long bit = 1ull << (dev & 63);
+  if (done.load() & bit) return cudaSuccess;
+  e = cudaFuncSetAttribute(Kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e == cudaSuccess) done.fetch_or(bit);
+  return e;
+}
+
 inline int find_cfg(int block, int rpt) {
   for (int i = 0; i < kNumCfg; ++i)
     if (kCfgs[i].block == block && kCfgs[i].rpt == rpt) return i;
@@ -30,6 +46,8 @@ inline int find_cfg(int block, int rpt) {
 
 // Plain launch: one CTA per ray tile of block * rpt rays.
 cudaError_t launch_shoot(int cfg, const rsdev::ShootDesc& d, cudaStream_t s);
+// Resident CTAs per SM of the plain shoot kernel of launch shape cfg.
+cudaError_t shoot_blocks_per_sm(int cfg, bool mass, int* blocks);
 
 // Listed rays -> source positions (and deflections, and band half-widths), float32 path.
 cudaError_t launch_trace(const rsdev::FieldDev& f, double or0, double or1, double sp0, double sp1,

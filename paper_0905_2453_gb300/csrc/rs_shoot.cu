@@ -10,10 +10,11 @@ using namespace rsdev;
 // default allocation, which spills); eight-warp CTAs keep the default allocation.
 template <int WARPS, int RPT, int TILE, bool MASS>
 __global__ void __launch_bounds__(WARPS * 32, WARPS <= 4 ? 2 : 1) shoot_kernel(const ShootDesc d) {
-  __shared__ LensSmem<TILE, WARPS> sm;
+  extern __shared__ __align__(128) unsigned char rs_smem[];
+  auto& ss = *reinterpret_cast<ShootSmem<WARPS, RPT, TILE>*>(rs_smem);
   PipeState ps;
-  pipe_init(sm.bar, ps);
-  (void)shoot_tile<WARPS, RPT, TILE, MASS>(d, (int64_t)blockIdx.x, sm, ps);
+  pipe_init(ss.lens.bar, ps);
+  (void)shoot_tile<WARPS, RPT, TILE, MASS>(d, (int64_t)blockIdx.x, ss, ps);
 }
 
 template <int BLOCK, int RPT, int TILE, bool MASS>
@@ -50,11 +51,23 @@ __global__ void __launch_bounds__(BLOCK)
       alpha[2 * r + 1] = a2[q];
     }
     if (err != nullptr) {
-      const double b = (double)band_halfwidth(sig[q], f.lamabs, x1[q], x2[q]);
+      // the ray's largest-term bound over every lens: the value the shoot kernels reach through
+      // their near-lens search
+      const float tn = near_term_all<MASS>(f, x1[q], x2[q]);
+      const double b = (double)band_halfwidth(sig[q], tn, f.lamabs, x1[q], x2[q]);
       err[2 * r] = b;
       err[2 * r + 1] = b;
     }
   }
+}
+
+template <int WARPS, int RPT, bool MASS>
+cudaError_t launch_shoot_m(const ShootDesc& d, int64_t grid, cudaStream_t s) {
+  constexpr size_t smem = sizeof(ShootSmem<WARPS, RPT, rsint::kTile>);
+  cudaError_t e = rsint::smem_opt_in<shoot_kernel<WARPS, RPT, rsint::kTile, MASS>>(smem);
+  if (e != cudaSuccess) return e;
+  shoot_kernel<WARPS, RPT, rsint::kTile, MASS><<<(unsigned)grid, WARPS * 32, smem, s>>>(d);
+  return cudaGetLastError();
 }
 
 template <int WARPS, int RPT>
@@ -62,16 +75,38 @@ cudaError_t launch_shoot_t(const ShootDesc& d, cudaStream_t s) {
   const int64_t grid = shoot_tiles<WARPS, RPT>(d.n_rows, d.n0);
   if (grid <= 0) return cudaSuccess;
   if (grid >= ((int64_t)1 << 31)) return cudaErrorInvalidValue;
-  if (d.f.has_mass)
-    shoot_kernel<WARPS, RPT, rsint::kTile, true><<<(unsigned)grid, WARPS * 32, 0, s>>>(d);
-  else
-    shoot_kernel<WARPS, RPT, rsint::kTile, false><<<(unsigned)grid, WARPS * 32, 0, s>>>(d);
-  return cudaGetLastError();
+  return d.f.has_mass ? launch_shoot_m<WARPS, RPT, true>(d, grid, s) : launch_shoot_m<WARPS, RPT, false>(d, grid, s);
+}
+
+template <int WARPS, int RPT, bool MASS>
+cudaError_t occupancy_m(int* blocks) {
+  constexpr size_t smem = sizeof(ShootSmem<WARPS, RPT, rsint::kTile>);
+  cudaError_t e = rsint::smem_opt_in<shoot_kernel<WARPS, RPT, rsint::kTile, MASS>>(smem);
+  if (e != cudaSuccess) return e;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, shoot_kernel<WARPS, RPT, rsint::kTile, MASS>,
+                                                       WARPS * 32, smem);
+}
+
+template <int WARPS, int RPT>
+cudaError_t occupancy_t(bool mass, int* blocks) {
+  return mass ? occupancy_m<WARPS, RPT, true>(blocks) : occupancy_m<WARPS, RPT, false>(blocks);
 }
 
 }  // namespace
 
 namespace rsint {
+
+cudaError_t shoot_blocks_per_sm(int cfg, bool mass, int* blocks) {
+  switch (cfg) {
+    case 0: return occupancy_t<2, 8>(mass, blocks);
+    case 1: return occupancy_t<4, 4>(mass, blocks);
+    case 2: return occupancy_t<4, 8>(mass, blocks);
+    case 3: return occupancy_t<8, 4>(mass, blocks);
+    case 4: return occupancy_t<8, 8>(mass, blocks);
+    case 5: return occupancy_t<8, 6>(mass, blocks);
+    default: return cudaErrorInvalidValue;
+  }
+}
 
 cudaError_t launch_shoot(int cfg, const rsdev::ShootDesc& d, cudaStream_t s) {
   switch (cfg) {

@@ -1,10 +1,10 @@
 // Lens-partitioned ("staged") shooting, the billion-lens scheme of Section 3.3: the deflection of
 // every ray is summed over the lenses of one partition at a time, the partially deflected rays
 // carried between passes, and the rays are mapped and binned after the last partition.  The carried
-// state is the shoot kernel's own per-ray accumulators (two-float alpha sums and error-band sums),
-// so with partitions of multiples of 256 lenses the final sums are bitwise those of one pass over
-// all lenses.  Certified binning re-evaluates the listed rays in float-float, again partition by
-// partition.
+// state is the shoot kernel's own per-ray accumulators (two-float alpha sums and error-band sums)
+// and the ray's largest-term bound so far (a maximum over partitions), so with partitions of
+// multiples of 256 lenses the final sums and bands are bitwise those of one pass over all lenses.
+// Certified binning re-evaluates the listed rays in float-float, again partition by partition.
 #include "rs_ff.cuh"
 #include "rs_internal.h"
 
@@ -13,13 +13,15 @@ namespace {
 using namespace rsdev;
 
 constexpr int kWarps = 4, kRpt = 8, kNp = kRpt / 2, kBlock = kWarps * 32;
+constexpr int kStateWords = 7;  // per ray pair: H1, L1, H2, L2, SS, AB (packed pairs), T (a float pair)
 
-// State layout: word k (0..6*kNp-1) of thread t of tile T at state[(T * 6 * kNp + k) * kBlock + t],
-// coalesced across the threads of a CTA.
-__device__ __forceinline__ void state_io(uint64_t* __restrict__ st, DeflectAcc<kNp>& a, bool store) {
-  uint64_t* w[6] = {a.H1, a.L1, a.H2, a.L2, a.SS, a.AB};
+// State layout: word k (0 .. kStateWords * kNp - 1) of thread t of tile T at
+// state[(T * kStateWords * kNp + k) * kBlock + t], coalesced across the threads of a CTA.
+__device__ __forceinline__ void state_io(uint64_t* __restrict__ st, DeflectAcc<kNp>& a, uint64_t (&tn)[kNp],
+                                         bool store) {
+  uint64_t* w[kStateWords] = {a.H1, a.L1, a.H2, a.L2, a.SS, a.AB, tn};
 #pragma unroll
-  for (int k = 0; k < 6; ++k)
+  for (int k = 0; k < kStateWords; ++k)
 #pragma unroll
     for (int q = 0; q < kNp; ++q) {
       uint64_t* p = st + (size_t)(k * kNp + q) * kBlock;
@@ -30,10 +32,14 @@ __device__ __forceinline__ void state_io(uint64_t* __restrict__ st, DeflectAcc<k
     }
 }
 
+using StagedSmem = ShootSmem<kWarps, kRpt, rsint::kTile>;
+
 template <bool MASS>
 __global__ void __launch_bounds__(kBlock, 2) staged_kernel(const ShootDesc d, uint64_t* __restrict__ state, int first,
                                                            int last) {
-  __shared__ LensSmem<rsint::kTile, kWarps> sm;
+  extern __shared__ __align__(128) unsigned char rs_smem[];
+  auto& ss = *reinterpret_cast<StagedSmem*>(rs_smem);
+  LensSmem<rsint::kTile, kWarps>& sm = ss.lens;
   PipeState ps;
   pipe_init(sm.bar, ps);
   constexpr int SEG = 32 * kRpt;
@@ -57,24 +63,42 @@ __global__ void __launch_bounds__(kBlock, 2) staged_kernel(const ShootDesc d, ui
     x2[k] = x2r;
   }
   if (lane == 0) sm.x2row[warp] = x2r;
+  if (threadIdx.x == 0) {
+    const int64_t ia = tcol * SEG, ib = min(ia + SEG, d.n0) - 1;
+    const int64_t ja = trow * kWarps, jb = min(ja + kWarps, d.n_rows) - 1;
+    near_set_box(ss.near, 0, ray_coord(ia, d.sp0, d.or0), ray_coord(ib, d.sp0, d.or0),
+                 ray_coord(d.j_begin + ja, d.sp1, d.or1), ray_coord(d.j_begin + jb, d.sp1, d.or1));
+  }
   uint64_t X1[kNp], X2[kNp];
   pack_rays<kRpt>(x1, x2, X1, X2);
   DeflectAcc<kNp> acc;
-  uint64_t* st = state + (size_t)tile * 6 * kNp * kBlock + threadIdx.x;
+  uint64_t tp[kNp];  // largest-term bound of each ray pair over the partitions so far
+  uint64_t* st = state + (size_t)tile * kStateWords * kNp * kBlock + threadIdx.x;
   if (first) {
 #pragma unroll
-    for (int q = 0; q < kNp; ++q) acc.H1[q] = acc.L1[q] = acc.H2[q] = acc.L2[q] = acc.SS[q] = acc.AB[q] = 0ull;
+    for (int q = 0; q < kNp; ++q) acc.H1[q] = acc.L1[q] = acc.H2[q] = acc.L2[q] = acc.SS[q] = acc.AB[q] = tp[q] = 0ull;
   } else {
-    state_io(st, acc, false);
+    state_io(st, acc, tp, false);
   }
-  if (!deflect_accumulate<kRpt, rsint::kTile, MASS, true, kWarps>(d.f, X1, X2, acc, sm, ps)) return;
+#pragma unroll
+  for (int k = 0; k < kRpt; ++k) ss.near.t[k * kBlock + threadIdx.x] = 0.f;
+  __syncthreads();  // the box and the row coordinates are set
+  if (!deflect_accumulate<kRpt, rsint::kTile, MASS, true, kWarps>(d.f, X1, X2, acc, sm, ps, &ss.near)) return;
+  float tn[kRpt];
+#pragma unroll
+  for (int q = 0; q < kNp; ++q) {
+    f2_unpack(tp[q], tn[2 * q], tn[2 * q + 1]);
+    tn[2 * q] = fmaxf(tn[2 * q], fmaxf(ss.near.t[(2 * q) * kBlock + threadIdx.x], d.f.mcap));
+    tn[2 * q + 1] = fmaxf(tn[2 * q + 1], fmaxf(ss.near.t[(2 * q + 1) * kBlock + threadIdx.x], d.f.mcap));
+    tp[q] = f2_pack(tn[2 * q], tn[2 * q + 1]);
+  }
   if (!last) {
-    state_io(st, acc, true);
+    state_io(st, acc, tp, true);
     return;
   }
   float a1h[kRpt], a1l[kRpt], a2h[kRpt], a2l[kRpt], sig[kRpt];
   deflect_finish<kRpt>(acc, a1h, a1l, a2h, a2l, sig);
-  bin_rays<kRpt, 32>(d, x1, x2, a1h, a1l, a2h, a2l, sig, valid, jrel, tcol * SEG + lane, lane);
+  bin_rays<kRpt, 32>(d, x1, x2, a1h, a1l, a2h, a2l, sig, tn, valid, jrel, tcol * SEG + lane, lane);
 }
 
 // ---- float-float re-evaluation of the listed rays, partition by partition ----------------------
@@ -151,18 +175,25 @@ namespace rsint {
 int64_t staged_tiles(int64_t n_rows, int64_t n0) { return shoot_tiles<kWarps, kRpt>(n_rows, n0); }
 
 size_t staged_state_bytes(int64_t n_rows, int64_t n0) {
-  return (size_t)staged_tiles(n_rows, n0) * 6 * kNp * kBlock * sizeof(uint64_t);
+  return (size_t)staged_tiles(n_rows, n0) * kStateWords * kNp * kBlock * sizeof(uint64_t);
+}
+
+template <bool MASS>
+cudaError_t launch_staged_m(const rsdev::ShootDesc& d, uint64_t* state, bool first, bool last, int64_t grid,
+                            cudaStream_t s) {
+  constexpr size_t smem = sizeof(StagedSmem);
+  cudaError_t e = smem_opt_in<staged_kernel<MASS>>(smem);
+  if (e != cudaSuccess) return e;
+  staged_kernel<MASS><<<(unsigned)grid, kBlock, smem, s>>>(d, state, first ? 1 : 0, last ? 1 : 0);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_staged(const rsdev::ShootDesc& d, uint64_t* state, bool first, bool last, cudaStream_t s) {
   const int64_t grid = staged_tiles(d.n_rows, d.n0);
   if (grid <= 0) return cudaSuccess;
   if (grid >= ((int64_t)1 << 31)) return cudaErrorInvalidValue;
-  if (d.f.has_mass)
-    staged_kernel<true><<<(unsigned)grid, kBlock, 0, s>>>(d, state, first ? 1 : 0, last ? 1 : 0);
-  else
-    staged_kernel<false><<<(unsigned)grid, kBlock, 0, s>>>(d, state, first ? 1 : 0, last ? 1 : 0);
-  return cudaGetLastError();
+  return d.f.has_mass ? launch_staged_m<true>(d, state, first, last, grid, s)
+                      : launch_staged_m<false>(d, state, first, last, grid, s);
 }
 
 cudaError_t launch_recheck_part(const rsdev::ShootDesc& d, const uint2* list, const unsigned int* count,

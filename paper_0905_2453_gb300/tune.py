@@ -36,13 +36,21 @@ def cache_key(field, grid) -> str:
             f"|n0=2^{_bucket(int(grid.n[0]))}")
 
 
-def wave_rows(n0: int, block: int, rpt: int, sms: int) -> int:
+def wave_rows(n0: int, block: int, rpt: int, sms: int, ctas_per_sm: int = 2) -> int:
     """The smallest number of grid rows whose CTAs (of `block` threads x `rpt` rays per thread, one warp per
-    row and 32 x rpt columns per CTA) fill whole waves of 2 x sms CTAs: whole waves at one or two resident
-    CTAs per SM (every launch shape of the library)."""
+    row and 32 x rpt columns per CTA) fill whole waves of ctas_per_sm x sms CTAs (the default, two resident
+    CTAs per SM, makes whole waves at one or two)."""
     warps, seg = block // 32, 32 * rpt
     cpr = -(-int(n0) // seg)  # CTAs per group of `warps` rows
-    return (2 * sms) // math.gcd(2 * sms, cpr) * warps
+    wave = int(ctas_per_sm) * int(sms)
+    return wave // math.gcd(wave, cpr) * warps
+
+
+def shape_rates(field, grid, cache_path: str = None) -> dict:
+    """Steady-state interactions/s of every launch shape from the tuner's cache entry for (field, grid)
+    ({} if the pair was never tuned)."""
+    cache = _load(cache_path or os.environ.get("RS_TUNE_CACHE", DEFAULT_CACHE))
+    return dict(cache.get(cache_key(field, grid), {}).get("interactions_per_s", {}))
 
 
 def _load(path):

@@ -23,6 +23,17 @@ def test_reference_arm_json_line():
     assert line["config"]["workload"].startswith("tiny") and line["config"]["n_lens"] == 100
 
 
+def test_reference_arm_samples_rays_of_large_workloads():
+    """A workload whose grid rows are too costly for the oracle (1e6 lenses, 16384 rays per row) is sampled
+    on random rays of its grid, new ones every step."""
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--workload", "n1e6",
+                        "--steps", "1", "--warmup", "3"], capture_output=True, text=True, timeout=900, cwd=ROOT)
+    assert r.returncode == 0, r.stderr[-2000:]
+    line = json.loads(r.stdout.strip().splitlines()[-1])
+    assert line["value"] > 0 and "random rays" in line["cpu_baseline"]["sample"]
+    assert line["config"]["n_lens"] == 1_000_000 and line["config"]["ray_grid"] == [16384, 16384]
+
+
 def test_warmup_below_three_is_refused():
     r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
                         "--warmup", "2"], capture_output=True, text=True, timeout=120, cwd=ROOT)
