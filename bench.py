@@ -275,33 +275,40 @@ def headline_rows(rs, spec, field, sms, stream, launch_shape=None):
     from paper_0905_2453_gb300 import tune
     n_lens, weighted = field.info()
     if launch_shape:
-        b, r = (int(v) for v in launch_shape.split("x"))
-        rs.rs_set_launch_config(weighted, b, r)
+        shape = parse_shape(launch_shape)
+        rs.rs_set_launch_config(weighted, *shape)
         rates = {}
     else:
-        b, r, _ = tune.autotune(field, spec.grid, spec.window, stream=stream)
+        shape = tuple(tune.autotune(field, spec.grid, spec.window, stream=stream)[:3])
         rates = tune.shape_rates(field, spec.grid)
     n0, n1 = int(spec.grid.n[0]), int(spec.grid.n[1])
     if spec.interactions <= FULL_LIMIT:
-        return 0, n1, (b, r), "whole grid"
+        return 0, n1, shape, "whole grid"
 
-    def unit_of(shape):
-        occ = rs.rs_launch_occupancy(weighted, *shape)
-        return tune.wave_rows(n0, shape[0], shape[1], sms, occ), occ
+    def unit_of(sh):
+        occ = rs.rs_launch_occupancy(weighted, *sh)
+        return tune.wave_rows(n0, sh[0], sh[1], sms, occ), occ
 
-    best = rates.get(f"{b}x{r}")
-    cands = [(b, r)]
+    best = rates.get("x".join(str(v) for v in shape))
+    cands = [shape]
     if best:
-        cands += [tuple(int(v) for v in k.split("x")) for k, v in rates.items() if v >= 0.99 * best]
-    b, r = min(cands, key=lambda sh: (unit_of(sh)[0], cands.index(sh)))
-    rs.rs_set_launch_config(weighted, b, r)
-    unit, occ = unit_of((b, r))
+        cands += [parse_shape(k) for k, v in rates.items() if v >= 0.99 * best]
+    shape = min(cands, key=lambda sh: (unit_of(sh)[0], cands.index(sh)))
+    b, r, _ = shape
+    rs.rs_set_launch_config(weighted, *shape)
+    unit, occ = unit_of(shape)
     warps = b // 32
     r0 = (n1 - unit) // 2 // warps * warps
     ctas = -(-n0 // (32 * r)) * (unit // warps)
     note = (f"central rows [{r0}, {r0 + unit}) of the {n0} x {n1} grid: {ctas} CTAs of {b} threads = "
             f"{ctas // (occ * sms)} whole wave(s) of {occ} CTAs x {sms} SMs")
-    return r0, r0 + unit, (b, r), note
+    return r0, r0 + unit, shape, note
+
+
+def parse_shape(text):
+    """'128x8x512' (threads x rays per thread x lens tile; the tile defaults to 256) -> (128, 8, 512)."""
+    v = [int(x) for x in text.split("x")]
+    return (v[0], v[1], v[2] if len(v) > 2 else 256)
 
 
 def oracle_sample_rate(spec, target_s: float):
@@ -359,6 +366,8 @@ def run_ours(args):
     field = rs.Field.from_spec(spec, stream)
     sms, max_mhz = peaks(local)
     r0, r1, shape, rows_note = headline_rows(rs, spec, field, sms, stream, args.launch_shape)
+    from paper_0905_2453_gb300 import tune
+    rates_headline = {} if args.launch_shape else tune.shape_rates(field, spec.grid)
     npix = (int(spec.window.npix[1]), int(spec.window.npix[0]))
     counts = torch.zeros(npix, dtype=torch.int32, device=device)
     oow = torch.zeros(1, dtype=torch.int64, device=device)
@@ -430,7 +439,7 @@ def run_ours(args):
             f.close()
 
         e2e_step()
-        n_e2e = max(3, min(args.steps, 20 if inter_step <= FULL_LIMIT else 3))
+        n_e2e = max(2, min(args.steps, 20 if inter_step <= FULL_LIMIT else 2))
         barrier()
         torch.cuda.synchronize(device)
         t0 = time.perf_counter()
@@ -504,7 +513,10 @@ def run_ours(args):
     cfg["l2"] = ("inputs larger than L2 (lenses: %.2f GB on the device); L2 also flushed between steps (512 MiB "
                  "write)" % (spec.n_lens * (24 if spec.masses is not None else 16) / 1e9)
                  if spec.n_lens * 16 > (129 << 20) else "flushed between timed steps (512 MiB write)")
-    cfg["launch_shape"] = f"{shape[0]} threads x {shape[1]} rays/thread" + ("" if args.launch_shape else " (autotuned)")
+    cfg["launch_shape"] = (f"{shape[0]} threads x {shape[1]} rays/thread x {shape[2]}-lens tiles"
+                           + ("" if args.launch_shape else " (autotuned)"))
+    if rates_headline:
+        cfg["tuner_rates"] = rates_headline
     cfg["certified_binning"] = rs.rs_get_certified_binning()
     rl.update({"kernel": "shoot_kernel (span of rs_shoot_rows: list reset, shoot, certified re-evaluation)",
                "kernel_ms": shoot_avg_s * 1e3,
@@ -767,8 +779,8 @@ def run_section(args):
     if args.section == "zoom":
         spec = workload(args.workload, seed=0)
         if args.launch_shape:
-            b_, r_ = (int(v) for v in args.launch_shape.split("x"))
-            rs.rs_set_launch_config(spec.masses is not None and not bool(np.all(spec.masses == 1.0)), b_, r_)
+            rs.rs_set_launch_config(spec.masses is not None and not bool(np.all(spec.masses == 1.0)),
+                                    *parse_shape(args.launch_shape))
         out = {"zoom": run_zoom(rs, torch, device, stream, spec),
                "culled_full_map": run_zoom(rs, torch, device, stream, spec, factor=1, quarter=False)}
     elif args.section == "batch-small":
@@ -923,10 +935,10 @@ def run_configs(rs, torch, device, stream, names, cpu=True, full_limit=2e12, max
         f = rs.Field.from_spec(spec, stream)
         n_lens, weighted = f.info()
         if launch_shape:
-            b, r = (int(v) for v in launch_shape.split("x"))
-            rs.rs_set_launch_config(weighted, b, r)
+            b, r, t = parse_shape(launch_shape)
+            rs.rs_set_launch_config(weighted, b, r, t)
         else:
-            b, r, _ = tune.autotune(f, spec.grid, spec.window, stream=stream)
+            b, r, t, _ = tune.autotune(f, spec.grid, spec.window, stream=stream)
         n0, n1 = int(spec.grid.n[0]), int(spec.grid.n[1])
         npix = (int(spec.window.npix[1]), int(spec.window.npix[0]))
         c = torch.zeros(npix, dtype=torch.int32, device=device)
@@ -956,7 +968,8 @@ def run_configs(rs, torch, device, stream, names, cpu=True, full_limit=2e12, max
             return ms
 
         entry = {"workload": spec.name, "n_lens": n_lens, "weighted_kernels": bool(weighted),
-                 "launch_shape": f"{b}x{r}", "full_grid_interactions": spec.interactions}
+                 "launch_shape": f"{b}x{r}x{t}", "full_grid_interactions": spec.interactions,
+                 "tuner_rates": tune.shape_rates(f, spec.grid)}
         if spec.interactions <= full_limit:
             ms = timed(0, n1)
             rate = spec.interactions / (ms / 1e3)
@@ -1023,7 +1036,8 @@ def main():
     ap.add_argument("--batch-reps", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
-    ap.add_argument("--launch-shape", default=None, help="fix the launch shape, e.g. 128x8 (skips the autotuner)")
+    ap.add_argument("--launch-shape", default=None,
+                    help="fix the launch shape, e.g. 128x8x512 (threads x rays/thread x lens tile; skips the autotuner)")
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")

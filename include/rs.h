@@ -314,20 +314,22 @@ int rs_field_status(rs_field_t f, int clear, int* status);
 
 /*
  * Launch shapes.  The library carries kernels for several (threads per CTA,
- * rays per thread) shapes; all compute bitwise identical results, so the
- * choice only affects speed.  rs_set_launch_config selects the shape used by
- * rs_shoot / rs_shoot_rows (and, for has_masses = 1, by batches planned
- * afterwards) for fields without (has_masses = 0) or with per-lens masses.
- * rs_launch_configs lists the compiled shapes: up to `cap` (block, rpt)
- * pairs into `pairs` (int[2*cap]); returns the number available via *count.
+ * rays per thread, lenses per shared-memory stage) shapes (Section 2.2's choice
+ * of threads per block, widened); all compute bitwise identical results (the
+ * lens tile is a multiple of the 256-lens summation period), so the choice
+ * only affects speed.  rs_set_launch_config selects the shape used by
+ * rs_shoot / rs_shoot_rows / rs_shoot_rows_noalloc (and by batches planned
+ * afterwards) for fields without (has_masses = 0) or with per-lens masses;
+ * RS_EINVAL for a shape that is not compiled.  rs_launch_configs lists the
+ * compiled shapes: up to `cap` (block, rpt, lens_tile) triples into `triples`
+ * (int[3*cap]); returns the number available via *count.
  * rs_launch_occupancy reports how many CTAs of a shape's shoot kernel are
- * resident per SM on the current device (SMs x that = one wave of CTAs);
- * RS_EINVAL for a shape that is not compiled.
+ * resident per SM on the current device (SMs x that = one wave of CTAs).
  */
-int rs_set_launch_config(int has_masses, int block, int rays_per_thread);
-int rs_get_launch_config(int has_masses, int* block, int* rays_per_thread);
-int rs_launch_configs(int* pairs, int cap, int* count);
-int rs_launch_occupancy(int has_masses, int block, int rays_per_thread, int* ctas_per_sm);
+int rs_set_launch_config(int has_masses, int block, int rays_per_thread, int lens_tile);
+int rs_get_launch_config(int has_masses, int* block, int* rays_per_thread, int* lens_tile);
+int rs_launch_configs(int* triples, int cap, int* count);
+int rs_launch_occupancy(int has_masses, int block, int rays_per_thread, int lens_tile, int* ctas_per_sm);
 
 /*
  * Light curves (Section 1: a source of finite size moves across the magnification map; the

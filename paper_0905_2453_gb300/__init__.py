@@ -157,10 +157,10 @@ def load():
         "rs_last_error": ([], ctypes.c_char_p),
         "rs_version": ([], ctypes.c_char_p),
         "rs_device_code_version": ([ctypes.POINTER(i32)], i32),
-        "rs_set_launch_config": ([i32, i32, i32], i32),
-        "rs_get_launch_config": ([i32, ctypes.POINTER(i32), ctypes.POINTER(i32)], i32),
+        "rs_set_launch_config": ([i32, i32, i32, i32], i32),
+        "rs_get_launch_config": ([i32, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32)], i32),
         "rs_launch_configs": ([ctypes.POINTER(i32), i32, ctypes.POINTER(i32)], i32),
-        "rs_launch_occupancy": ([i32, i32, i32, ctypes.POINTER(i32)], i32),
+        "rs_launch_occupancy": ([i32, i32, i32, i32, ctypes.POINTER(i32)], i32),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -583,30 +583,32 @@ def rs_field_status(handle: int, clear: bool = False) -> int:
     return int(st.value)
 
 
-def rs_set_launch_config(has_masses: bool, block: int, rays_per_thread: int) -> None:
-    _check(load().rs_set_launch_config(1 if has_masses else 0, int(block), int(rays_per_thread)),
+def rs_set_launch_config(has_masses: bool, block: int, rays_per_thread: int, lens_tile: int = 256) -> None:
+    _check(load().rs_set_launch_config(1 if has_masses else 0, int(block), int(rays_per_thread), int(lens_tile)),
            "rs_set_launch_config")
 
 
 def rs_get_launch_config(has_masses: bool):
-    b, r = ctypes.c_int(), ctypes.c_int()
-    _check(load().rs_get_launch_config(1 if has_masses else 0, ctypes.byref(b), ctypes.byref(r)),
+    """(block, rays_per_thread, lens_tile) of the mass mode's current launch shape."""
+    b, r, t = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _check(load().rs_get_launch_config(1 if has_masses else 0, ctypes.byref(b), ctypes.byref(r), ctypes.byref(t)),
            "rs_get_launch_config")
-    return int(b.value), int(r.value)
+    return int(b.value), int(r.value), int(t.value)
 
 
 def rs_launch_configs():
+    """The compiled launch shapes as (block, rays_per_thread, lens_tile) triples."""
     cnt = ctypes.c_int()
-    buf = (ctypes.c_int * 64)()
+    buf = (ctypes.c_int * 96)()
     _check(load().rs_launch_configs(buf, 32, ctypes.byref(cnt)), "rs_launch_configs")
-    return [(buf[2 * i], buf[2 * i + 1]) for i in range(min(cnt.value, 32))]
+    return [(buf[3 * i], buf[3 * i + 1], buf[3 * i + 2]) for i in range(min(cnt.value, 32))]
 
 
-def rs_launch_occupancy(has_masses: bool, block: int, rays_per_thread: int) -> int:
+def rs_launch_occupancy(has_masses: bool, block: int, rays_per_thread: int, lens_tile: int = 256) -> int:
     """Resident CTAs per SM of a launch shape's shoot kernel on the current device."""
     v = ctypes.c_int(0)
-    _check(load().rs_launch_occupancy(int(bool(has_masses)), int(block), int(rays_per_thread), ctypes.byref(v)),
-           "rs_launch_occupancy")
+    _check(load().rs_launch_occupancy(int(bool(has_masses)), int(block), int(rays_per_thread), int(lens_tile),
+                                      ctypes.byref(v)), "rs_launch_occupancy")
     return int(v.value)
 
 

@@ -272,34 +272,40 @@ int rs_device_code_version(int* binary_version) {
   return RS_OK;
 }
 
-int rs_set_launch_config(int has_masses, int block, int rays_per_thread) {
-  const int c = rsint::find_cfg(block, rays_per_thread);
-  if (c < 0) return fail(RS_EINVAL, "no compiled launch shape (%d threads, %d rays/thread)", block, rays_per_thread);
+int rs_set_launch_config(int has_masses, int block, int rays_per_thread, int lens_tile) {
+  const int c = rsint::find_cfg(block, rays_per_thread, lens_tile);
+  if (c < 0)
+    return fail(RS_EINVAL, "no compiled launch shape (%d threads, %d rays/thread, %d-lens tiles)", block,
+                rays_per_thread, lens_tile);
   g_cfg[has_masses ? 1 : 0] = c;
   return RS_OK;
 }
 
-int rs_get_launch_config(int has_masses, int* block, int* rays_per_thread) {
+int rs_get_launch_config(int has_masses, int* block, int* rays_per_thread, int* lens_tile) {
   const int c = g_cfg[has_masses ? 1 : 0];
   if (block) *block = rsint::kCfgs[c].block;
   if (rays_per_thread) *rays_per_thread = rsint::kCfgs[c].rpt;
+  if (lens_tile) *lens_tile = rsint::kCfgs[c].tile;
   return RS_OK;
 }
 
-int rs_launch_occupancy(int has_masses, int block, int rays_per_thread, int* ctas_per_sm) {
+int rs_launch_occupancy(int has_masses, int block, int rays_per_thread, int lens_tile, int* ctas_per_sm) {
   if (!ctas_per_sm) return fail(RS_EINVAL, "ctas_per_sm is NULL");
-  const int c = rsint::find_cfg(block, rays_per_thread);
-  if (c < 0) return fail(RS_EINVAL, "no compiled launch shape (%d threads, %d rays/thread)", block, rays_per_thread);
+  const int c = rsint::find_cfg(block, rays_per_thread, lens_tile);
+  if (c < 0)
+    return fail(RS_EINVAL, "no compiled launch shape (%d threads, %d rays/thread, %d-lens tiles)", block,
+                rays_per_thread, lens_tile);
   cudaError_t e = rsint::shoot_blocks_per_sm(c, has_masses != 0, ctas_per_sm);
   if (e != cudaSuccess) return cuda_fail(e, "occupancy query");
   return RS_OK;
 }
 
-int rs_launch_configs(int* pairs, int cap, int* count) {
+int rs_launch_configs(int* triples, int cap, int* count) {
   if (count) *count = rsint::kNumCfg;
-  for (int i = 0; i < rsint::kNumCfg && i < cap && pairs; ++i) {
-    pairs[2 * i] = rsint::kCfgs[i].block;
-    pairs[2 * i + 1] = rsint::kCfgs[i].rpt;
+  for (int i = 0; i < rsint::kNumCfg && i < cap && triples; ++i) {
+    triples[3 * i] = rsint::kCfgs[i].block;
+    triples[3 * i + 1] = rsint::kCfgs[i].rpt;
+    triples[3 * i + 2] = rsint::kCfgs[i].tile;
   }
   return RS_OK;
 }
@@ -454,8 +460,9 @@ int rs_destroy_field(rs_field_t f) {
   return RS_OK;
 }
 
-static_assert(rsdev::kRenorm % rsint::kTile == 0 && rsdev::kLensPad % rsint::kTile == 0,
-              "view ranges start on lens-tile boundaries");
+// a view starts on a summation-period boundary (the group and renormalisation schedule then runs as in
+// its parent); its lens tiles are copied exactly (rounded up to an even count), inside the parent's padding
+static_assert(rsdev::kLensPad % 2 == 0 && rsdev::kRenorm % rsdev::kGroup == 0, "views on period boundaries");
 
 int rs_create_field_view(rs_field_t parent, int64_t lens_begin, int64_t n_lens, rs_field_t* out) {
   if (!out) return fail(RS_EINVAL, "out is NULL");

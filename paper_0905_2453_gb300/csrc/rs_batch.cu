@@ -43,35 +43,35 @@ __global__ void __launch_bounds__(WARPS * 32, WARPS <= 4 ? 2 : 1)
   }
 }
 
-template <int WARPS, int RPT, bool MASS>
+template <int WARPS, int RPT, int TILE, bool MASS>
 cudaError_t launch_batch_m(const ShootDesc* descs, const int2* items, int n_items, int* counter, int grid,
                            cudaStream_t s) {
-  constexpr size_t smem = sizeof(ShootSmem<WARPS, RPT, rsint::kTile>);
-  cudaError_t e = rsint::smem_opt_in<batch_kernel<WARPS, RPT, rsint::kTile, MASS>>(smem);
+  constexpr size_t smem = sizeof(ShootSmem<WARPS, RPT, TILE>);
+  cudaError_t e = rsint::smem_opt_in<batch_kernel<WARPS, RPT, TILE, MASS>>(smem);
   if (e != cudaSuccess) return e;
-  batch_kernel<WARPS, RPT, rsint::kTile, MASS><<<grid, WARPS * 32, smem, s>>>(descs, items, n_items, counter);
+  batch_kernel<WARPS, RPT, TILE, MASS><<<grid, WARPS * 32, smem, s>>>(descs, items, n_items, counter);
   return cudaGetLastError();
 }
 
-template <int WARPS, int RPT>
+template <int WARPS, int RPT, int TILE>
 cudaError_t launch_batch_t(bool mass, const ShootDesc* descs, const int2* items, int n_items, int* counter, int grid,
                            cudaStream_t s) {
-  return mass ? launch_batch_m<WARPS, RPT, true>(descs, items, n_items, counter, grid, s)
-              : launch_batch_m<WARPS, RPT, false>(descs, items, n_items, counter, grid, s);
+  return mass ? launch_batch_m<WARPS, RPT, TILE, true>(descs, items, n_items, counter, grid, s)
+              : launch_batch_m<WARPS, RPT, TILE, false>(descs, items, n_items, counter, grid, s);
 }
 
-template <int WARPS, int RPT, bool MASS>
+template <int WARPS, int RPT, int TILE, bool MASS>
 cudaError_t occ_m(int* blocks) {
-  constexpr size_t smem = sizeof(ShootSmem<WARPS, RPT, rsint::kTile>);
-  cudaError_t e = rsint::smem_opt_in<batch_kernel<WARPS, RPT, rsint::kTile, MASS>>(smem);
+  constexpr size_t smem = sizeof(ShootSmem<WARPS, RPT, TILE>);
+  cudaError_t e = rsint::smem_opt_in<batch_kernel<WARPS, RPT, TILE, MASS>>(smem);
   if (e != cudaSuccess) return e;
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, batch_kernel<WARPS, RPT, rsint::kTile, MASS>,
-                                                       WARPS * 32, smem);
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, batch_kernel<WARPS, RPT, TILE, MASS>, WARPS * 32,
+                                                       smem);
 }
 
-template <int WARPS, int RPT>
+template <int WARPS, int RPT, int TILE>
 cudaError_t occ_t(bool mass, int* blocks) {
-  return mass ? occ_m<WARPS, RPT, true>(blocks) : occ_m<WARPS, RPT, false>(blocks);
+  return mass ? occ_m<WARPS, RPT, TILE, true>(blocks) : occ_m<WARPS, RPT, TILE, false>(blocks);
 }
 
 }  // namespace
@@ -81,24 +81,30 @@ namespace rsint {
 cudaError_t launch_batch(int cfg, bool mass, const rsdev::ShootDesc* descs, const int2* items, int n_items,
                          int* counter, int grid, cudaStream_t s) {
   switch (cfg) {
-    case 0: return launch_batch_t<2, 8>(mass, descs, items, n_items, counter, grid, s);
-    case 1: return launch_batch_t<4, 4>(mass, descs, items, n_items, counter, grid, s);
-    case 2: return launch_batch_t<4, 8>(mass, descs, items, n_items, counter, grid, s);
-    case 3: return launch_batch_t<8, 4>(mass, descs, items, n_items, counter, grid, s);
-    case 4: return launch_batch_t<8, 8>(mass, descs, items, n_items, counter, grid, s);
-    case 5: return launch_batch_t<8, 6>(mass, descs, items, n_items, counter, grid, s);
+    case 0: return launch_batch_t<2, 8, 256>(mass, descs, items, n_items, counter, grid, s);
+    case 1: return launch_batch_t<4, 4, 256>(mass, descs, items, n_items, counter, grid, s);
+    case 2: return launch_batch_t<4, 8, 256>(mass, descs, items, n_items, counter, grid, s);
+    case 3: return launch_batch_t<8, 4, 256>(mass, descs, items, n_items, counter, grid, s);
+    case 4: return launch_batch_t<8, 8, 256>(mass, descs, items, n_items, counter, grid, s);
+    case 5: return launch_batch_t<8, 6, 256>(mass, descs, items, n_items, counter, grid, s);
+    case 6: return launch_batch_t<2, 8, 512>(mass, descs, items, n_items, counter, grid, s);
+    case 7: return launch_batch_t<4, 4, 512>(mass, descs, items, n_items, counter, grid, s);
+    case 8: return launch_batch_t<4, 8, 512>(mass, descs, items, n_items, counter, grid, s);
     default: return cudaErrorInvalidValue;
   }
 }
 
 cudaError_t batch_blocks_per_sm(int cfg, bool mass, int* blocks) {
   switch (cfg) {
-    case 0: return occ_t<2, 8>(mass, blocks);
-    case 1: return occ_t<4, 4>(mass, blocks);
-    case 2: return occ_t<4, 8>(mass, blocks);
-    case 3: return occ_t<8, 4>(mass, blocks);
-    case 4: return occ_t<8, 8>(mass, blocks);
-    case 5: return occ_t<8, 6>(mass, blocks);
+    case 0: return occ_t<2, 8, 256>(mass, blocks);
+    case 1: return occ_t<4, 4, 256>(mass, blocks);
+    case 2: return occ_t<4, 8, 256>(mass, blocks);
+    case 3: return occ_t<8, 4, 256>(mass, blocks);
+    case 4: return occ_t<8, 8, 256>(mass, blocks);
+    case 5: return occ_t<8, 6, 256>(mass, blocks);
+    case 6: return occ_t<2, 8, 512>(mass, blocks);
+    case 7: return occ_t<4, 4, 512>(mass, blocks);
+    case 8: return occ_t<4, 8, 512>(mass, blocks);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -263,62 +263,65 @@ struct NoNear {
 };
 
 // Near-lens search state of a CTA of BLOCK threads holding RPT rays each, whose rays form NG groups
-// (NG = 1: one box around all rays of the CTA; NG = warps: one box per warp).
+// (NG = 1: one box around all rays of the CTA; NG = warps: one box per warp).  While a lens tile is
+// being summed, each warp checks its share of the tile's lenses against the boxes and lists the hits
+// (field lens indices) in the list of the tile's parity; the list is evaluated during the next tile,
+// after the end-of-tile barrier that already separates the two, so the search adds no barrier and
+// nothing to the serial part of a tile boundary.
 template <int TILE, int NG, int BLOCK, int RPT>
 struct __align__(16) NearSmem {
   static constexpr bool kOn = true;
   static constexpr int kGroups = NG;
   float box[NG][4];        // x1 lo, x1 hi, x2 lo, x2 hi of each group's rays, widened by h (rounded outwards)
-  int n[NG];               // lenses of the current tile inside each box
-  uint16_t idx[NG][TILE];  // their indices within the tile
+  int n[2][NG];            // lenses listed per tile parity and group
+  int idx[2][NG][TILE];    // their indices in the field
   float t[RPT * BLOCK];    // per ray: the largest near term so far (thread x's ray k at k * BLOCK + x)
 };
 
 // Box of the rays [x1a, x1b] x [x2a, x2b] widened by kNearPad: a lens outside it is farther than h
-// from every ray inside, in float32 as well (its rounded d1 or d2 exceeds h).
+// from every ray inside, in float32 as well (its rounded d1 or d2 exceeds h).  Empties the group's lists.
 template <class NS>
 __device__ __forceinline__ void near_set_box(NS& ns, int g, float x1a, float x1b, float x2a, float x2b) {
   ns.box[g][0] = __double2float_rd(__dsub_rd((double)x1a, kNearPad));
   ns.box[g][1] = __double2float_ru(__dadd_ru((double)x1b, kNearPad));
   ns.box[g][2] = __double2float_rd(__dsub_rd((double)x2a, kNearPad));
   ns.box[g][3] = __double2float_ru(__dadd_ru((double)x2b, kNearPad));
-  ns.n[g] = 0;
+  ns.n[0][g] = 0;
+  ns.n[1][g] = 0;
 }
 
-// Lists the lenses of the current tile (cnt lenses at l4) that lie inside each group's box.  All
-// threads of the CTA call it; the lists start empty.
-template <class NS>
-__device__ __forceinline__ void near_gather(NS& ns, const float4* l4, int cnt, int nthreads) {
-  const int lane = threadIdx.x & 31;
-  for (int l0 = 0; l0 < cnt; l0 += nthreads) {  // CTA-uniform trip count
-    const int l = l0 + (int)threadIdx.x;
-    float lx = 0.f, ly = 0.f;
-    if (l < cnt) {
-      const float4 L = l4[l];
-      lx = L.x;
-      ly = L.z;
-    }
+// The calling warp's share of the current tile (cnt lenses at l4, field index of the first: base):
+// lenses inside a group's box are appended to that group's list of parity par.  Whole warps call it.
+template <int TILE, class NS>
+__device__ __forceinline__ void near_gather(NS& ns, int par, const float4* l4, int cnt, int base, int nwarps) {
+  constexpr int NG = NS::kGroups;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int share = (TILE + nwarps - 1) / nwarps;
+  const int l0 = warp * share, l1 = min(l0 + share, cnt);
+  for (int l = l0 + lane; l - lane < l1; l += 32) {  // warp-uniform trip count
+    const bool ok = l < l1;
+    const float4 L = l4[ok ? l : l0];
 #pragma unroll
-    for (int g = 0; g < NS::kGroups; ++g) {
-      const bool in = l < cnt && lx >= ns.box[g][0] && lx <= ns.box[g][1] && ly >= ns.box[g][2] && ly <= ns.box[g][3];
+    for (int g = 0; g < NG; ++g) {
+      const bool in = ok && L.x >= ns.box[g][0] && L.x <= ns.box[g][1] && L.z >= ns.box[g][2] && L.z <= ns.box[g][3];
       const unsigned mask = __ballot_sync(0xffffffffu, in);
       if (mask != 0u) {
         const int leader = __ffs(mask) - 1;
-        int base = 0;
-        if (lane == leader) base = atomicAdd(&ns.n[g], __popc(mask));
-        base = __shfl_sync(0xffffffffu, base, leader);
-        if (in) ns.idx[g][base + __popc(mask & ((1u << lane) - 1u))] = (uint16_t)l;
+        int slot = 0;
+        if (lane == leader) slot = atomicAdd(&ns.n[par][g], __popc(mask));
+        slot = __shfl_sync(0xffffffffu, slot, leader);
+        if (in) ns.idx[par][g][slot + __popc(mask & ((1u << lane) - 1u))] = base + l;
       }
     }
   }
 }
 
-// Near terms of group g's listed lenses of the current tile for the thread's rays (packed pairs X1,
-// X2), folded into the thread's entries of ns.t.
+// Near terms of group g's lenses listed with parity par for the thread's rays (packed pairs X1, X2),
+// folded into the thread's entries of ns.t; lens coordinates from the field's arrays.
 template <int NP, bool MASS, class NS>
-__device__ __forceinline__ void near_eval(NS& ns, int g, const float4* l4, const float2* m2,
-                                          const uint64_t (&X1)[NP], const uint64_t (&X2)[NP], int nthreads) {
-  const int n = ns.n[g];
+__device__ __forceinline__ void near_eval(NS& ns, int par, int g, const FieldDev& f, const uint64_t (&X1)[NP],
+                                          const uint64_t (&X2)[NP], int nthreads) {
+  const int n = ns.n[par][g];
   if (n == 0) return;
   float x1[2 * NP], x2[2 * NP], t[2 * NP];
 #pragma unroll
@@ -329,9 +332,9 @@ __device__ __forceinline__ void near_eval(NS& ns, int g, const float4* l4, const
 #pragma unroll
   for (int k = 0; k < 2 * NP; ++k) t[k] = ns.t[k * nthreads + threadIdx.x];
   for (int e = 0; e < n; ++e) {
-    const int l = ns.idx[g][e];
-    const float4 L = l4[l];
-    const float m = MASS ? m2[l].x : 1.f;
+    const int l = ns.idx[par][g][e];
+    const float4 L = __ldg(f.lens4 + l);
+    const float m = MASS ? __ldg(f.mass2 + l).x : 1.f;
 #pragma unroll
     for (int k = 0; k < 2 * NP; ++k) t[k] = fmaxf(t[k], near_term(x1[k], x2[k], L.x, L.z, m));
   }
@@ -379,9 +382,13 @@ __device__ __forceinline__ void pipe_init(uint64_t* bar, PipeState& ps) {
 
 template <int TILE, bool MASS, int ROWS>
 __device__ __forceinline__ void issue_lens_tile(const FieldDev& f, LensSmem<TILE, ROWS>& sm, int tile, int buf) {
-  // called by one thread; full tiles are always in bounds thanks to the kLensPad padding
-  const uint32_t b4 = TILE * sizeof(float4);
-  const uint32_t b2 = MASS ? TILE * sizeof(float2) : 0u;
+  // called by one thread.  The tile's lenses rounded up to an even count (16-byte multiples for both
+  // arrays): at most one lens past the field's last, which the padding of the device arrays (and of a
+  // view's parent) always holds; lenses past the count are never read.
+  const int cnt = min(TILE, f.n_lens - tile * TILE);
+  const uint32_t n2 = (uint32_t)(cnt + (cnt & 1));
+  const uint32_t b4 = n2 * (uint32_t)sizeof(float4);
+  const uint32_t b2 = MASS ? n2 * (uint32_t)sizeof(float2) : 0u;
   fence_proxy_async_smem();
   mbar_expect_tx(&sm.bar[buf], b4 + b2);
   bulk_g2s(&sm.lens4[buf][0], f.lens4 + (size_t)tile * TILE, b4, &sm.bar[buf]);
@@ -572,12 +579,16 @@ __device__ __forceinline__ bool deflect_accumulate(const FieldDev& f, const uint
       break;
     }
     const int cnt = min(TILE, n - t * TILE);
-    if constexpr (NS::kOn) near_gather(*ns, &sm.lens4[b][0], cnt, (int)blockDim.x);
-    if (ROW) build_row_table<TILE, ROWS>(sm, b);
-    if (ROW || NS::kOn) __syncthreads();
-    if constexpr (NS::kOn)
-      near_eval<NP, MASS>(*ns, NS::kGroups == 1 ? 0 : (int)(threadIdx.x >> 5), &sm.lens4[b][0], &sm.mass2[b][0], X1,
-                          X2, (int)blockDim.x);
+    if (ROW) {
+      build_row_table<TILE, ROWS>(sm, b);
+      __syncthreads();
+    }
+    if constexpr (NS::kOn) {
+      // the previous tile's list is complete (end-of-tile barrier); this tile's share goes to the other list
+      if (t > 0) near_eval<NP, MASS>(*ns, (t - 1) & 1, NS::kGroups == 1 ? 0 : (int)(threadIdx.x >> 5), f, X1, X2,
+                                     (int)blockDim.x);
+      near_gather<TILE>(*ns, t & 1, &sm.lens4[b][0], cnt, t * TILE, (int)(blockDim.x >> 5));
+    }
     const uint32_t lbase = smem_u32(&sm.lens4[b][0]);
     const uint32_t mbase = smem_u32(&sm.mass2[b][0]);
     int g = 0;
@@ -646,12 +657,17 @@ __device__ __forceinline__ bool deflect_accumulate(const FieldDev& f, const uint
         AB[q] = f2_add_x(AB[q], f2_add_x(f2_abs(P1[q]), f2_abs(P2[q])));
       }
     }
-    __syncthreads();  // every thread is done with buffer b, the row table and the near lists
+    __syncthreads();  // every thread is done with buffer b, the row table and the previous tile's near list
     if (threadIdx.x == 0) {
       if constexpr (NS::kOn)
-        for (int g = 0; g < NS::kGroups; ++g) ns->n[g] = 0;
+        for (int g = 0; g < NS::kGroups; ++g) ns->n[(t + 1) & 1][g] = 0;  // evaluated: free for tile t + 1
       if (t + 2 < ntiles) issue_lens_tile<TILE, MASS>(f, sm, t + 2, b);
     }
+  }
+  if constexpr (NS::kOn) {
+    if (ok && ntiles > 0)  // the last tile's list (complete: end-of-tile barrier)
+      near_eval<NP, MASS>(*ns, (ntiles - 1) & 1, NS::kGroups == 1 ? 0 : (int)(threadIdx.x >> 5), f, X1, X2,
+                          (int)blockDim.x);
   }
   if (!ok) {
     // Record the timeout and drain this CTA's copies still in flight (bounded) before leaving:

@@ -72,4 +72,47 @@ __device__ __forceinline__ void lens_term_ff(const FieldDev& f, int l, float x1,
   ff_add(A2h, A2l, t2h, t2l);
 }
 
+// Lanes per listed ray of the float-float evaluation: one warp for fields of up to kFfSmallField
+// lenses, kFfWarps warps above (a single warp over 1e8 lenses is latency-bound for a fraction of a
+// second per ray).  The lens split and the reduction order depend only on the lens count, so every
+// kernel that evaluates a ray in float-float gets the same value.
+constexpr int kFfSmallField = 1 << 16;
+constexpr int kFfWarps = 16;
+__host__ __device__ __forceinline__ int ff_warps(int n_lens) { return n_lens > kFfSmallField ? kFfWarps : 1; }
+
+// Float-float deflection of one ray by lenses [0, f.n_lens) of a field, summed by the W warps of a
+// group: lane lam = w * 32 + lane sums lenses lam, lam + 32 W, ... in order; each warp's 32 partials
+// are combined by a fixed shuffle tree (16, 8, 4, 2, 1) and warp 0 adds warps 1 .. W-1 in order
+// through red (W entries of shared memory).  Every thread of the group must call it with the same
+// ray; W > 1 needs the whole CTA (a __syncthreads inside).  Thread 0 of the group returns alpha as
+// float pairs {a1 hi, a1 lo, a2 hi, a2 lo}.
+template <bool MASS>
+__device__ __forceinline__ float4 deflect_ff_group(const FieldDev& f, float x1, float x2, int W, int w, float4* red) {
+  const int lane = threadIdx.x & 31;
+  float A1h = 0.f, A1l = 0.f, A2h = 0.f, A2l = 0.f;
+  const int n = f.n_lens, stride = 32 * W;
+  for (int l = w * 32 + lane; l < n; l += stride) lens_term_ff<MASS>(f, l, x1, x2, A1h, A1l, A2h, A2l);
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    const float b1h = __shfl_down_sync(0xffffffffu, A1h, off);
+    const float b1l = __shfl_down_sync(0xffffffffu, A1l, off);
+    const float b2h = __shfl_down_sync(0xffffffffu, A2h, off);
+    const float b2l = __shfl_down_sync(0xffffffffu, A2l, off);
+    ff_add(A1h, A1l, b1h, b1l);
+    ff_add(A2h, A2l, b2h, b2l);
+  }
+  if (W > 1) {
+    if (lane == 0) red[w] = make_float4(A1h, A1l, A2h, A2l);
+    __syncthreads();
+    if (w == 0 && lane == 0)
+      for (int k = 1; k < W; ++k) {
+        const float4 o = red[k];
+        ff_add(A1h, A1l, o.x, o.y);
+        ff_add(A2h, A2l, o.z, o.w);
+      }
+    __syncthreads();  // red is free again
+  }
+  return make_float4(A1h, A1l, A2h, A2l);
+}
+
 }  // namespace rsdev

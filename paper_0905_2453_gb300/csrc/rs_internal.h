@@ -10,18 +10,23 @@
 
 namespace rsint {
 
-// Lenses per shared-memory stage (a multiple of rsdev::kGroup, a divisor of rsdev::kLensPad).
+// Lenses per shared-memory stage of the kernels without a tile choice (listed rays, culled cells,
+// staged partitions); a multiple of rsdev::kGroup.
 constexpr int kTile = 256;
 
-// Launch shapes compiled into the library; the per-ray arithmetic is identical for all.
-// A CTA of block / 32 warps covers block / 32 grid rows by 32 * rpt columns.
+// Launch shapes compiled into the library; the per-ray arithmetic is identical for all (the lens
+// tile is a multiple of the 256-lens summation period, so the group and renormalisation schedule
+// does not depend on it).  A CTA of block / 32 warps covers block / 32 grid rows by 32 * rpt columns
+// and stages tile lenses per step.
 struct KernelCfg {
   int block;  // threads per CTA (a multiple of 32)
   int rpt;    // rays per thread (even: packed pairs)
+  int tile;   // lenses per shared-memory stage (256 or 512)
 };
-constexpr int kNumCfg = 6;
-constexpr KernelCfg kCfgs[kNumCfg] = {{64, 8}, {128, 4}, {128, 8}, {256, 4}, {256, 8}, {256, 6}};
-constexpr int kDefaultCfg = 2;
+constexpr int kNumCfg = 9;
+constexpr KernelCfg kCfgs[kNumCfg] = {{64, 8, 256},  {128, 4, 256}, {128, 8, 256}, {256, 4, 256}, {256, 8, 256},
+                                      {256, 6, 256}, {64, 8, 512},  {128, 4, 512}, {128, 8, 512}};
+constexpr int kDefaultCfg = 8;
 
 // Dynamic shared memory beyond 48 KiB per CTA needs a one-time opt-in per kernel and device.
 template <auto Kernel>
@@ -38,9 +43,9 @@ cudaError_t smem_opt_in(size_t bytes) {
   return e;
 }
 
-inline int find_cfg(int block, int rpt) {
+inline int find_cfg(int block, int rpt, int tile) {
   for (int i = 0; i < kNumCfg; ++i)
-    if (kCfgs[i].block == block && kCfgs[i].rpt == rpt) return i;
+    if (kCfgs[i].block == block && kCfgs[i].rpt == rpt && kCfgs[i].tile == tile) return i;
   return -1;
 }
 

@@ -61,35 +61,36 @@ __global__ void __launch_bounds__(BLOCK)
   }
 }
 
-template <int WARPS, int RPT, bool MASS>
+template <int WARPS, int RPT, int TILE, bool MASS>
 cudaError_t launch_shoot_m(const ShootDesc& d, int64_t grid, cudaStream_t s) {
-  constexpr size_t smem = sizeof(ShootSmem<WARPS, RPT, rsint::kTile>);
-  cudaError_t e = rsint::smem_opt_in<shoot_kernel<WARPS, RPT, rsint::kTile, MASS>>(smem);
+  constexpr size_t smem = sizeof(ShootSmem<WARPS, RPT, TILE>);
+  cudaError_t e = rsint::smem_opt_in<shoot_kernel<WARPS, RPT, TILE, MASS>>(smem);
   if (e != cudaSuccess) return e;
-  shoot_kernel<WARPS, RPT, rsint::kTile, MASS><<<(unsigned)grid, WARPS * 32, smem, s>>>(d);
+  shoot_kernel<WARPS, RPT, TILE, MASS><<<(unsigned)grid, WARPS * 32, smem, s>>>(d);
   return cudaGetLastError();
 }
 
-template <int WARPS, int RPT>
+template <int WARPS, int RPT, int TILE>
 cudaError_t launch_shoot_t(const ShootDesc& d, cudaStream_t s) {
   const int64_t grid = shoot_tiles<WARPS, RPT>(d.n_rows, d.n0);
   if (grid <= 0) return cudaSuccess;
   if (grid >= ((int64_t)1 << 31)) return cudaErrorInvalidValue;
-  return d.f.has_mass ? launch_shoot_m<WARPS, RPT, true>(d, grid, s) : launch_shoot_m<WARPS, RPT, false>(d, grid, s);
+  return d.f.has_mass ? launch_shoot_m<WARPS, RPT, TILE, true>(d, grid, s)
+                      : launch_shoot_m<WARPS, RPT, TILE, false>(d, grid, s);
 }
 
-template <int WARPS, int RPT, bool MASS>
+template <int WARPS, int RPT, int TILE, bool MASS>
 cudaError_t occupancy_m(int* blocks) {
-  constexpr size_t smem = sizeof(ShootSmem<WARPS, RPT, rsint::kTile>);
-  cudaError_t e = rsint::smem_opt_in<shoot_kernel<WARPS, RPT, rsint::kTile, MASS>>(smem);
+  constexpr size_t smem = sizeof(ShootSmem<WARPS, RPT, TILE>);
+  cudaError_t e = rsint::smem_opt_in<shoot_kernel<WARPS, RPT, TILE, MASS>>(smem);
   if (e != cudaSuccess) return e;
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, shoot_kernel<WARPS, RPT, rsint::kTile, MASS>,
-                                                       WARPS * 32, smem);
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, shoot_kernel<WARPS, RPT, TILE, MASS>, WARPS * 32,
+                                                       smem);
 }
 
-template <int WARPS, int RPT>
+template <int WARPS, int RPT, int TILE>
 cudaError_t occupancy_t(bool mass, int* blocks) {
-  return mass ? occupancy_m<WARPS, RPT, true>(blocks) : occupancy_m<WARPS, RPT, false>(blocks);
+  return mass ? occupancy_m<WARPS, RPT, TILE, true>(blocks) : occupancy_m<WARPS, RPT, TILE, false>(blocks);
 }
 
 }  // namespace
@@ -98,24 +99,30 @@ namespace rsint {
 
 cudaError_t shoot_blocks_per_sm(int cfg, bool mass, int* blocks) {
   switch (cfg) {
-    case 0: return occupancy_t<2, 8>(mass, blocks);
-    case 1: return occupancy_t<4, 4>(mass, blocks);
-    case 2: return occupancy_t<4, 8>(mass, blocks);
-    case 3: return occupancy_t<8, 4>(mass, blocks);
-    case 4: return occupancy_t<8, 8>(mass, blocks);
-    case 5: return occupancy_t<8, 6>(mass, blocks);
+    case 0: return occupancy_t<2, 8, 256>(mass, blocks);
+    case 1: return occupancy_t<4, 4, 256>(mass, blocks);
+    case 2: return occupancy_t<4, 8, 256>(mass, blocks);
+    case 3: return occupancy_t<8, 4, 256>(mass, blocks);
+    case 4: return occupancy_t<8, 8, 256>(mass, blocks);
+    case 5: return occupancy_t<8, 6, 256>(mass, blocks);
+    case 6: return occupancy_t<2, 8, 512>(mass, blocks);
+    case 7: return occupancy_t<4, 4, 512>(mass, blocks);
+    case 8: return occupancy_t<4, 8, 512>(mass, blocks);
     default: return cudaErrorInvalidValue;
   }
 }
 
 cudaError_t launch_shoot(int cfg, const rsdev::ShootDesc& d, cudaStream_t s) {
   switch (cfg) {
-    case 0: return launch_shoot_t<2, 8>(d, s);
-    case 1: return launch_shoot_t<4, 4>(d, s);
-    case 2: return launch_shoot_t<4, 8>(d, s);
-    case 3: return launch_shoot_t<8, 4>(d, s);
-    case 4: return launch_shoot_t<8, 8>(d, s);
-    case 5: return launch_shoot_t<8, 6>(d, s);
+    case 0: return launch_shoot_t<2, 8, 256>(d, s);
+    case 1: return launch_shoot_t<4, 4, 256>(d, s);
+    case 2: return launch_shoot_t<4, 8, 256>(d, s);
+    case 3: return launch_shoot_t<8, 4, 256>(d, s);
+    case 4: return launch_shoot_t<8, 8, 256>(d, s);
+    case 5: return launch_shoot_t<8, 6, 256>(d, s);
+    case 6: return launch_shoot_t<2, 8, 512>(d, s);
+    case 7: return launch_shoot_t<4, 4, 512>(d, s);
+    case 8: return launch_shoot_t<4, 8, 512>(d, s);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -5,6 +5,8 @@
 // and the ray's largest-term bound so far (a maximum over partitions), so with partitions of
 // multiples of 256 lenses the final sums and bands are bitwise those of one pass over all lenses.
 // Certified binning re-evaluates the listed rays in float-float, again partition by partition.
+#include <algorithm>
+
 #include "rs_ff.cuh"
 #include "rs_internal.h"
 
@@ -104,41 +106,34 @@ __global__ void __launch_bounds__(kBlock, 2) staged_kernel(const ShootDesc d, ui
 // ---- float-float re-evaluation of the listed rays, partition by partition ----------------------
 
 // Partial float-float deflection of each listed ray by one partition, added to ff[e] = {A1h, A1l,
-// A2h, A2l} (set on the first partition).  One warp per listed ray, lanes split the partition's
-// lenses, fixed reduction tree.
-template <bool MASS>
-__global__ void __launch_bounds__(128) recheck_part_kernel(const ShootDesc d, const uint2* __restrict__ list,
-                                                           const unsigned int* __restrict__ count, unsigned int cap,
-                                                           float4* __restrict__ ff, int first) {
+// A2h, A2l} (set on the first partition).  W warps per listed ray (see ff_warps), lanes split the
+// partition's lenses, fixed reduction order.
+template <int W, bool MASS>
+__global__ void __launch_bounds__(W == 1 ? 128 : 32 * W) recheck_part_kernel(const ShootDesc d,
+                                                                               const uint2* __restrict__ list,
+                                                                               const unsigned int* __restrict__ count,
+                                                                               unsigned int cap,
+                                                                               float4* __restrict__ ff, int first) {
+  __shared__ float4 red[W];
+  constexpr int G = W == 1 ? 4 : 1;  // groups (rays in flight) per CTA
   const unsigned int n = min(*count, cap);
-  const unsigned int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const unsigned int nwarps = (gridDim.x * blockDim.x) >> 5;
-  const int lane = threadIdx.x & 31;
-  for (unsigned int e = warp; e < n; e += nwarps) {
+  const unsigned int g = threadIdx.x / (32 * W);
+  for (unsigned int e0 = blockIdx.x * G; e0 < n; e0 += gridDim.x * G) {  // CTA-uniform
+    const unsigned int e = e0 + g;
+    if (e >= n) continue;  // only when G > 1, where no barrier is used
     const int64_t r = (int64_t)list[e].y;
     const int64_t jrel = r / d.n0;
     const int64_t i = r - jrel * d.n0;
     const float x1 = ray_coord(i, d.sp0, d.or0);
     const float x2 = ray_coord(d.j_begin + jrel, d.sp1, d.or1);
-    float A1h = 0.f, A1l = 0.f, A2h = 0.f, A2l = 0.f;
-    for (int l = lane; l < d.f.n_lens; l += 32) lens_term_ff<MASS>(d.f, l, x1, x2, A1h, A1l, A2h, A2l);
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-      const float b1h = __shfl_down_sync(0xffffffffu, A1h, off);
-      const float b1l = __shfl_down_sync(0xffffffffu, A1l, off);
-      const float b2h = __shfl_down_sync(0xffffffffu, A2h, off);
-      const float b2l = __shfl_down_sync(0xffffffffu, A2l, off);
-      ff_add(A1h, A1l, b1h, b1l);
-      ff_add(A2h, A2l, b2h, b2l);
+    float4 a = deflect_ff_group<MASS>(d.f, x1, x2, W, (int)(threadIdx.x >> 5) % W, red);
+    if ((threadIdx.x & (32 * W - 1)) != 0) continue;
+    if (!first) {
+      const float4 o = ff[e];
+      ff_add(a.x, a.y, o.x, o.y);
+      ff_add(a.z, a.w, o.z, o.w);
     }
-    if (lane == 0) {
-      if (!first) {
-        const float4 o = ff[e];
-        ff_add(A1h, A1l, o.x, o.y);
-        ff_add(A2h, A2l, o.z, o.w);
-      }
-      ff[e] = make_float4(A1h, A1l, A2h, A2l);
-    }
+    ff[e] = a;
   }
 }
 
@@ -199,10 +194,19 @@ cudaError_t launch_staged(const rsdev::ShootDesc& d, uint64_t* state, bool first
 cudaError_t launch_recheck_part(const rsdev::ShootDesc& d, const uint2* list, const unsigned int* count,
                                 unsigned int cap, float4* ff, bool first, int grid, cudaStream_t s) {
   if (cap == 0) return cudaSuccess;
-  if (d.f.has_mass)
-    recheck_part_kernel<true><<<grid, 128, 0, s>>>(d, list, count, cap, ff, first ? 1 : 0);
-  else
-    recheck_part_kernel<false><<<grid, 128, 0, s>>>(d, list, count, cap, ff, first ? 1 : 0);
+  const int f = first ? 1 : 0;
+  if (ff_warps(d.f.n_lens) == 1) {
+    if (d.f.has_mass)
+      recheck_part_kernel<1, true><<<grid, 128, 0, s>>>(d, list, count, cap, ff, f);
+    else
+      recheck_part_kernel<1, false><<<grid, 128, 0, s>>>(d, list, count, cap, ff, f);
+  } else {
+    const int g = std::max(1, grid / 4), t = 32 * kFfWarps;
+    if (d.f.has_mass)
+      recheck_part_kernel<kFfWarps, true><<<g, t, 0, s>>>(d, list, count, cap, ff, f);
+    else
+      recheck_part_kernel<kFfWarps, false><<<g, t, 0, s>>>(d, list, count, cap, ff, f);
+  }
   return cudaGetLastError();
 }
 

@@ -1,10 +1,11 @@
 """Launch-shape autotuner.
 
 The library carries kernels for several launch shapes (threads per CTA x rays per
-thread, see ``rs_launch_configs``).  All of them compute bitwise identical
-results, so the choice only affects speed.  ``autotune`` times every shape on a
-proxy run (a block of the workload's own grid rows) with CUDA events, selects the
-fastest with ``rs_set_launch_config`` and caches the choice in a JSON file keyed
+thread x lenses per shared-memory stage, see ``rs_launch_configs``).  All of them
+compute bitwise identical results, so the choice only affects speed.  ``autotune`` times every shape on a
+proxy run (a block of the workload's own grid rows; for fields larger than the proxy,
+one whole wave of CTAs per launch) with CUDA events, selects the fastest with
+``rs_set_launch_config`` and caches the choice in a JSON file keyed
 by (GPU name, library version, mass mode, lens-count bucket, row-length bucket).  This replaces the
 paper's occupancy-calculator choice of 128 or 256 threads (Section 2.2).  Fields of more than
 ``max_proxy_lenses`` lenses are timed on a view of their first lenses: past a few lens tiles the cost
@@ -19,7 +20,7 @@ import os
 
 import torch
 
-from . import rs_launch_configs, rs_set_launch_config, rs_shoot_rows, rs_version
+from . import rs_launch_configs, rs_launch_occupancy, rs_set_launch_config, rs_shoot_rows, rs_version
 
 DEFAULT_CACHE = os.path.join(os.environ.get("XDG_CACHE_HOME", os.path.expanduser("~/.cache")),
                              "rs_gb300", "tune.json")
@@ -47,8 +48,8 @@ def wave_rows(n0: int, block: int, rpt: int, sms: int, ctas_per_sm: int = 2) -> 
 
 
 def shape_rates(field, grid, cache_path: str = None) -> dict:
-    """Steady-state interactions/s of every launch shape from the tuner's cache entry for (field, grid)
-    ({} if the pair was never tuned)."""
+    """Steady-state interactions/s of every launch shape ("block x rpt x lens_tile") from the tuner's cache
+    entry for (field, grid) ({} if the pair was never tuned)."""
     cache = _load(cache_path or os.environ.get("RS_TUNE_CACHE", DEFAULT_CACHE))
     return dict(cache.get(cache_key(field, grid), {}).get("interactions_per_s", {}))
 
@@ -63,16 +64,16 @@ def _load(path):
 
 def autotune(field, grid, window, min_rays: float = 8e6, max_interactions: float = 3e11, reps: int = 3,
              cache_path: str = None, force: bool = False, stream=None, max_proxy_lenses: int = 1 << 16):
-    """Pick and set the fastest launch shape for this (field, grid); returns (block, rpt, timings_ms)
-    with each shape's time for its own (largest) proxy block of rows."""
+    """Pick and set the fastest launch shape for this (field, grid); returns (block, rpt, lens_tile,
+    timings_ms) with each shape's time for its own (largest) proxy block of rows."""
     cache_path = cache_path or os.environ.get("RS_TUNE_CACHE", DEFAULT_CACHE)
     n_lens, has_mass = field.info()
     key = cache_key(field, grid)
     cache = _load(cache_path)
     if not force and key in cache:
-        b, r = cache[key]["block"], cache[key]["rpt"]
-        rs_set_launch_config(has_mass, b, r)
-        return b, r, cache[key].get("ms", {})
+        b, r, t = cache[key]["block"], cache[key]["rpt"], cache[key].get("tile", 256)
+        rs_set_launch_config(has_mass, b, r, t)
+        return b, r, t, cache[key].get("ms", {})
     # proxy: blocks of the grid's rows, capped in work; very large fields through a view of their
     # first lenses.  Where the grid allows, each shape shoots k and 2k units of rows holding a whole
     # number of waves (a multiple of 2 x SMs CTAs: whole waves at one or two resident CTAs per SM) and
@@ -101,11 +102,22 @@ def autotune(field, grid, window, min_rays: float = 8e6, max_interactions: float
 
     timings, rates, shape_rows = {}, {}, {}
     try:
-        for block, rpt in rs_launch_configs():
+        for block, rpt, tile in rs_launch_configs():
             unit = wave_rows(n0, block, rpt, sms)
             k = min(max(1, round(rows / unit)), n1 // (2 * unit))
-            name = f"{block}x{rpt}"
-            rs_set_launch_config(has_mass, block, rpt)
+            name = f"{block}x{rpt}x{tile}"
+            rs_set_launch_config(has_mass, block, rpt, tile)
+            if proxy is not field:
+                # A large field's CTAs each run for seconds, all CTAs of a wave in step with one another
+                # (their warps then compete for the same pipe at the same time); short proxy CTAs drift
+                # apart over many waves and hide that.  So each launch here is exactly the rows of one
+                # whole wave at the shape's real occupancy, as a block of the large field runs.
+                wave = wave_rows(n0, block, rpt, sms, rs_launch_occupancy(has_mass, block, rpt, tile))
+                if wave <= n1:
+                    rs_shoot_rows(proxy.handle, grid, 0, wave, window, counts, None, st)  # warm-up
+                    timings[name], shape_rows[name] = timed(wave), [wave]
+                    rates[name] = wave * n0 * n_proxy / max(timings[name], 1e-6) * 1e3
+                    continue
             if rows < n1 and k >= 1 and unit * n0 * n_proxy <= 4 * max_interactions:
                 rs_shoot_rows(proxy.handle, grid, 0, k * unit, window, counts, None, st)  # warm-up
                 t1, t2 = timed(k * unit), timed(2 * k * unit)
@@ -120,9 +132,9 @@ def autotune(field, grid, window, min_rays: float = 8e6, max_interactions: float
         if proxy is not field:
             proxy.close()
     best = max(rates, key=rates.get)
-    b, r = (int(t) for t in best.split("x"))
-    rs_set_launch_config(has_mass, b, r)
-    cache[key] = {"block": b, "rpt": r, "ms": timings, "rows": shape_rows, "interactions_per_s": rates,
+    b, r, t = (int(v) for v in best.split("x"))
+    rs_set_launch_config(has_mass, b, r, t)
+    cache[key] = {"block": b, "rpt": r, "tile": t, "ms": timings, "rows": shape_rows, "interactions_per_s": rates,
                   "proxy_lenses": n_proxy}
     try:
         os.makedirs(os.path.dirname(cache_path), exist_ok=True)
@@ -132,4 +144,4 @@ def autotune(field, grid, window, min_rays: float = 8e6, max_interactions: float
         os.replace(tmp, cache_path)
     except OSError:
         pass
-    return b, r, timings
+    return b, r, t, timings

@@ -105,8 +105,16 @@ def test_grid_window_validation(rs):
     assert lib.rs_shoot_rows(fake, ctypes.byref(g), 2, 9, ctypes.byref(w), ctypes.c_void_p(16), None,
                              None) == rs.RS_EINVAL
     # unknown launch shape
-    assert lib.rs_set_launch_config(0, 96, 3) == rs.RS_EINVAL
-    assert len(rs.rs_launch_configs()) >= 4
+    assert lib.rs_set_launch_config(0, 96, 3, 256) == rs.RS_EINVAL
+    assert lib.rs_set_launch_config(0, 128, 8, 384) == rs.RS_EINVAL   # no such lens tile
+    shapes = rs.rs_launch_configs()
+    assert len(shapes) >= 4 and {t for _, _, t in shapes} == {256, 512}
+    saved = rs.rs_get_launch_config(False)
+    try:
+        rs.rs_set_launch_config(False, 128, 8, 512)
+        assert rs.rs_get_launch_config(False) == (128, 8, 512)
+    finally:
+        rs.rs_set_launch_config(False, *saved)
 
 
 def test_struct_layouts_match_binding(rs, tmp_path):

@@ -121,9 +121,10 @@ def test_autotune_times_large_fields_on_a_prefix_view(tmp_path):
     old = m.rs_get_launch_config(False)
     cache = str(tmp_path / "tune.json")
     try:
-        b, r, ms = tune.autotune(f, spec.grid, spec.window, cache_path=cache, force=True, reps=1,
-                                 min_rays=1e6, max_proxy_lenses=1024)
-        assert (b, r) in [tuple(x) for x in m.rs_launch_configs()] and len(ms) == len(m.rs_launch_configs())
+        b, r, t, ms = tune.autotune(f, spec.grid, spec.window, cache_path=cache, force=True, reps=1,
+                                    min_rays=1e6, max_proxy_lenses=1024)
+        assert (b, r, t) in [tuple(x) for x in m.rs_launch_configs()] and len(ms) == len(m.rs_launch_configs())
+        assert m.rs_get_launch_config(False) == (b, r, t)
         entry = next(iter(json.load(open(cache)).values()))
         assert entry["proxy_lenses"] == 1024
         assert f.status() == m.RS_OK

@@ -24,3 +24,14 @@ def test_wave_rows_of_the_workloads():
         assert wave_rows(n0, 128, 8, 152) == 76
     assert wave_rows(16384, 64, 8, 152) == 38
     assert wave_rows(16384, 256, 8, 152) == 152
+
+
+@pytest.mark.parametrize("occ", [1, 2, 3, 4])
+def test_wave_rows_at_other_occupancies(occ):
+    for n0 in (4096, 8192, 16384, 1000):
+        for block, rpt in ((64, 8), (128, 8), (128, 4)):
+            warps, cpr = block // 32, -(-n0 // (32 * rpt))
+            unit = wave_rows(n0, block, rpt, 152, occ)
+            assert unit % warps == 0 and ((unit // warps) * cpr) % (occ * 152) == 0
+    # the 1e8-lens grid: 64-thread CTAs four to an SM fill one wave with 38 rows
+    assert wave_rows(8192, 64, 8, 152, 4) == 38
