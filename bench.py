@@ -360,24 +360,44 @@ def run_ours(args):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         return float(t.item())
 
-    # weak scaling: each rank shoots its own realisation of the workload
-    spec = workload(args.workload, seed=rank)
+    # sharded (default): one map per step whose rows are split over the ranks, the count maps summed by one
+    # NCCL all_reduce; realisations: every rank shoots its own realisation of the workload, no collective
+    sharded = args.mode == "sharded"
+    spec = workload(args.workload, seed=0 if sharded else rank)
     stream = torch.cuda.current_stream(device)
     field = rs.Field.from_spec(spec, stream)
     sms, max_mhz = peaks(local)
     r0, r1, shape, rows_note = headline_rows(rs, spec, field, sms, stream, args.launch_shape)
     from paper_0905_2453_gb300 import tune
+    from paper_0905_2453_gb300.shard import device_row_shooter, shoot_sharded
     rates_headline = {} if args.launch_shape else tune.shape_rates(field, spec.grid)
     npix = (int(spec.window.npix[1]), int(spec.window.npix[0]))
     counts = torch.zeros(npix, dtype=torch.int32, device=device)
     oow = torch.zeros(1, dtype=torch.int64, device=device)
     mu = torch.empty(npix, dtype=torch.float32, device=device)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=device)
-    inter_step = (r1 - r0) * int(spec.grid.n[0]) * spec.n_lens
-    rays_step = (r1 - r0) * int(spec.grid.n[0])
+    n0, n1 = int(spec.grid.n[0]), int(spec.grid.n[1])
+    whole = r0 == 0 and r1 == n1
+    if sharded:
+        # the step's rows: the whole grid (split over the ranks: strong scaling), or one whole-wave unit per rank
+        # (weak scaling of one sharded block)
+        warps = shape[0] // 32
+        total_rows = n1 if whole else min(n1, world * (r1 - r0))
+        row0 = 0 if whole else (n1 - total_rows) // 2 // warps * warps
+        shooter = device_row_shooter(field, spec.grid, spec.window, stream)
+        rows_note = (rows_note if world == 1 else
+                     f"rows [{row0}, {row0 + total_rows}) split over {world} ranks, counts summed by NCCL all_reduce")
+        inter_step = total_rows * n0 * spec.n_lens      # the whole job's interactions per step
+        rays_step = total_rows * n0
+    else:
+        inter_step = (r1 - r0) * n0 * spec.n_lens       # per rank
+        rays_step = (r1 - r0) * n0
 
     def shoot():
-        rs.rs_shoot_rows(field.handle, spec.grid, r0, r1, spec.window, counts, oow, stream)
+        if sharded:
+            shoot_sharded(shooter, total_rows, counts, oow, rank, world, row_begin=row0)
+        else:
+            rs.rs_shoot_rows(field.handle, spec.grid, r0, r1, spec.window, counts, oow, stream)
 
     def step():
         counts.zero_()
@@ -417,7 +437,7 @@ def run_ours(args):
     if status != rs.RS_OK:
         raise SystemExit(f"device reported status {status}")
     conserved = int(counts.sum(dtype=torch.int64).item()) + int(oow.item()) == rays_step
-    value = inter_step * args.steps * world / total_s
+    value = inter_step * args.steps * (1 if sharded else world) / total_s
 
     # ---------------- end to end through the public API with host buffers
     e2e = None
@@ -431,7 +451,11 @@ def run_ours(args):
             f = rs.Field(h_xy.numpy(), None if h_m is None else h_m.numpy(), spec.kappa_c, spec.gamma, stream)
             counts.zero_()
             oow.zero_()
-            rs.rs_shoot_rows(f.handle, spec.grid, r0, r1, spec.window, counts, oow, stream)
+            if sharded:
+                shoot_sharded(device_row_shooter(f, spec.grid, spec.window, stream), total_rows, counts, oow, rank,
+                              world, row_begin=row0)
+            else:
+                rs.rs_shoot_rows(f.handle, spec.grid, r0, r1, spec.window, counts, oow, stream)
             rs.rs_magnification(counts, spec.grid, spec.window, mu, stream)
             h_mu.copy_(mu, non_blocking=True)
             h_oow.copy_(oow, non_blocking=True)
@@ -448,7 +472,8 @@ def run_ours(args):
         dt = max_over_ranks(time.perf_counter() - t0)
         h2d = h_xy.numel() * 4 + (0 if h_m is None else h_m.numel() * 4)
         d2h = h_mu.numel() * 4 + 8
-        e2e = {"value": inter_step * n_e2e * world / dt, "unit": "interactions/s", "h2d_bytes_per_step": h2d,
+        e2e = {"value": inter_step * n_e2e * (1 if sharded else world) / dt, "unit": "interactions/s",
+               "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h, "steps": n_e2e,
                "includes": "field upload from pinned host memory + validation + repack, shoot of the step's rows, "
                            "normalise, D2H of mu and the out-of-window count, field release"}
@@ -503,11 +528,15 @@ def run_ours(args):
         if dist is not None:
             dist.destroy_process_group()
         return
-    rl = roofline_entry(inter_step, shoot_avg_s, sms, max_mhz, profiled_traffic(args.workload))
+    # per GPU: the whole job's interactions of a sharded step over the ranks, the shoot span the slowest rank's
+    rl = roofline_entry(inter_step / (world if sharded else 1), shoot_avg_s, sms, max_mhz,
+                        profiled_traffic(args.workload))
     med = clk.get("sm_mhz")
     cfg = workload_config(spec, args.workload)
-    cfg["rows_per_step"] = [r0, r1]
+    cfg["rows_per_step"] = [row0, row0 + total_rows] if sharded else [r0, r1]
     cfg["rays_per_step"] = rays_step
+    cfg["parallelism"] = (f"rows of one map sharded over {world} GPU(s), count maps summed (NCCL all_reduce)"
+                          if sharded else f"{world} independent realisation(s), one per GPU, no collective")
     cfg["interactions_per_step"] = inter_step
     cfg["sample"] = rows_note
     cfg["l2"] = ("inputs larger than L2 (lenses: %.2f GB on the device); L2 also flushed between steps (512 MiB "
@@ -525,8 +554,8 @@ def run_ours(args):
     line = {
         "metric": METRIC, "value": value, "unit": "interactions/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_s / args.steps * 1e3, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": cfg,
+        "scaling": "strong" if (sharded and whole) else "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic", "config": cfg,
         "pct_fp32_peak": 100.0 * rl["frac"],
         "pct_fp32_peak_at_measured_clock": (100.0 * rl["achieved"] / fp32_peak_tflops(sms, med)) if med else None,
         "roofline": rl,
@@ -1017,6 +1046,9 @@ def main():
     ap.add_argument("--steps", type=int, default=60)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--mode", choices=["sharded", "realisations"], default="sharded",
+                    help="N > 1: one map per step with its rows split over the GPUs and the counts summed (sharded), "
+                         "or an independent realisation per GPU (realisations)")
     ap.add_argument("--workload", default="n1e8")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batch", action="store_true")

@@ -25,11 +25,11 @@ __device__ __forceinline__ void ff_add(float& ah, float& al, float bh, float bl)
   fast_two_sum(s, e, ah, al);
 }
 
-// One lens term of Eq. 2 for ray (x1, x2) in float-float, added to (A1h, A1l), (A2h, A2l).
+// One lens term of Eq. 2 for ray (x1, x2) in float-float, added to (A1h, A1l), (A2h, A2l); the lens
+// L = {x1, x1, x2, x2} with mass m (read only with MASS).
 template <bool MASS>
-__device__ __forceinline__ void lens_term_ff(const FieldDev& f, int l, float x1, float x2, float& A1h, float& A1l,
-                                             float& A2h, float& A2l) {
-  const float4 L = __ldg(f.lens4 + l);
+__device__ __forceinline__ void lens_term_ff_at(const float4 L, float m, float x1, float x2, float& A1h, float& A1l,
+                                                float& A2h, float& A2l) {
   // exact differences x - x_l as float pairs
   float ah, al, bh, bl;
   two_sum(x1, -L.x, ah, al);
@@ -53,7 +53,6 @@ __device__ __forceinline__ void lens_term_ff(const FieldDev& f, int l, float x1,
   float wh, wl;
   fast_two_sum(w0, __fmul_rn(w0, e), wh, wl);
   if (MASS) {
-    const float m = __ldg(f.mass2 + l).x;
     const float mh = __fmul_rn(wh, m);
     float ml = __fmaf_rn(wh, m, -mh);
     ml = __fmaf_rn(wl, m, ml);
@@ -70,6 +69,33 @@ __device__ __forceinline__ void lens_term_ff(const FieldDev& f, int l, float x1,
   t2l = __fmaf_rn(wl, bh, t2l);
   ff_add(A1h, A1l, t1h, t1l);
   ff_add(A2h, A2l, t2h, t2l);
+}
+
+// Lens l of field f (see lens_term_ff_at).
+template <bool MASS>
+__device__ __forceinline__ void lens_term_ff(const FieldDev& f, int l, float x1, float x2, float& A1h, float& A1l,
+                                             float& A2h, float& A2l) {
+  lens_term_ff_at<MASS>(__ldg(f.lens4 + l), MASS ? __ldg(f.mass2 + l).x : 0.f, x1, x2, A1h, A1l, A2h, A2l);
+}
+
+// Lenses l0, l0 + stride, ... (< n) of field f in that order, four loads in flight at a time (the terms
+// are still added one after the other, in lens order).
+template <bool MASS>
+__device__ __forceinline__ void lens_terms_ff_strided(const FieldDev& f, int l0, int stride, int n, float x1, float x2,
+                                                      float& A1h, float& A1l, float& A2h, float& A2l) {
+  int l = l0;
+  for (; l + 3 * stride < n; l += 4 * stride) {
+    float4 L[4];
+    float m[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      L[k] = __ldg(f.lens4 + l + k * stride);
+      m[k] = MASS ? __ldg(f.mass2 + l + k * stride).x : 0.f;
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) lens_term_ff_at<MASS>(L[k], m[k], x1, x2, A1h, A1l, A2h, A2l);
+  }
+  for (; l < n; l += stride) lens_term_ff<MASS>(f, l, x1, x2, A1h, A1l, A2h, A2l);
 }
 
 // Lanes per listed ray of the float-float evaluation: one warp for fields of up to kFfSmallField
@@ -90,8 +116,7 @@ template <bool MASS>
 __device__ __forceinline__ float4 deflect_ff_group(const FieldDev& f, float x1, float x2, int W, int w, float4* red) {
   const int lane = threadIdx.x & 31;
   float A1h = 0.f, A1l = 0.f, A2h = 0.f, A2l = 0.f;
-  const int n = f.n_lens, stride = 32 * W;
-  for (int l = w * 32 + lane; l < n; l += stride) lens_term_ff<MASS>(f, l, x1, x2, A1h, A1l, A2h, A2l);
+  lens_terms_ff_strided<MASS>(f, w * 32 + lane, 32 * W, f.n_lens, x1, x2, A1h, A1l, A2h, A2l);
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) {
     const float b1h = __shfl_down_sync(0xffffffffu, A1h, off);

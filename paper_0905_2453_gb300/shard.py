@@ -28,16 +28,19 @@ def row_partition(n_rows: int, world: int) -> List[Tuple[int, int]]:
     return out
 
 
-def shoot_sharded(shoot_rows: Callable, n_rows: int, counts, out_of_window, rank: int, world: int, group=None):
-    """Shoot this rank's row block into ``counts``/``out_of_window`` and sum them over ranks in place.
+def shoot_sharded(shoot_rows: Callable, n_rows: int, counts, out_of_window, rank: int, world: int, group=None,
+                  row_begin: int = 0):
+    """Shoot this rank's block of rows [row_begin, row_begin + n_rows) into ``counts``/``out_of_window`` and sum
+    them over ranks in place.
 
     shoot_rows(begin, end, counts, out_of_window) accumulates the rows' counts.
     counts: int32 tensor (uint32 bit patterns; the sum wraps like uint32);
     out_of_window: int64 tensor of one element.  Both must start at zero on every rank.
-    Returns this rank's row block.
+    Returns this rank's row block (grid rows).
     """
     import torch.distributed as dist
     b, e = row_partition(n_rows, world)[rank]
+    b, e = b + row_begin, e + row_begin
     if e > b:
         shoot_rows(b, e, counts, out_of_window)
     if world > 1:

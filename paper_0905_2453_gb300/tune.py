@@ -4,7 +4,8 @@ The library carries kernels for several launch shapes (threads per CTA x rays pe
 thread x lenses per shared-memory stage, see ``rs_launch_configs``).  All of them
 compute bitwise identical results, so the choice only affects speed.  ``autotune`` times every shape on a
 proxy run (a block of the workload's own grid rows; for fields larger than the proxy,
-one whole wave of CTAs per launch) with CUDA events, selects the fastest with
+one whole wave of CTAs per launch, and the proxy's best three again on the field itself
+where a whole-wave unit of it is affordable) with CUDA events, selects the fastest with
 ``rs_set_launch_config`` and caches the choice in a JSON file keyed
 by (GPU name, library version, mass mode, lens-count bucket, row-length bucket).  This replaces the
 paper's occupancy-calculator choice of 128 or 256 threads (Section 2.2).  Fields of more than
@@ -48,10 +49,12 @@ def wave_rows(n0: int, block: int, rpt: int, sms: int, ctas_per_sm: int = 2) -> 
 
 
 def shape_rates(field, grid, cache_path: str = None) -> dict:
-    """Steady-state interactions/s of every launch shape ("block x rpt x lens_tile") from the tuner's cache
-    entry for (field, grid) ({} if the pair was never tuned)."""
+    """Steady-state interactions/s per launch shape ("block x rpt x lens_tile") from the tuner's cache entry for
+    (field, grid): the shapes verified on the field itself if any, else every shape on the proxy ({} if the pair
+    was never tuned)."""
     cache = _load(cache_path or os.environ.get("RS_TUNE_CACHE", DEFAULT_CACHE))
-    return dict(cache.get(cache_key(field, grid), {}).get("interactions_per_s", {}))
+    entry = cache.get(cache_key(field, grid), {})
+    return dict(entry.get("field_interactions_per_s") or entry.get("interactions_per_s", {}))
 
 
 def _load(path):
@@ -62,8 +65,42 @@ def _load(path):
         return {}
 
 
+def _verify_on_field(field, grid, window, counts, st, rates, timings, shape_rows, has_mass, sms, n0, n1, n_lens,
+                     verify_interactions, top=3):
+    """Rates on the field itself ({} if unaffordable) of the proxy's best `top` shapes, where a whole-wave unit of
+    its rows costs at most verify_interactions: one and two units, rated by the difference (the steady state of
+    many waves).  The proxy ranks shapes within a few percent only; a unit of the field settles it."""
+    cands = sorted(rates, key=rates.get, reverse=True)[:top]
+    verified = {}
+    field_handle = field.handle
+    for name in cands:
+        block, rpt, tile = (int(v) for v in name.split("x"))
+        unit = wave_rows(n0, block, rpt, sms, rs_launch_occupancy(has_mass, block, rpt, tile))
+        if 2 * unit > n1 or unit * n0 * n_lens > verify_interactions:
+            return {}
+        rs_set_launch_config(has_mass, block, rpt, tile)
+        warps = block // 32
+        r0 = (n1 - 2 * unit) // 2 // warps * warps
+
+        def timed(rows):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            rs_shoot_rows(field_handle, grid, r0, r0 + rows, window, counts, None, st)
+            e1.record(st)
+            e1.synchronize()
+            return e0.elapsed_time(e1)
+
+        timed(unit)  # warm-up
+        t1, t2 = timed(unit), timed(2 * unit)
+        verified[name] = (unit * n0 * n_lens / max(t2 - t1, 1e-6) * 1e3 if t2 > t1
+                          else 2 * unit * n0 * n_lens / max(t2, 1e-6) * 1e3)
+        timings[name + "/field"], shape_rows[name + "/field"] = t2, [unit, 2 * unit]
+    return verified
+
+
 def autotune(field, grid, window, min_rays: float = 8e6, max_interactions: float = 3e11, reps: int = 3,
-             cache_path: str = None, force: bool = False, stream=None, max_proxy_lenses: int = 1 << 16):
+             cache_path: str = None, force: bool = False, stream=None, max_proxy_lenses: int = 1 << 16,
+             verify_interactions: float = 2e12):
     """Pick and set the fastest launch shape for this (field, grid); returns (block, rpt, lens_tile,
     timings_ms) with each shape's time for its own (largest) proxy block of rows."""
     cache_path = cache_path or os.environ.get("RS_TUNE_CACHE", DEFAULT_CACHE)
@@ -128,14 +165,19 @@ def autotune(field, grid, window, min_rays: float = 8e6, max_interactions: float
                 rs_shoot_rows(proxy.handle, grid, 0, rows, window, counts, None, st)  # warm-up
                 timings[name], shape_rows[name] = timed(rows), [rows]
                 rates[name] = rows * n0 * n_proxy / max(timings[name], 1e-6) * 1e3
+        field_rates = {}
+        if proxy is not field:
+            field_rates = _verify_on_field(field, grid, window, counts, st, rates, timings, shape_rows, has_mass, sms,
+                                           n0, n1, n_lens, verify_interactions)
     finally:
         if proxy is not field:
             proxy.close()
-    best = max(rates, key=rates.get)
+    ranked = field_rates or rates
+    best = max(ranked, key=ranked.get)
     b, r, t = (int(v) for v in best.split("x"))
     rs_set_launch_config(has_mass, b, r, t)
     cache[key] = {"block": b, "rpt": r, "tile": t, "ms": timings, "rows": shape_rows, "interactions_per_s": rates,
-                  "proxy_lenses": n_proxy}
+                  "field_interactions_per_s": field_rates, "proxy_lenses": n_proxy}
     try:
         os.makedirs(os.path.dirname(cache_path), exist_ok=True)
         tmp = cache_path + f".tmp{os.getpid()}"

@@ -153,6 +153,28 @@ def test_row_sharding_accumulates_bitwise():
     assert np.array_equal(counts.cpu().numpy().view(np.uint32), full) and int(oow.item()) == oow_full
 
 
+def test_sharded_step_single_process_equals_plain_shoot():
+    """shoot_sharded with the device row shooter (one process: no collective) on a block of rows equals
+    rs_shoot_rows of the block, bit for bit (the benchmark's N = 1 sharded step)."""
+    m = rs()
+    from paper_0905_2453_gb300.shard import device_row_shooter, shoot_sharded
+    spec = ri.disc_field("shard1", 700, 0.5, 0.1, 0.25, 600, 96, seed=12, mass="salpeter")
+    f = m.Field.from_spec(spec)
+    try:
+        npix = (int(spec.window.npix[1]), int(spec.window.npix[0]))
+        c1 = torch.zeros(npix, dtype=torch.int32, device=dev())
+        o1 = torch.zeros(1, dtype=torch.int64, device=dev())
+        c2, o2 = torch.zeros_like(c1), torch.zeros_like(o1)
+        blk = shoot_sharded(device_row_shooter(f, spec.grid, spec.window), 200, c1, o1, 0, 1, row_begin=150)
+        m.rs_shoot_rows(f.handle, spec.grid, 150, 350, spec.window, c2, o2)
+        torch.cuda.synchronize()
+        assert blk == (150, 350)
+        assert torch.equal(c1, c2) and int(o1.item()) == int(o2.item())
+        assert int(c1.sum().item()) + int(o1.item()) == 200 * spec.grid.n[0]
+    finally:
+        f.close()
+
+
 RAGGED_LENS_COUNTS = (1, 2, 3, 31, 32, 33, 63, 64, 65, 127, 255, 256, 257, 511, 512, 513, 1023, 1024, 1025, 1279)
 
 

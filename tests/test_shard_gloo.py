@@ -23,7 +23,7 @@ def _free_port():
     return p
 
 
-def _worker(rank, world, port, q):
+def _worker(rank, world, port, q, row_begin=0, n_rows=None):
     import sys
     sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
     import oracle
@@ -40,7 +40,8 @@ def _worker(rank, world, port, q):
             _, oo = oracle.shoot_field(f, rows=(b, e), counts=cn)
             o += oo
 
-        blk = shoot_sharded(shoot_rows, f.grid.n[1], counts, oow, rank, world)
+        blk = shoot_sharded(shoot_rows, f.grid.n[1] if n_rows is None else n_rows, counts, oow, rank, world,
+                            row_begin=row_begin)
         q.put((rank, blk, counts.numpy().copy(), int(oow.item())))
     finally:
         dist.destroy_process_group()
@@ -76,6 +77,30 @@ def test_two_rank_map_equals_single_process():
     ref, oow_ref = oracle.shoot_field(f)
     blocks = sorted(r[1] for r in res)
     assert blocks == [(0, 49), (49, 97)]
+    for _, _, counts, oow in res:
+        assert np.array_equal(counts.view(np.uint32), ref)
+        assert oow == oow_ref
+
+
+def test_two_rank_block_with_row_offset_equals_single_process():
+    """The benchmark's sharded step: a block of rows [row_begin, row_begin + n) split over two ranks and summed
+    equals one process shooting the block."""
+    import oracle
+    import rs_inputs as ri
+    world, row_begin, n = 2, 17, 44
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_worker, args=(r, world, port, q, row_begin, n)) for r in range(world)]
+    for p in procs:
+        p.start()
+    res = [q.get(timeout=300) for _ in range(world)]
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    f = ri.disc_field("shard", 150, 0.5, 0.1, 0.2, 97, 48, seed=4, mass="salpeter")
+    ref, oow_ref = oracle.shoot_field(f, rows=(row_begin, row_begin + n))
+    assert sorted(r[1] for r in res) == [(17, 39), (39, 61)]
     for _, _, counts, oow in res:
         assert np.array_equal(counts.view(np.uint32), ref)
         assert oow == oow_ref
