@@ -225,6 +225,33 @@ int rs_shoot_streamed(const float* h_lens_xy, const float* h_masses, int64_t n_l
 int rs_set_staged_state_budget(uint64_t bytes);  /* also used by rs_shoot_streamed */
 
 /*
+ * Partition passes -- the steps of rs_shoot_staged with caller-owned buffers, for lens partitions held
+ * by different processes or GPUs (Section 3.3's pipeline of partially deflected rays from GPU to GPU).
+ * For rows [row_begin, row_end) of grid g, the holder of partition p calls rs_partition_pass with the
+ * ray block's state buffer, after the holder of partition p - 1 (first = 1 for p = 0: the state starts
+ * from zero); any transport (e.g. NCCL send/recv of the buffer) carries the state between them.  The
+ * last partition's pass (last = 1) maps and bins the rays into d_counts / d_out_of_window (accumulated)
+ * instead of storing the state; with certified binning on it lists the rays to re-evaluate in d_list.
+ * Those rays then go around the partitions once more: every holder calls rs_partition_recheck with the
+ * list (a copy of the last holder's) and the float-float buffer d_ff in the same order (first = 1 for
+ * partition 0), and the last call (last = 1) bins them.  With the same partitions, the counts equal those
+ * of rs_shoot_staged bit for bit.  Partitions as rs_shoot_staged (multiples of 256 lenses but the last;
+ * masses given to all or to none); weighted = 1 runs every pass with per-lens masses (required when any
+ * partition's masses are not all 1; every pass and re-evaluation of a shoot must use the same value).
+ *   rs_partition_buffer_bytes: device bytes of the state (28 per ray, padded to CTA tiles), of the list
+ *     (16 + 8 per entry; capacity max(4096, rays/32)) and of d_ff (16 per entry) for the row block.
+ * Calls are asynchronous on `stream`; buffers are caller-owned device memory.
+ */
+int rs_partition_buffer_bytes(const rs_ray_grid* g, int64_t row_begin, int64_t row_end, uint64_t* state_bytes,
+                              uint64_t* list_bytes, uint64_t* ff_bytes);
+int rs_partition_pass(rs_field_t part, int weighted, const rs_ray_grid* g, int64_t row_begin, int64_t row_end,
+                      const rs_window* w, void* d_state, int first, int last, uint32_t* d_counts,
+                      uint64_t* d_out_of_window, void* d_list, void* stream);
+int rs_partition_recheck(rs_field_t part, int weighted, const rs_ray_grid* g, int64_t row_begin, int64_t row_end,
+                         const rs_window* w, const void* d_list, void* d_ff, int first, int last, uint32_t* d_counts,
+                         uint64_t* d_out_of_window, void* stream);
+
+/*
  * rs_trace -- source positions of listed rays through the float32 path, for checks.
  *   d_ray_ij : int64[2*k] device, (i, j) per ray (each within the grid).
  *   d_y      : double[2*k] device, receives (y1, y2) per ray (Eq. 6).

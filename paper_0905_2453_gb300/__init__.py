@@ -34,6 +34,7 @@ __all__ = [
     "rs_create_moving_field", "rs_field_set_time", "rs_field_time", "rs_shoot_staged", "rs_shoot_streamed",
     "rs_set_staged_state_budget", "rs_set_alloc_failure", "rs_light_curve_plan_create", "rs_light_curve_plan_samples",
     "rs_light_curve_plan_launch", "rs_light_curve_plan_destroy", "rs_create_field_view", "rs_device_code_version", "rs_launch_occupancy",
+    "rs_partition_buffer_bytes", "rs_partition_pass", "rs_partition_recheck",
 ]
 
 RS_OK, RS_EINVAL, RS_ENOMEM, RS_ECUDA, RS_EOVERFLOW, RS_ETIMEOUT = 0, 1, 2, 3, 4, 5
@@ -49,6 +50,7 @@ EXPORTED_SYMBOLS = (
     "rs_set_staged_state_budget", "rs_set_alloc_failure",
     "rs_light_curve_plan_create", "rs_light_curve_plan_samples", "rs_light_curve_plan_launch",
     "rs_light_curve_plan_destroy", "rs_create_field_view", "rs_device_code_version", "rs_launch_occupancy",
+    "rs_partition_buffer_bytes", "rs_partition_pass", "rs_partition_recheck",
 )
 
 
@@ -161,6 +163,10 @@ def load():
         "rs_get_launch_config": ([i32, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32)], i32),
         "rs_launch_configs": ([ctypes.POINTER(i32), i32, ctypes.POINTER(i32)], i32),
         "rs_launch_occupancy": ([i32, i32, i32, i32, ctypes.POINTER(i32)], i32),
+        "rs_partition_buffer_bytes": ([gp, i64, i64, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64),
+                                       ctypes.POINTER(ctypes.c_uint64)], i32),
+        "rs_partition_pass": ([vp, i32, gp, i64, i64, wp, vp, i32, i32, vp, vp, vp, vp], i32),
+        "rs_partition_recheck": ([vp, i32, gp, i64, i64, wp, vp, vp, i32, i32, vp, vp, vp], i32),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -371,6 +377,55 @@ def rs_shoot_staged(handles, grid, row_begin: int, row_end: int, window, counts,
     g, w = _cgrid(grid), _cwin(window)
     _check(load().rs_shoot_staged(n, H, ctypes.byref(g), int(row_begin), int(row_end), ctypes.byref(w), pc, po,
                                   _stream(stream)), "rs_shoot_staged")
+
+
+def rs_partition_buffer_bytes(grid, row_begin: int, row_end: int):
+    """(state, list, float-float) device buffer bytes of a partition pass over rows [row_begin, row_end)."""
+    a, b, c = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_uint64()
+    g = _cgrid(grid)
+    _check(load().rs_partition_buffer_bytes(ctypes.byref(g), int(row_begin), int(row_end), ctypes.byref(a),
+                                            ctypes.byref(b), ctypes.byref(c)), "rs_partition_buffer_bytes")
+    return int(a.value), int(b.value), int(c.value)
+
+
+def _byte_ptr(t, name, nbytes):
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or not t.is_contiguous():
+        raise TypeError(f"{name} must be a contiguous CUDA tensor")
+    if t.numel() * t.element_size() < nbytes:
+        raise ValueError(f"{name} holds {t.numel() * t.element_size()} bytes, needs {nbytes}")
+    return t.data_ptr()
+
+
+def rs_partition_pass(handle, weighted: bool, grid, row_begin: int, row_end: int, window, state, first: bool,
+                      last: bool, counts=None, out_of_window=None, lst=None, stream=None):
+    """One lens partition's pass over rows [row_begin, row_end): adds its lenses to `state`; the last one maps
+    and bins into counts / out_of_window and lists the rays to re-evaluate in `lst` (device byte buffers of
+    rs_partition_buffer_bytes' sizes)."""
+    sb, lb, _ = rs_partition_buffer_bytes(grid, row_begin, row_end)
+    npx = int(window.npix[0]) * int(window.npix[1])
+    pc = _dptr(counts, _COUNT_DTYPES, "counts", npx) if last else None
+    po = _dptr(out_of_window, _OOW_DTYPES, "out_of_window", 1) if last else None
+    g, w = _cgrid(grid), _cwin(window)
+    _check(load().rs_partition_pass(handle, int(bool(weighted)), ctypes.byref(g), int(row_begin), int(row_end),
+                                    ctypes.byref(w), _byte_ptr(state, "state", sb), int(bool(first)), int(bool(last)),
+                                    pc, po, _byte_ptr(lst, "list", lb) if last else None, _stream(stream)),
+           "rs_partition_pass")
+
+
+def rs_partition_recheck(handle, weighted: bool, grid, row_begin: int, row_end: int, window, lst, ff, first: bool,
+                         last: bool, counts=None, out_of_window=None, stream=None):
+    """One lens partition's float-float share of the listed rays (added to ff); the last call bins them."""
+    _, lb, fb = rs_partition_buffer_bytes(grid, row_begin, row_end)
+    npx = int(window.npix[0]) * int(window.npix[1])
+    pc = _dptr(counts, _COUNT_DTYPES, "counts", npx) if last else None
+    po = _dptr(out_of_window, _OOW_DTYPES, "out_of_window", 1) if last else None
+    g, w = _cgrid(grid), _cwin(window)
+    _check(load().rs_partition_recheck(handle, int(bool(weighted)), ctypes.byref(g), int(row_begin), int(row_end),
+                                       ctypes.byref(w), _byte_ptr(lst, "list", lb), _byte_ptr(ff, "ff", fb),
+                                       int(bool(first)), int(bool(last)), pc, po, _stream(stream)),
+           "rs_partition_recheck")
 
 
 def rs_shoot_streamed(lens_xy, masses, kappa_c: float, gamma: float, lenses_per_pass: int, grid, row_begin: int,

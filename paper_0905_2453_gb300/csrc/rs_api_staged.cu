@@ -260,4 +260,96 @@ int rs_shoot_streamed(const float* h_lens_xy, const float* h_masses, int64_t n_l
   return RS_OK;
 }
 
+// ------------------------------------------------------------------------------------------------ partition passes
+//
+// The steps of a lens-partitioned shoot with caller-owned buffers, for partitions held by different
+// processes (Section 3.3 across GPUs): the per-ray state, the list of rays to re-evaluate and their
+// float-float partial deflections travel between the holders of the partitions by any transport.
+
+int rs_partition_buffer_bytes(const rs_ray_grid* g, int64_t row_begin, int64_t row_end, uint64_t* state_bytes,
+                              uint64_t* list_bytes, uint64_t* ff_bytes) {
+  int rc;
+  if ((rc = check_grid(g)) != RS_OK) return rc;
+  if (row_begin < 0 || row_end < row_begin || row_end > g->n[1])
+    return fail(RS_EINVAL, "row range [%lld, %lld) outside [0, %lld]", (long long)row_begin, (long long)row_end,
+                (long long)g->n[1]);
+  const int64_t rows = row_end - row_begin;
+  if (g->n[0] > 0 && rows > 0 && (rows > ((int64_t)1 << 32) / g->n[0] || rows * g->n[0] >= ((int64_t)1 << 32)))
+    return fail(RS_EOVERFLOW, "a pass covers at most 2^32 - 1 rays");
+  const unsigned cap = rsint::recheck_capacity(rows * g->n[0]);
+  if (state_bytes) *state_bytes = rsint::staged_state_bytes(rows, g->n[0]);
+  if (list_bytes) *list_bytes = 16 + sizeof(uint2) * (uint64_t)cap;
+  if (ff_bytes) *ff_bytes = sizeof(float4) * (uint64_t)cap;
+  return RS_OK;
+}
+
+namespace {
+
+int partition_desc(rs_field_t part, int weighted, const rs_ray_grid* g, int64_t row_begin, int64_t row_end,
+                   const rs_window* w, uint32_t* d_counts, uint64_t* d_oow, bool binning, ShootDesc* d) {
+  if (!part) return fail(RS_EINVAL, "partition field is NULL");
+  int rc;
+  if ((rc = check_grid(g)) != RS_OK) return rc;
+  if ((rc = check_window(w)) != RS_OK) return rc;
+  if (binning && !d_counts) return fail(RS_EINVAL, "d_counts is NULL");
+  if (row_begin < 0 || row_end < row_begin || row_end > g->n[1])
+    return fail(RS_EINVAL, "row range [%lld, %lld) outside [0, %lld]", (long long)row_begin, (long long)row_end,
+                (long long)g->n[1]);
+  if (weighted && !part->dev.mass2)
+    return fail(RS_EINVAL, "weighted passes need partitions created with masses (all partitions or none)");
+  if (!weighted && part->dev.has_mass)
+    return fail(RS_EINVAL, "the partition's masses are not all 1: every pass of the shoot must be weighted");
+  if ((rc = check_field_device(part)) != RS_OK) return rc;
+  if ((rc = fill_desc(part, g, row_begin, row_end, w, d_counts, d_oow, d)) != RS_OK) return rc;
+  d->f.has_mass = weighted ? 1 : 0;
+  return RS_OK;
+}
+
+}  // namespace
+
+int rs_partition_pass(rs_field_t part, int weighted, const rs_ray_grid* g, int64_t row_begin, int64_t row_end,
+                      const rs_window* w, void* d_state, int first, int last, uint32_t* d_counts,
+                      uint64_t* d_out_of_window, void* d_list, void* stream) {
+  ShootDesc d;
+  int rc;
+  if ((rc = partition_desc(part, weighted, g, row_begin, row_end, w, d_counts, d_out_of_window, last != 0, &d)) !=
+      RS_OK)
+    return rc;
+  if (d.n_rows == 0 || d.n0 == 0) return RS_OK;
+  if (!d_state) return fail(RS_EINVAL, "d_state is NULL");
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaSuccess;
+  if (last && g_certify) {
+    if (!d_list) return fail(RS_EINVAL, "d_list is NULL (certified binning is on)");
+    d.rc_cap = rsint::recheck_capacity(d.n_rows * d.n0);
+    d.rc_count = reinterpret_cast<unsigned int*>(d_list);
+    d.rc_list = reinterpret_cast<uint2*>(reinterpret_cast<char*>(d_list) + 16);
+    e = cudaMemsetAsync(d.rc_count, 0, sizeof(unsigned int), s);
+  }
+  if (e == cudaSuccess) e = rsint::launch_staged(d, reinterpret_cast<uint64_t*>(d_state), first != 0, last != 0, s);
+  if (e != cudaSuccess) return cuda_fail(e, "partition pass launch");
+  return RS_OK;
+}
+
+int rs_partition_recheck(rs_field_t part, int weighted, const rs_ray_grid* g, int64_t row_begin, int64_t row_end,
+                         const rs_window* w, const void* d_list, void* d_ff, int first, int last, uint32_t* d_counts,
+                         uint64_t* d_out_of_window, void* stream) {
+  ShootDesc d;
+  int rc;
+  if ((rc = partition_desc(part, weighted, g, row_begin, row_end, w, d_counts, d_out_of_window, last != 0, &d)) !=
+      RS_OK)
+    return rc;
+  if (d.n_rows == 0 || d.n0 == 0) return RS_OK;
+  if (!d_list || !d_ff) return fail(RS_EINVAL, "d_list / d_ff is NULL");
+  const unsigned cap = rsint::recheck_capacity(d.n_rows * d.n0);
+  const unsigned* count = reinterpret_cast<const unsigned int*>(d_list);
+  const uint2* list = reinterpret_cast<const uint2*>(reinterpret_cast<const char*>(d_list) + 16);
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  const int grid = recheck_grid(part->device);
+  cudaError_t e = rsint::launch_recheck_part(d, list, count, cap, reinterpret_cast<float4*>(d_ff), first != 0, grid, s);
+  if (e == cudaSuccess && last) e = rsint::launch_recheck_bin(d, list, count, cap, reinterpret_cast<float4*>(d_ff), grid, s);
+  if (e != cudaSuccess) return cuda_fail(e, "partition re-evaluation launch");
+  return RS_OK;
+}
+
 }  // extern "C"
