@@ -510,20 +510,21 @@ __device__ __forceinline__ void lens_pair_all(uint32_t lbase, uint32_t mbase, ui
 
 // Row table for the current lens tile: entry (r, l) = {d2, d2, d2^2, d2^2} with d2 = x2(row r) - x2(lens l),
 // the same float32 operations a thread would otherwise repeat for every lens.
+// (Only the tile's cnt lenses: the last tile of a small field may hold far fewer than TILE.)
 template <int TILE, int ROWS>
-__device__ __forceinline__ void build_row_table(LensSmem<TILE, ROWS>& sm, int b) {
+__device__ __forceinline__ void build_row_table(LensSmem<TILE, ROWS>& sm, int b, int cnt) {
   constexpr int BLOCK = ROWS * 32;
-#pragma unroll 4
-  for (int e = threadIdx.x; e < ROWS * TILE; e += BLOCK) {
-    const int r = e / TILE, l = e - (e / TILE) * TILE;
-    const uint64_t X2D = f2_pack(sm.x2row[r], sm.x2row[r]);
+  for (int l = threadIdx.x; l < cnt; l += BLOCK) {
     const float y = sm.lens4[b][l].z;
-    const uint64_t D2 = f2_sub(X2D, f2_pack(y, y));
-    const uint64_t S2 = f2_mul(D2, D2);
-    float d0, d1, s0, s1;
-    f2_unpack(D2, d0, d1);
-    f2_unpack(S2, s0, s1);
-    sm.rowtab[r][l] = make_float4(d0, d1, s0, s1);
+#pragma unroll
+    for (int r = 0; r < ROWS; ++r) {
+      const uint64_t D2 = f2_sub(f2_pack(sm.x2row[r], sm.x2row[r]), f2_pack(y, y));
+      const uint64_t S2 = f2_mul(D2, D2);
+      float d0, d1, s0, s1;
+      f2_unpack(D2, d0, d1);
+      f2_unpack(S2, s0, s1);
+      sm.rowtab[r][l] = make_float4(d0, d1, s0, s1);
+    }
   }
 }
 
@@ -580,7 +581,7 @@ __device__ __forceinline__ bool deflect_accumulate(const FieldDev& f, const uint
     }
     const int cnt = min(TILE, n - t * TILE);
     if (ROW) {
-      build_row_table<TILE, ROWS>(sm, b);
+      build_row_table<TILE, ROWS>(sm, b, cnt);
       __syncthreads();
     }
     if constexpr (NS::kOn) {
@@ -625,6 +626,12 @@ __device__ __forceinline__ bool deflect_accumulate(const FieldDev& f, const uint
 #pragma unroll
       for (int q = 0; q < NP; ++q) P1[q] = P2[q] = 0ull;
       int p = 0;
+      for (; g + 2 * p + 8 <= cnt; p += 4) {  // whole blocks of four pairs first (p = 0 mod 4 at each)
+        lens_pair_all<NP, mont_pair<MASS>(0), MASS, ROW>(lbase, mbase, rt, g + 2 * p + 0, X1, X2, P1, P2);
+        lens_pair_all<NP, mont_pair<MASS>(1), MASS, ROW>(lbase, mbase, rt, g + 2 * p + 2, X1, X2, P1, P2);
+        lens_pair_all<NP, mont_pair<MASS>(2), MASS, ROW>(lbase, mbase, rt, g + 2 * p + 4, X1, X2, P1, P2);
+        lens_pair_all<NP, mont_pair<MASS>(3), MASS, ROW>(lbase, mbase, rt, g + 2 * p + 6, X1, X2, P1, P2);
+      }
       for (; g + 2 * p + 1 < cnt; ++p) {
         if (mont_pair<MASS>(p))
           lens_pair_all<NP, true, MASS, ROW>(lbase, mbase, rt, g + 2 * p, X1, X2, P1, P2);
@@ -810,9 +817,37 @@ __device__ __forceinline__ int ff_pixel(float x, float lh, float ll, float ah, f
 }
 
 // ----------------------------------------------------------------------------------------------
+// One axis of Eq. 6 and of the pixel coordinate in float32 only: uf = ((lh x - ah) - loh) * sch, and a bound E on
+// |uf - u| for the exact u of (lam, alpha, lo, sc): the four roundings (<= u each of the magnitudes involved,
+// A = |lh x| + |ah| + |loh| in pixel units) and the dropped low parts (|ll x| <= u |lh x|, |lol| <= u |loh|,
+// |scl| <= u sch, and |al| itself) sum to <= 5u (A + |uf|) + |al| sch; E = 2^-21 (A + |uf|) + |al| sch is that
+// with more than 1.5x to spare, which also covers the float32 rounding of E.
+__device__ __forceinline__ float fast_pixel(float x, float lh, float ah, float al, float loh, float sch, float& e) {
+  const float pr = __fmul_rn(lh, x);
+  const float uf = __fmul_rn(__fsub_rn(__fsub_rn(pr, ah), loh), sch);
+  e = __fmaf_rn(fabsf(al), sch, 0x1p-21f * __fmaf_rn(fabsf(pr) + fabsf(ah) + fabsf(loh), sch, fabsf(uf)));
+  return uf;
+}
+
+// Certain decision of one axis from u = p + f (f in [0, 1)) known to within m (m < 1/2): inside pixel p of
+// the np pixels, or outside the window on this axis.
+__device__ __forceinline__ bool axis_inside(int p, float f, float m, int np) {
+  return p >= 0 && p < np && f >= m && f <= 1.f - m;
+}
+__device__ __forceinline__ bool axis_outside(int p, float f, float m, int np) {
+  // u + m < 0 iff p <= -2, or p = -1 and 1 - f > m; u - m >= np iff p > np, or p = np and f >= m
+  return p <= -2 || (p == -1 && 1.f - f > m) || p > np || (p == np && f >= m);
+}
+
+// ----------------------------------------------------------------------------------------------
 // Eq. 6 and binning of a thread's RPT rays (ray k at grid column i_base + STRIDE k of call row
 // jrel): counts, the out-of-window count, and, with certified binning, the list of rays to
 // re-evaluate in float-float.  Every lane of the warp must call it (warp-aggregated atomics).
+//
+// With certified binning most rays are decided from a float32 evaluation of u with a bound on its
+// own rounding (fast_pixel): certain when u's band, widened by that bound, lies inside one pixel or
+// outside the window.  The others take the float-float evaluation (ff_pixel) and its narrower margin,
+// and those still uncertain are listed for the float-float re-evaluation over the lenses.
 // ----------------------------------------------------------------------------------------------
 template <int RPT, int STRIDE>
 __device__ __forceinline__ void bin_rays(const ShootDesc& d, const float (&x1)[RPT], const float (&x2)[RPT],
@@ -820,32 +855,54 @@ __device__ __forceinline__ void bin_rays(const ShootDesc& d, const float (&x1)[R
                                          const float (&a2l)[RPT], const float (&sig)[RPT], const float (&tn)[RPT],
                                          const bool (&valid)[RPT], int64_t jrel, int64_t i_base, int lane) {
   unsigned oow_lane = 0;
+  const bool certify = d.rc_list != nullptr;
 #pragma unroll
   for (int k = 0; k < RPT; ++k) {
-    // Eq. 6 and u = (y - lo) * npix / (hi - lo) in float-float (~2^-44 relative): pixel index p and
-    // fraction f of u, and the bound eu on the float-float rounding (pixel units)
-    int p1, p2;
-    float f1, f2, eu1, eu2;
-    const int st1 = ff_pixel(x1[k], d.lam1h, d.lam1l, a1h[k], a1l[k], d.lo0h, d.lo0l, d.sc0h, d.sc0l, p1, f1, eu1);
-    const int st2 = ff_pixel(x2[k], d.lam2h, d.lam2l, a2h[k], a2l[k], d.lo1h, d.lo1l, d.sc1h, d.sc1l, p2, f2, eu2);
-    const bool inwin = st1 == kUOk && st2 == kUOk && (p1 >= 0) && (p1 < d.np0) && (p2 >= 0) && (p2 < d.np1);
+    int p1 = -1, p2 = -1;
+    bool inwin = false, decided = false, need = false;
+    float band = 0.f;
+    if (certify) {
+      band = band_halfwidth(sig[k], tn[k], d.f.lamabs, x1[k], x2[k]);
+      float e1, e2;
+      const float u1 = fast_pixel(x1[k], d.lam1h, a1h[k], a1l[k], d.lo0h, d.sc0h, e1);
+      const float u2 = fast_pixel(x2[k], d.lam2h, a2h[k], a2l[k], d.lo1h, d.sc1h, e2);
+      const float m1 = band * d.scf0 + e1 + 1e-7f, m2 = band * d.scf1 + e2 + 1e-7f;
+      if (fabsf(u1) < 0x1p22f && fabsf(u2) < 0x1p22f && m1 < 0.5f && m2 < 0.5f) {  // NaN fails
+        const float k1 = floorf(u1), k2 = floorf(u2);
+        const int q1 = (int)k1, q2 = (int)k2;
+        const float f1 = __fsub_rn(u1, k1), f2 = __fsub_rn(u2, k2);  // exact for |u| < 2^22
+        const bool in_sure = axis_inside(q1, f1, m1, d.np0) && axis_inside(q2, f2, m2, d.np1);
+        const bool out_sure = axis_outside(q1, f1, m1, d.np0) || axis_outside(q2, f2, m2, d.np1);
+        decided = in_sure || out_sure;
+        inwin = in_sure;
+        p1 = q1;
+        p2 = q2;
+      }
+    }
+    if (!decided) {
+      // Eq. 6 and u = (y - lo) * npix / (hi - lo) in float-float (~2^-44 relative): pixel index p and
+      // fraction f of u, and the bound eu on the float-float rounding (pixel units)
+      float f1, f2, eu1, eu2;
+      const int st1 = ff_pixel(x1[k], d.lam1h, d.lam1l, a1h[k], a1l[k], d.lo0h, d.lo0l, d.sc0h, d.sc0l, p1, f1, eu1);
+      const int st2 = ff_pixel(x2[k], d.lam2h, d.lam2l, a2h[k], a2l[k], d.lo1h, d.lo1l, d.sc1h, d.sc1l, p2, f2, eu2);
+      inwin = st1 == kUOk && st2 == kUOk && (p1 >= 0) && (p1 < d.np0) && (p2 >= 0) && (p2 < d.np1);
+      if (certify) {
+        // Certain: the band [u - du, u + du] lies inside one pixel of the window, or outside the window
+        // on some axis.  Margins: the band in pixel units, the float-float rounding, and 1e-7 for the
+        // float rounding of the fraction (margins below 1/2; wider bands are never certain).
+        const float m1 = band * d.scf0 + eu1 + 1e-7f, m2 = band * d.scf1 + eu2 + 1e-7f;
+        const bool ok1 = st1 == kUOk && m1 < 0.5f, ok2 = st2 == kUOk && m2 < 0.5f;
+        const bool out1 = ok1 && axis_outside(p1, f1, m1, d.np0);
+        const bool out2 = ok2 && axis_outside(p2, f2, m2, d.np1);
+        // a non-finite position is out of window by definition; |u| >= 2^22 is when the window is narrower
+        const bool out_sure = st1 == kUNaN || st2 == kUNaN || (st1 == kUFar && d.np0 <= (1 << 21)) ||
+                              (st2 == kUFar && d.np1 <= (1 << 21)) || out1 || out2;
+        const bool in_sure = inwin && ok1 && ok2 && axis_inside(p1, f1, m1, d.np0) && axis_inside(p2, f2, m2, d.np1);
+        need = valid[k] && !out_sure && !in_sure;
+      }
+    }
     bool bin_now = valid[k];
-    if (d.rc_list != nullptr) {
-      // Certain: the band [u - du, u + du] lies inside one pixel of the window, or outside the window
-      // on some axis.  Margins: the band in pixel units, the float-float rounding, and 1e-7 for the
-      // float rounding of the fraction.
-      const float band = band_halfwidth(sig[k], tn[k], d.f.lamabs, x1[k], x2[k]);
-      const float m1 = band * d.scf0 + eu1 + 1e-7f, m2 = band * d.scf1 + eu2 + 1e-7f;
-      // with u = p + f: u + m < 0 iff p <= -2, or p = -1 and 1 - f > m; u - m >= np iff p > np, or
-      // p = np and f >= m (margins below 1/2; wider bands are never certain)
-      const bool ok1 = st1 == kUOk && m1 < 0.5f, ok2 = st2 == kUOk && m2 < 0.5f;
-      const bool out1 = ok1 && (p1 <= -2 || (p1 == -1 && 1.f - f1 > m1) || p1 > d.np0 || (p1 == d.np0 && f1 >= m1));
-      const bool out2 = ok2 && (p2 <= -2 || (p2 == -1 && 1.f - f2 > m2) || p2 > d.np1 || (p2 == d.np1 && f2 >= m2));
-      // a non-finite position is out of window by definition; |u| >= 2^22 is when the window is narrower
-      const bool out_sure = st1 == kUNaN || st2 == kUNaN || (st1 == kUFar && d.np0 <= (1 << 21)) ||
-                            (st2 == kUFar && d.np1 <= (1 << 21)) || out1 || out2;
-      const bool in_sure = inwin && ok1 && ok2 && (f1 >= m1) && (f1 <= 1.f - m1) && (f2 >= m2) && (f2 <= 1.f - m2);
-      const bool need = valid[k] && !out_sure && !in_sure;
+    if (certify) {
       const unsigned mask = __ballot_sync(0xffffffffu, need);
       if (mask != 0u) {
         const int leader = __ffs(mask) - 1;

@@ -67,9 +67,9 @@ def _load(path):
 
 def _verify_on_field(field, grid, window, counts, st, rates, timings, shape_rows, has_mass, sms, n0, n1, n_lens,
                      verify_interactions, top=3):
-    """Rates on the field itself ({} if unaffordable) of the proxy's best `top` shapes, where a whole-wave unit of
-    its rows costs at most verify_interactions: one and two units, rated by the difference (the steady state of
-    many waves).  The proxy ranks shapes within a few percent only; a unit of the field settles it."""
+    """Rates on the field itself of those of the proxy's best `top` shapes whose whole-wave unit of rows costs at
+    most verify_interactions ({} if none): one and two units, rated by the difference (the steady state of many
+    waves).  The proxy ranks shapes within a few percent only; a unit of the field settles it."""
     cands = sorted(rates, key=rates.get, reverse=True)[:top]
     verified = {}
     field_handle = field.handle
@@ -77,7 +77,7 @@ def _verify_on_field(field, grid, window, counts, st, rates, timings, shape_rows
         block, rpt, tile = (int(v) for v in name.split("x"))
         unit = wave_rows(n0, block, rpt, sms, rs_launch_occupancy(has_mass, block, rpt, tile))
         if 2 * unit > n1 or unit * n0 * n_lens > verify_interactions:
-            return {}
+            continue  # this shape's whole-wave unit does not fit the grid or the budget
         rs_set_launch_config(has_mass, block, rpt, tile)
         warps = block // 32
         r0 = (n1 - 2 * unit) // 2 // warps * warps

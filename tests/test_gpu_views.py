@@ -128,7 +128,7 @@ def test_autotune_times_large_fields_on_a_prefix_view(tmp_path):
         assert m.rs_get_launch_config(False) == (b, r, t)
         # the proxy's best shapes were timed again on the field itself; the choice is the best of those
         field_rates = tune.shape_rates(f, spec.grid, cache_path=cache)
-        assert 1 <= len(field_rates) <= 3 and max(field_rates, key=field_rates.get) == f"{b}x{r}x{t}"
+        assert 1 <= len(field_rates) <= 3 and max(field_rates, key=field_rates.get) == f"{b}x{r}x{t}", field_rates
         entry = next(iter(json.load(open(cache)).values()))
         assert entry["proxy_lenses"] == 1024
         assert f.status() == m.RS_OK
