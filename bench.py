@@ -662,10 +662,27 @@ def run_batched(rs, torch, device, stream, reps=10):
     ratios = sorted(p / q for p, q in zip(tp, tb))
     inter = sum(s.interactions for s in specs)
     b.close()
+    # the same batch with a launch shape tuned per lens-count bucket
+    shapes = tune.batch_shapes(fields, grids, wins, stream=stream)
+    bs = rs.Batch(fields, grids, wins, shapes=shapes)
+    bs.launch(stream)
+    torch.cuda.synchronize(device)
+    same_shaped = all(torch.equal(bs.counts[k], counts_plain[k]) for k in range(len(specs)))
+    es = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(reps)]
+    for e in es:
+        e[0].record(stream)
+        bs.launch(stream)
+        e[1].record(stream)
+    torch.cuda.synchronize(device)
+    t_shaped = statistics.median(e[0].elapsed_time(e[1]) / 1e3 for e in es)
+    bs.close()
     for f in fields:
         f.close()
     sms = torch.cuda.get_device_properties(device).multi_processor_count
     return {"workload": "64 Salpeter fields, N* log-uniform [1e2,1e5], rays 1024^2-4096^2, maps 512^2-1024^2",
+            "per_bucket_shapes": {"maps_per_s": len(specs) / t_shaped, "speedup_vs_plain": t_plain / t_shaped,
+                                  "bitwise_equal": bool(same_shaped),
+                                  "shapes": sorted({"x".join(str(v) for v in sh) for sh in shapes})},
             "maps_per_s": len(specs) / t_batch, "plain_maps_per_s": len(specs) / t_plain,
             "speedup": t_plain / t_batch,
             "speedup_per_rep": {"min": ratios[0], "median": statistics.median(ratios), "max": ratios[-1]},
@@ -814,6 +831,8 @@ def run_section(args):
                "culled_full_map": run_zoom(rs, torch, device, stream, spec, factor=1, quarter=False)}
     elif args.section == "batch-small":
         out = {"small_fields": run_batched_small(rs, torch, device, stream)}
+    elif args.section == "batch":
+        out = {"batched": run_batched(rs, torch, device, stream, reps=args.batch_reps)}
     elif args.section == "staged":
         spec = workload(args.workload, seed=0)
         out = {"staged": run_staged(rs, torch, device, stream, spec)}
@@ -1062,7 +1081,8 @@ def main():
                     help="workloads of the configs sub-object (comma-separated: tiny, n1e4, n1e6, n1e8; the "
                          "headline workload is left out)")
     ap.add_argument("--no-configs", action="store_true")
-    ap.add_argument("--section", choices=["zoom", "light-curves", "frames", "staged", "batch-small", "configs"],
+    ap.add_argument("--section", choices=["zoom", "light-curves", "frames", "staged", "batch", "batch-small",
+                                          "configs"],
                     default=None,
                     help="run one secondary measurement alone and print its JSON object (for profiling)")
     ap.add_argument("--batch-reps", type=int, default=10)

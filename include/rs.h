@@ -315,6 +315,10 @@ int rs_magnification(const uint32_t* d_counts, const rs_ray_grid* g, const rs_wi
  *   zeroes the counts and the work counter and runs the persistent kernel.
  *   The fields must outlive the plan.  Unlike rs_shoot, the graph ZEROES the
  *   counts and out-of-window counters on every launch.
+ * rs_batch_create_shaped -- as rs_batch_create with a launch shape per field: shapes = host int[3 *
+ *   n_fields] of (block, rays per thread, lens tile) triples from rs_launch_configs (NULL: every field
+ *   takes its mass mode's rs_set_launch_config shape).  The items of each (shape, mass mode) form one
+ *   persistent launch of the graph; the counts are the same bits for every choice.
  * rs_batch_launch -- replay the plan's graph on `stream`.
  * rs_batch_destroy -- release the plan (synchronises first).  NULL is a no-op.
  * rs_shoot_batch -- create + launch + destroy in one call (synchronous).
@@ -324,6 +328,9 @@ typedef struct rs_batch* rs_batch_t;
 int rs_batch_create(int n_fields, const rs_field_t* fields, const rs_ray_grid* grids,
                     const rs_window* windows, uint32_t* const* d_counts, uint64_t* d_out_of_window,
                     rs_batch_t* out);
+int rs_batch_create_shaped(int n_fields, const rs_field_t* fields, const rs_ray_grid* grids,
+                           const rs_window* windows, uint32_t* const* d_counts, uint64_t* d_out_of_window,
+                           const int* shapes, rs_batch_t* out);
 int rs_batch_launch(rs_batch_t b, void* stream);
 int rs_batch_destroy(rs_batch_t b);
 int rs_shoot_batch(int n_fields, const rs_field_t* fields, const rs_ray_grid* grids,

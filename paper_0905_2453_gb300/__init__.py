@@ -34,7 +34,7 @@ __all__ = [
     "rs_create_moving_field", "rs_field_set_time", "rs_field_time", "rs_shoot_staged", "rs_shoot_streamed",
     "rs_set_staged_state_budget", "rs_set_alloc_failure", "rs_light_curve_plan_create", "rs_light_curve_plan_samples",
     "rs_light_curve_plan_launch", "rs_light_curve_plan_destroy", "rs_create_field_view", "rs_device_code_version", "rs_launch_occupancy",
-    "rs_partition_buffer_bytes", "rs_partition_pass", "rs_partition_recheck",
+    "rs_partition_buffer_bytes", "rs_partition_pass", "rs_partition_recheck", "rs_batch_create_shaped",
 ]
 
 RS_OK, RS_EINVAL, RS_ENOMEM, RS_ECUDA, RS_EOVERFLOW, RS_ETIMEOUT = 0, 1, 2, 3, 4, 5
@@ -50,7 +50,7 @@ EXPORTED_SYMBOLS = (
     "rs_set_staged_state_budget", "rs_set_alloc_failure",
     "rs_light_curve_plan_create", "rs_light_curve_plan_samples", "rs_light_curve_plan_launch",
     "rs_light_curve_plan_destroy", "rs_create_field_view", "rs_device_code_version", "rs_launch_occupancy",
-    "rs_partition_buffer_bytes", "rs_partition_pass", "rs_partition_recheck",
+    "rs_partition_buffer_bytes", "rs_partition_pass", "rs_partition_recheck", "rs_batch_create_shaped",
 )
 
 
@@ -152,6 +152,7 @@ def load():
         "rs_light_curve_plan_launch": ([vp, vp, vp, vp], i32),
         "rs_light_curve_plan_destroy": ([vp], i32),
         "rs_batch_create": ([i32, vp, vp, vp, vp, vp, ctypes.POINTER(vp)], i32),
+        "rs_batch_create_shaped": ([i32, vp, vp, vp, vp, vp, vp, ctypes.POINTER(vp)], i32),
         "rs_batch_launch": ([vp, vp], i32),
         "rs_batch_destroy": ([vp], i32),
         "rs_shoot_batch": ([i32, vp, vp, vp, vp, vp, vp], i32),
@@ -619,6 +620,19 @@ def rs_batch_create(handles, grids, windows, counts_list, out_of_window=None) ->
     return b.value
 
 
+def rs_batch_create_shaped(handles, grids, windows, counts_list, out_of_window=None, shapes=None) -> int:
+    """rs_batch_create with a launch shape (block, rays per thread, lens tile) per field (None: the defaults)."""
+    n, H, G, W, C, po = _batch_arrays(handles, grids, windows, counts_list, out_of_window)
+    S = None
+    if shapes is not None:
+        if len(shapes) != n:
+            raise ValueError("one launch shape per field")
+        S = (ctypes.c_int * (3 * n))(*[int(v) for sh in shapes for v in sh])
+    b = ctypes.c_void_p()
+    _check(load().rs_batch_create_shaped(n, H, G, W, C, po, S, ctypes.byref(b)), "rs_batch_create_shaped")
+    return b.value
+
+
 def rs_batch_launch(batch: int, stream=None):
     _check(load().rs_batch_launch(batch, _stream(stream)), "rs_batch_launch")
 
@@ -787,7 +801,7 @@ def magnification(counts, grid, window, stream=None):
 class Batch:
     """A planned batch of fields (persistent kernel captured in a CUDA graph)."""
 
-    def __init__(self, fields, grids, windows, counts_list=None, out_of_window=None):
+    def __init__(self, fields, grids, windows, counts_list=None, out_of_window=None, shapes=None):
         dev = torch.device("cuda", torch.cuda.current_device())
         if counts_list is None:
             counts_list = [torch.zeros((int(w.npix[1]), int(w.npix[0])), dtype=torch.int32, device=dev)
@@ -797,7 +811,8 @@ class Batch:
         self.fields = list(fields)
         self.counts = counts_list
         self.out_of_window = out_of_window
-        self.handle = rs_batch_create([f.handle for f in self.fields], grids, windows, counts_list, out_of_window)
+        self.handle = rs_batch_create_shaped([f.handle for f in self.fields], grids, windows, counts_list,
+                                             out_of_window, shapes)
 
     def launch(self, stream=None):
         rs_batch_launch(self.handle, stream)

@@ -1,5 +1,5 @@
 // C-ABI layer, batches (Section 4's many maps): the LPT-ordered work plan of many fields and its
-// CUDA graph (memsets, persistent kernels per mass mode, float-float re-evaluation).
+// CUDA graph (memsets, persistent kernels per launch shape and mass mode, float-float re-evaluation).
 #include <algorithm>
 #include <cmath>
 #include <new>
@@ -14,12 +14,12 @@ using namespace rshost;
 struct rs_batch {
   int device;
   int n_fields;
-  // work items of fields without (group 0) and with (group 1) per-lens masses: one persistent
-  // kernel per group, each with its own launch shape
-  int n_items[2];
-  int item_offset[2];
-  int cfg[2];
-  int grid[2];
+  // work items grouped by (launch shape, mass mode): one persistent kernel per group; group
+  // g = 2 * cfg + mass (mass 0: unit masses, 1: per-lens masses)
+  static constexpr int kGroups = 2 * rsint::kNumCfg;
+  int n_items[kGroups];
+  int item_offset[kGroups];
+  int grid[kGroups];
   ShootDesc* d_descs;
   int2* d_items;
   int* d_counter;
@@ -34,8 +34,8 @@ extern "C" {
 
 // ------------------------------------------------------------------------------------------------ batch
 
-int rs_batch_create(int n_fields, const rs_field_t* fields, const rs_ray_grid* grids, const rs_window* windows,
-                    uint32_t* const* d_counts, uint64_t* d_out_of_window, rs_batch_t* out) {
+int rs_batch_create_shaped(int n_fields, const rs_field_t* fields, const rs_ray_grid* grids, const rs_window* windows,
+                           uint32_t* const* d_counts, uint64_t* d_out_of_window, const int* shapes, rs_batch_t* out) {
   if (!out) return fail(RS_EINVAL, "out is NULL");
   *out = nullptr;
   if (n_fields <= 0) return fail(RS_EINVAL, "n_fields must be >= 1");
@@ -50,7 +50,9 @@ int rs_batch_create(int n_fields, const rs_field_t* fields, const rs_ray_grid* g
     int field;
     int tile;
   };
-  std::vector<Item> items[2];
+  constexpr int G = rs_batch::kGroups;
+  std::vector<Item> items[G];
+  int64_t n_total = 0;
   for (int k = 0; k < n_fields; ++k) {
     if (!fields[k]) return fail(RS_EINVAL, "fields[%d] is NULL", k);
     if (fields[k]->device != dev) return fail(RS_EINVAL, "fields[%d] lives on another device", k);
@@ -60,15 +62,23 @@ int rs_batch_create(int n_fields, const rs_field_t* fields, const rs_ray_grid* g
     if ((rc = fill_desc(fields[k], &grids[k], 0, grids[k].n[1], &windows[k], d_counts[k],
                         d_out_of_window ? d_out_of_window + k : nullptr, &descs[k])) != RS_OK)
       return rc;
-    const int grp = fields[k]->dev.has_mass ? 1 : 0;
-    const int warps = rsint::kCfgs[g_cfg[grp]].block / 32;
-    const int64_t seg = 32 * (int64_t)rsint::kCfgs[g_cfg[grp]].rpt;
+    const int mass = fields[k]->dev.has_mass ? 1 : 0;
+    int cfg = g_cfg[mass];
+    if (shapes) {
+      cfg = rsint::find_cfg(shapes[3 * k], shapes[3 * k + 1], shapes[3 * k + 2]);
+      if (cfg < 0)
+        return fail(RS_EINVAL, "shapes[%d] = (%d, %d, %d) is not a compiled launch shape", k, shapes[3 * k],
+                    shapes[3 * k + 1], shapes[3 * k + 2]);
+    }
+    const int grp = 2 * cfg + mass;
+    const int warps = rsint::kCfgs[cfg].block / 32;
+    const int64_t seg = 32 * (int64_t)rsint::kCfgs[cfg].rpt;
     const int64_t n0 = descs[k].n0, nr = descs[k].n_rows;
     if (n0 == 0 || nr == 0) continue;
     const int64_t ncol = (n0 + seg - 1) / seg;
     const int64_t nt = ((nr + warps - 1) / warps) * ncol;
-    if ((int64_t)(items[0].size() + items[1].size()) + nt >= ((int64_t)1 << 31))
-      return fail(RS_EOVERFLOW, "too many work items");
+    if (n_total + nt >= ((int64_t)1 << 31)) return fail(RS_EOVERFLOW, "too many work items");
+    n_total += nt;
     for (int64_t t = 0; t < nt; ++t) {
       const int64_t trow = t / ncol, tcol = t - trow * ncol;
       const int64_t rows = std::min<int64_t>(warps, nr - trow * warps);
@@ -83,15 +93,16 @@ int rs_batch_create(int n_fields, const rs_field_t* fields, const rs_ray_grid* g
   if (!b) return fail(RS_ENOMEM, "host allocation failed");
   b->device = dev;
   b->n_fields = n_fields;
-  for (int grp = 0; grp < 2; ++grp) {
+  for (int grp = 0; grp < G; ++grp) {
     std::stable_sort(items[grp].begin(), items[grp].end(),
                      [](const Item& x, const Item& y) { return x.cost > y.cost; });
     b->item_offset[grp] = (int)h_items.size();
     b->n_items[grp] = (int)items[grp].size();
     for (const Item& it : items[grp]) h_items.push_back(make_int2(it.field, it.tile));
-    b->cfg[grp] = g_cfg[grp];
+    b->grid[grp] = 0;
+    if (b->n_items[grp] == 0) continue;
     int bps = 0;
-    if (rsint::batch_blocks_per_sm(b->cfg[grp], grp == 1, &bps) != cudaSuccess || bps < 1) bps = 1;
+    if (rsint::batch_blocks_per_sm(grp / 2, (grp & 1) == 1, &bps) != cudaSuccess || bps < 1) bps = 1;
     b->grid[grp] = num_sms(dev) * bps;
   }
   auto cleanup = [&]() {
@@ -111,7 +122,7 @@ int rs_batch_create(int n_fields, const rs_field_t* fields, const rs_ray_grid* g
   }
   if ((e = dev_alloc(&b->d_descs, sizeof(ShootDesc) * n_fields)) != cudaSuccess ||
       (e = dev_alloc(&b->d_items, sizeof(int2) * std::max<size_t>(1, h_items.size()))) != cudaSuccess ||
-      (e = dev_alloc(&b->d_counter, 2 * sizeof(int))) != cudaSuccess ||
+      (e = dev_alloc(&b->d_counter, G * sizeof(int))) != cudaSuccess ||
       (b->rc_cap > 0 && (e = dev_alloc(&b->d_rc_list, sizeof(uint2) * (size_t)b->rc_cap)) != cudaSuccess) ||
       (b->rc_cap > 0 && (e = dev_alloc(&b->d_rc_count, sizeof(unsigned int))) != cudaSuccess)) {
     rc = cuda_fail(e, "cudaMalloc (batch)");
@@ -143,12 +154,18 @@ int rs_batch_create(int n_fields, const rs_field_t* fields, const rs_ray_grid* g
     for (int k = 0; k < n_fields && e == cudaSuccess; ++k)
       e = cudaMemsetAsync(d_counts[k], 0, sizeof(uint32_t) * (size_t)windows[k].npix[0] * (size_t)windows[k].npix[1], cs);
     if (e == cudaSuccess && d_out_of_window) e = cudaMemsetAsync(d_out_of_window, 0, sizeof(uint64_t) * n_fields, cs);
-    if (e == cudaSuccess) e = cudaMemsetAsync(b->d_counter, 0, 2 * sizeof(int), cs);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->d_counter, 0, G * sizeof(int), cs);
     if (e == cudaSuccess && b->rc_cap > 0) e = cudaMemsetAsync(b->d_rc_count, 0, sizeof(unsigned int), cs);
-    for (int grp = 1; grp >= 0 && e == cudaSuccess; --grp)
-      if (b->n_items[grp] > 0)
-        e = rsint::launch_batch(b->cfg[grp], grp == 1, b->d_descs, b->d_items + b->item_offset[grp], b->n_items[grp],
-                                b->d_counter + grp, b->grid[grp], cs);
+    // groups in decreasing order of their largest item (each group's items are already LPT-ordered)
+    std::vector<int> order;
+    for (int grp = 0; grp < G; ++grp)
+      if (b->n_items[grp] > 0) order.push_back(grp);
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return items[x][0].cost > items[y][0].cost; });
+    for (size_t i = 0; i < order.size() && e == cudaSuccess; ++i) {
+      const int grp = order[i];
+      e = rsint::launch_batch(grp / 2, (grp & 1) == 1, b->d_descs, b->d_items + b->item_offset[grp], b->n_items[grp],
+                              b->d_counter + grp, b->grid[grp], cs);
+    }
     if (e == cudaSuccess && b->rc_cap > 0)
       e = rsint::launch_recheck(nullptr, b->d_descs, b->d_rc_list, b->d_rc_count, b->rc_cap, recheck_grid(dev), cs);
     cudaError_t e2 = cudaStreamEndCapture(cs, &b->graph);
@@ -163,6 +180,11 @@ int rs_batch_create(int n_fields, const rs_field_t* fields, const rs_ray_grid* g
   }
   *out = b;
   return RS_OK;
+}
+
+int rs_batch_create(int n_fields, const rs_field_t* fields, const rs_ray_grid* grids, const rs_window* windows,
+                    uint32_t* const* d_counts, uint64_t* d_out_of_window, rs_batch_t* out) {
+  return rs_batch_create_shaped(n_fields, fields, grids, windows, d_counts, d_out_of_window, nullptr, out);
 }
 
 int rs_batch_launch(rs_batch_t b, void* stream) {

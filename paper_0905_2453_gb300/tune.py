@@ -187,3 +187,27 @@ def autotune(field, grid, window, min_rays: float = 8e6, max_interactions: float
     except OSError:
         pass
     return b, r, t, timings
+
+
+def batch_shapes(fields, grids, windows, stream=None, cache_path: str = None, **kw):
+    """A launch shape per field of a batch: fields are grouped by mass mode and lens-count bucket (the cache
+    key's), the largest field (most rays) of each group is tuned, and its shape serves the group.  Returns a list
+    of (block, rpt, lens_tile) for rs_batch_create_shaped.  The launch configuration of each mass mode is left as
+    it was."""
+    from . import rs_get_launch_config
+    saved = {m: rs_get_launch_config(m) for m in (False, True)}
+    groups = {}
+    for k, (f, g) in enumerate(zip(fields, grids)):
+        n_lens, has_mass = f.info()
+        groups.setdefault((int(has_mass), _bucket(n_lens)), []).append(k)
+    shapes = [None] * len(fields)
+    try:
+        for members in groups.values():
+            big = max(members, key=lambda k: int(grids[k].n[0]) * int(grids[k].n[1]))
+            b, r, t, _ = autotune(fields[big], grids[big], windows[big], stream=stream, cache_path=cache_path, **kw)
+            for k in members:
+                shapes[k] = (b, r, t)
+    finally:
+        for m, sh in saved.items():
+            rs_set_launch_config(m, *sh)
+    return shapes

@@ -271,6 +271,36 @@ def test_batch_equals_plain_launches_bitwise():
             fl.close()
 
 
+def test_batch_with_per_field_shapes_equals_plain_launches(tmp_path):
+    """A batch whose fields take different launch shapes (every compiled shape in turn, then the tuner's per
+    lens-count bucket choice) gives each field's plain-launch counts bit for bit."""
+    m = rs()
+    from paper_0905_2453_gb300 import tune
+    specs = ri.batch_fields(n_fields=7, ray_scale=0.125)
+    specs.append(ri.disc_field("eq", 200, 0.3, 0.0, 0.2, 160, 48, seed=3, mass="equal"))
+    fields = [m.Field.from_spec(s) for s in specs]
+    try:
+        all_shapes = m.rs_launch_configs()
+        cycled = [all_shapes[k % len(all_shapes)] for k in range(len(specs))]
+        tuned = tune.batch_shapes(fields, [s.grid for s in specs], [s.window for s in specs],
+                                  cache_path=str(tmp_path / "tune.json"), reps=1)
+        assert all(tuple(sh) in [tuple(x) for x in all_shapes] for sh in tuned)
+        refs = [shoot_gpu(s) for s in specs]
+        for shapes in (cycled, tuned):
+            b = m.Batch(fields, [s.grid for s in specs], [s.window for s in specs], shapes=shapes)
+            try:
+                b.launch()
+                torch.cuda.synchronize()
+                for k in range(len(specs)):
+                    assert np.array_equal(b.counts[k].cpu().numpy().view(np.uint32), refs[k][0]), (shapes[k], k)
+                    assert int(b.out_of_window[k].item()) == refs[k][1]
+            finally:
+                b.close()
+    finally:
+        for fl in fields:
+            fl.close()
+
+
 def test_batch_workload_full_size_vs_oracle():
     """The 64-field batch at full size, one persistent launch as the benchmark times it: every field's
     counts conserve its rays and equal its plain launch bit for bit, and the eight smallest fields
