@@ -264,14 +264,19 @@ def run_reference(args):
 
 FULL_LIMIT = 2e12  # grids of at most this many interactions are shot whole per step
 
+STEP_RATE_SLACK = 0.05  # rate a shape may give up for a smaller whole-wave step
+
 
 def headline_rows(rs, spec, field, sms, stream, launch_shape=None):
     """Rows [r0, r1) one step shoots, the launch shape and a description.
 
     Grids of at most FULL_LIMIT interactions are shot whole.  Larger ones are shot as the central block of
     the fewest rows that fill whole waves of CTAs (every CTA of the block runs at once, so the block's rate
-    is the full grid's steady state); the launch shape is the tuned best or, among the shapes within 1 % of
-    its rate, the one whose whole wave takes the fewest rows (every shape gives bitwise the same counts)."""
+    is the full grid's steady state); the launch shape is the tuned best or, among the shapes within
+    STEP_RATE_SLACK of its rate, the one whose whole wave takes the fewest rows (every shape gives bitwise the
+    same counts).  On the 8192-column grid of the 1e8-lens field a 3-CTA-per-SM shape fills whole waves only
+    with 228 rows (four waves, about 35 s a step) against 76 rows (two waves, about 12 s) at two CTAs per SM,
+    for a rate a few percent higher: the shorter step is kept unless the larger unit is faster by more."""
     from paper_0905_2453_gb300 import tune
     n_lens, weighted = field.info()
     if launch_shape:
@@ -279,7 +284,7 @@ def headline_rows(rs, spec, field, sms, stream, launch_shape=None):
         rs.rs_set_launch_config(weighted, *shape)
         rates = {}
     else:
-        shape = tuple(tune.autotune(field, spec.grid, spec.window, stream=stream)[:3])
+        shape = tuple(tune.autotune(field, spec.grid, spec.window, stream=stream)[:4])
         rates = tune.shape_rates(field, spec.grid)
     n0, n1 = int(spec.grid.n[0]), int(spec.grid.n[1])
     if spec.interactions <= FULL_LIMIT:
@@ -292,9 +297,9 @@ def headline_rows(rs, spec, field, sms, stream, launch_shape=None):
     best = rates.get("x".join(str(v) for v in shape))
     cands = [shape]
     if best:
-        cands += [parse_shape(k) for k, v in rates.items() if v >= 0.99 * best]
-    shape = min(cands, key=lambda sh: (unit_of(sh)[0], cands.index(sh)))
-    b, r, _ = shape
+        cands += [parse_shape(k) for k, v in rates.items() if v >= (1 - STEP_RATE_SLACK) * best]
+    shape = min(cands, key=lambda sh: (unit_of(sh)[0], -rates.get("x".join(str(v) for v in sh), 0.0)))
+    b, r = shape[0], shape[1]
     rs.rs_set_launch_config(weighted, *shape)
     unit, occ = unit_of(shape)
     warps = b // 32
@@ -306,9 +311,10 @@ def headline_rows(rs, spec, field, sms, stream, launch_shape=None):
 
 
 def parse_shape(text):
-    """'128x8x512' (threads x rays per thread x lens tile; the tile defaults to 256) -> (128, 8, 512)."""
+    """'128x8x512x2' (threads x rays per thread x lens tile x resident CTAs per SM; defaults 256 and 2)
+    -> (128, 8, 512, 2)."""
     v = [int(x) for x in text.split("x")]
-    return (v[0], v[1], v[2] if len(v) > 2 else 256)
+    return (v[0], v[1], v[2] if len(v) > 2 else 256, v[3] if len(v) > 3 else 2)
 
 
 def oracle_sample_rate(spec, target_s: float):
@@ -542,8 +548,8 @@ def run_ours(args):
     cfg["l2"] = ("inputs larger than L2 (lenses: %.2f GB on the device); L2 also flushed between steps (512 MiB "
                  "write)" % (spec.n_lens * (24 if spec.masses is not None else 16) / 1e9)
                  if spec.n_lens * 16 > (129 << 20) else "flushed between timed steps (512 MiB write)")
-    cfg["launch_shape"] = (f"{shape[0]} threads x {shape[1]} rays/thread x {shape[2]}-lens tiles"
-                           + ("" if args.launch_shape else " (autotuned)"))
+    cfg["launch_shape"] = (f"{shape[0]} threads x {shape[1]} rays/thread x {shape[2]}-lens tiles, compiled for "
+                           f"{shape[3]} CTAs/SM" + ("" if args.launch_shape else " (autotuned)"))
     if rates_headline:
         cfg["tuner_rates"] = rates_headline
     cfg["certified_binning"] = rs.rs_get_certified_binning()
@@ -983,10 +989,10 @@ def run_configs(rs, torch, device, stream, names, cpu=True, full_limit=2e12, max
         f = rs.Field.from_spec(spec, stream)
         n_lens, weighted = f.info()
         if launch_shape:
-            b, r, t = parse_shape(launch_shape)
-            rs.rs_set_launch_config(weighted, b, r, t)
+            b, r, t, mc = parse_shape(launch_shape)
+            rs.rs_set_launch_config(weighted, b, r, t, mc)
         else:
-            b, r, t, _ = tune.autotune(f, spec.grid, spec.window, stream=stream)
+            b, r, t, mc, _ = tune.autotune(f, spec.grid, spec.window, stream=stream)
         n0, n1 = int(spec.grid.n[0]), int(spec.grid.n[1])
         npix = (int(spec.window.npix[1]), int(spec.window.npix[0]))
         c = torch.zeros(npix, dtype=torch.int32, device=device)
@@ -1016,7 +1022,7 @@ def run_configs(rs, torch, device, stream, names, cpu=True, full_limit=2e12, max
             return ms
 
         entry = {"workload": spec.name, "n_lens": n_lens, "weighted_kernels": bool(weighted),
-                 "launch_shape": f"{b}x{r}x{t}", "full_grid_interactions": spec.interactions,
+                 "launch_shape": f"{b}x{r}x{t}x{mc}", "full_grid_interactions": spec.interactions,
                  "tuner_rates": tune.shape_rates(f, spec.grid)}
         if spec.interactions <= full_limit:
             ms = timed(0, n1)
@@ -1025,7 +1031,7 @@ def run_configs(rs, torch, device, stream, names, cpu=True, full_limit=2e12, max
                           "pct_fp32_peak_2070mhz": pct(rate)})
         else:
             warps, cpr = b // 32, -(-n0 // (32 * r))       # rows and CTAs per row group
-            unit = tune.wave_rows(n0, b, r, sms)
+            unit = tune.wave_rows(n0, b, r, sms, rs.rs_launch_occupancy(weighted, b, r, t, mc))
             per_unit = unit * n0 * n_lens
             k = max(1, min(n1 // (2 * unit), int(max_sample // (2 * per_unit))))
             blocks = []
@@ -1089,7 +1095,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--launch-shape", default=None,
-                    help="fix the launch shape, e.g. 128x8x512 (threads x rays/thread x lens tile; skips the autotuner)")
+                    help="fix the launch shape, e.g. 128x8x512x2 (threads x rays/thread x lens tile x CTAs/SM; skips "
+                         "the autotuner)")
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")

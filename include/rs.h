@@ -315,8 +315,8 @@ int rs_magnification(const uint32_t* d_counts, const rs_ray_grid* g, const rs_wi
  *   zeroes the counts and the work counter and runs the persistent kernel.
  *   The fields must outlive the plan.  Unlike rs_shoot, the graph ZEROES the
  *   counts and out-of-window counters on every launch.
- * rs_batch_create_shaped -- as rs_batch_create with a launch shape per field: shapes = host int[3 *
- *   n_fields] of (block, rays per thread, lens tile) triples from rs_launch_configs (NULL: every field
+ * rs_batch_create_shaped -- as rs_batch_create with a launch shape per field: shapes = host int[4 *
+ *   n_fields] of (block, rays per thread, lens tile, min_ctas) from rs_launch_configs (NULL: every field
  *   takes its mass mode's rs_set_launch_config shape).  The items of each (shape, mass mode) form one
  *   persistent launch of the graph; the counts are the same bits for every choice.
  * rs_batch_launch -- replay the plan's graph on `stream`.
@@ -348,22 +348,24 @@ int rs_field_status(rs_field_t f, int clear, int* status);
 
 /*
  * Launch shapes.  The library carries kernels for several (threads per CTA,
- * rays per thread, lenses per shared-memory stage) shapes (Section 2.2's choice
- * of threads per block, widened); all compute bitwise identical results (the
- * lens tile is a multiple of the 256-lens summation period), so the choice
- * only affects speed.  rs_set_launch_config selects the shape used by
- * rs_shoot / rs_shoot_rows / rs_shoot_rows_noalloc (and by batches planned
- * afterwards) for fields without (has_masses = 0) or with per-lens masses;
- * RS_EINVAL for a shape that is not compiled.  rs_launch_configs lists the
- * compiled shapes: up to `cap` (block, rpt, lens_tile) triples into `triples`
- * (int[3*cap]); returns the number available via *count.
- * rs_launch_occupancy reports how many CTAs of a shape's shoot kernel are
- * resident per SM on the current device (SMs x that = one wave of CTAs).
+ * rays per thread, lenses per shared-memory stage, resident CTAs per SM the
+ * kernel is compiled for) shapes (Section 2.2's choice of threads per block,
+ * widened); all compute bitwise identical results (the lens tile is a multiple
+ * of the 256-lens summation period), so the choice only affects speed.
+ * rs_set_launch_config selects the shape used by rs_shoot / rs_shoot_rows /
+ * rs_shoot_rows_noalloc (and by batches planned afterwards) for fields without
+ * (has_masses = 0) or with per-lens masses; RS_EINVAL for a shape that is not
+ * compiled.  rs_launch_configs lists the compiled shapes: up to `cap`
+ * (block, rpt, lens_tile, min_ctas) quadruples into `shapes` (int[4*cap]);
+ * returns the number available via *count.  rs_launch_occupancy reports how
+ * many CTAs of a shape's shoot kernel are resident per SM on the current device
+ * (SMs x that = one wave of CTAs).
  */
-int rs_set_launch_config(int has_masses, int block, int rays_per_thread, int lens_tile);
-int rs_get_launch_config(int has_masses, int* block, int* rays_per_thread, int* lens_tile);
-int rs_launch_configs(int* triples, int cap, int* count);
-int rs_launch_occupancy(int has_masses, int block, int rays_per_thread, int lens_tile, int* ctas_per_sm);
+int rs_set_launch_config(int has_masses, int block, int rays_per_thread, int lens_tile, int min_ctas);
+int rs_get_launch_config(int has_masses, int* block, int* rays_per_thread, int* lens_tile, int* min_ctas);
+int rs_launch_configs(int* shapes, int cap, int* count);
+int rs_launch_occupancy(int has_masses, int block, int rays_per_thread, int lens_tile, int min_ctas,
+                        int* ctas_per_sm);
 
 /*
  * Light curves (Section 1: a source of finite size moves across the magnification map; the

@@ -160,10 +160,10 @@ def load():
         "rs_last_error": ([], ctypes.c_char_p),
         "rs_version": ([], ctypes.c_char_p),
         "rs_device_code_version": ([ctypes.POINTER(i32)], i32),
-        "rs_set_launch_config": ([i32, i32, i32, i32], i32),
-        "rs_get_launch_config": ([i32, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32)], i32),
+        "rs_set_launch_config": ([i32, i32, i32, i32, i32], i32),
+        "rs_get_launch_config": ([i32] + [ctypes.POINTER(i32)] * 4, i32),
         "rs_launch_configs": ([ctypes.POINTER(i32), i32, ctypes.POINTER(i32)], i32),
-        "rs_launch_occupancy": ([i32, i32, i32, i32, ctypes.POINTER(i32)], i32),
+        "rs_launch_occupancy": ([i32, i32, i32, i32, i32, ctypes.POINTER(i32)], i32),
         "rs_partition_buffer_bytes": ([gp, i64, i64, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64),
                                        ctypes.POINTER(ctypes.c_uint64)], i32),
         "rs_partition_pass": ([vp, i32, gp, i64, i64, wp, vp, i32, i32, vp, vp, vp, vp], i32),
@@ -621,13 +621,14 @@ def rs_batch_create(handles, grids, windows, counts_list, out_of_window=None) ->
 
 
 def rs_batch_create_shaped(handles, grids, windows, counts_list, out_of_window=None, shapes=None) -> int:
-    """rs_batch_create with a launch shape (block, rays per thread, lens tile) per field (None: the defaults)."""
+    """rs_batch_create with a launch shape (block, rays per thread, lens tile, min_ctas) per field (None: the
+    defaults)."""
     n, H, G, W, C, po = _batch_arrays(handles, grids, windows, counts_list, out_of_window)
     S = None
     if shapes is not None:
         if len(shapes) != n:
             raise ValueError("one launch shape per field")
-        S = (ctypes.c_int * (3 * n))(*[int(v) for sh in shapes for v in sh])
+        S = (ctypes.c_int * (4 * n))(*[int(v) for sh in shapes for v in sh])
     b = ctypes.c_void_p()
     _check(load().rs_batch_create_shaped(n, H, G, W, C, po, S, ctypes.byref(b)), "rs_batch_create_shaped")
     return b.value
@@ -652,32 +653,34 @@ def rs_field_status(handle: int, clear: bool = False) -> int:
     return int(st.value)
 
 
-def rs_set_launch_config(has_masses: bool, block: int, rays_per_thread: int, lens_tile: int = 256) -> None:
-    _check(load().rs_set_launch_config(1 if has_masses else 0, int(block), int(rays_per_thread), int(lens_tile)),
-           "rs_set_launch_config")
+def rs_set_launch_config(has_masses: bool, block: int, rays_per_thread: int, lens_tile: int = 256,
+                         min_ctas: int = 2) -> None:
+    _check(load().rs_set_launch_config(1 if has_masses else 0, int(block), int(rays_per_thread), int(lens_tile),
+                                       int(min_ctas)), "rs_set_launch_config")
 
 
 def rs_get_launch_config(has_masses: bool):
-    """(block, rays_per_thread, lens_tile) of the mass mode's current launch shape."""
-    b, r, t = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
-    _check(load().rs_get_launch_config(1 if has_masses else 0, ctypes.byref(b), ctypes.byref(r), ctypes.byref(t)),
+    """(block, rays_per_thread, lens_tile, min_ctas) of the mass mode's current launch shape."""
+    v = [ctypes.c_int() for _ in range(4)]
+    _check(load().rs_get_launch_config(1 if has_masses else 0, *[ctypes.byref(x) for x in v]),
            "rs_get_launch_config")
-    return int(b.value), int(r.value), int(t.value)
+    return tuple(int(x.value) for x in v)
 
 
 def rs_launch_configs():
-    """The compiled launch shapes as (block, rays_per_thread, lens_tile) triples."""
+    """The compiled launch shapes as (block, rays_per_thread, lens_tile, min_ctas) quadruples."""
     cnt = ctypes.c_int()
-    buf = (ctypes.c_int * 96)()
+    buf = (ctypes.c_int * 128)()
     _check(load().rs_launch_configs(buf, 32, ctypes.byref(cnt)), "rs_launch_configs")
-    return [(buf[3 * i], buf[3 * i + 1], buf[3 * i + 2]) for i in range(min(cnt.value, 32))]
+    return [tuple(buf[4 * i + j] for j in range(4)) for i in range(min(cnt.value, 32))]
 
 
-def rs_launch_occupancy(has_masses: bool, block: int, rays_per_thread: int, lens_tile: int = 256) -> int:
+def rs_launch_occupancy(has_masses: bool, block: int, rays_per_thread: int, lens_tile: int = 256,
+                        min_ctas: int = 2) -> int:
     """Resident CTAs per SM of a launch shape's shoot kernel on the current device."""
     v = ctypes.c_int(0)
     _check(load().rs_launch_occupancy(int(bool(has_masses)), int(block), int(rays_per_thread), int(lens_tile),
-                                      ctypes.byref(v)), "rs_launch_occupancy")
+                                      int(min_ctas), ctypes.byref(v)), "rs_launch_occupancy")
     return int(v.value)
 
 

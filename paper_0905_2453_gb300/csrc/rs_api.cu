@@ -261,7 +261,7 @@ extern "C" {
 
 const char* rs_last_error(void) { return g_err.c_str(); }
 
-const char* rs_version(void) { return "rs-gb300 0.3 (sm_103a)"; }
+const char* rs_version(void) { return "rs-gb300 0.4 (sm_103a)"; }
 
 int rs_device_code_version(int* binary_version) {
   if (!binary_version) return fail(RS_EINVAL, "binary_version is NULL");
@@ -272,40 +272,43 @@ int rs_device_code_version(int* binary_version) {
   return RS_OK;
 }
 
-int rs_set_launch_config(int has_masses, int block, int rays_per_thread, int lens_tile) {
-  const int c = rsint::find_cfg(block, rays_per_thread, lens_tile);
+int rs_set_launch_config(int has_masses, int block, int rays_per_thread, int lens_tile, int min_ctas) {
+  const int c = rsint::find_cfg(block, rays_per_thread, lens_tile, min_ctas);
   if (c < 0)
-    return fail(RS_EINVAL, "no compiled launch shape (%d threads, %d rays/thread, %d-lens tiles)", block,
-                rays_per_thread, lens_tile);
+    return fail(RS_EINVAL, "no compiled launch shape (%d threads, %d rays/thread, %d-lens tiles, %d CTAs/SM)", block,
+                rays_per_thread, lens_tile, min_ctas);
   g_cfg[has_masses ? 1 : 0] = c;
   return RS_OK;
 }
 
-int rs_get_launch_config(int has_masses, int* block, int* rays_per_thread, int* lens_tile) {
+int rs_get_launch_config(int has_masses, int* block, int* rays_per_thread, int* lens_tile, int* min_ctas) {
   const int c = g_cfg[has_masses ? 1 : 0];
   if (block) *block = rsint::kCfgs[c].block;
   if (rays_per_thread) *rays_per_thread = rsint::kCfgs[c].rpt;
   if (lens_tile) *lens_tile = rsint::kCfgs[c].tile;
+  if (min_ctas) *min_ctas = rsint::kCfgs[c].min_ctas;
   return RS_OK;
 }
 
-int rs_launch_occupancy(int has_masses, int block, int rays_per_thread, int lens_tile, int* ctas_per_sm) {
+int rs_launch_occupancy(int has_masses, int block, int rays_per_thread, int lens_tile, int min_ctas,
+                        int* ctas_per_sm) {
   if (!ctas_per_sm) return fail(RS_EINVAL, "ctas_per_sm is NULL");
-  const int c = rsint::find_cfg(block, rays_per_thread, lens_tile);
+  const int c = rsint::find_cfg(block, rays_per_thread, lens_tile, min_ctas);
   if (c < 0)
-    return fail(RS_EINVAL, "no compiled launch shape (%d threads, %d rays/thread, %d-lens tiles)", block,
-                rays_per_thread, lens_tile);
+    return fail(RS_EINVAL, "no compiled launch shape (%d threads, %d rays/thread, %d-lens tiles, %d CTAs/SM)", block,
+                rays_per_thread, lens_tile, min_ctas);
   cudaError_t e = rsint::shoot_blocks_per_sm(c, has_masses != 0, ctas_per_sm);
   if (e != cudaSuccess) return cuda_fail(e, "occupancy query");
   return RS_OK;
 }
 
-int rs_launch_configs(int* triples, int cap, int* count) {
+int rs_launch_configs(int* shapes, int cap, int* count) {
   if (count) *count = rsint::kNumCfg;
-  for (int i = 0; i < rsint::kNumCfg && i < cap && triples; ++i) {
-    triples[3 * i] = rsint::kCfgs[i].block;
-    triples[3 * i + 1] = rsint::kCfgs[i].rpt;
-    triples[3 * i + 2] = rsint::kCfgs[i].tile;
+  for (int i = 0; i < rsint::kNumCfg && i < cap && shapes; ++i) {
+    shapes[4 * i] = rsint::kCfgs[i].block;
+    shapes[4 * i + 1] = rsint::kCfgs[i].rpt;
+    shapes[4 * i + 2] = rsint::kCfgs[i].tile;
+    shapes[4 * i + 3] = rsint::kCfgs[i].min_ctas;
   }
   return RS_OK;
 }

@@ -65,10 +65,11 @@ int rs_batch_create_shaped(int n_fields, const rs_field_t* fields, const rs_ray_
     const int mass = fields[k]->dev.has_mass ? 1 : 0;
     int cfg = g_cfg[mass];
     if (shapes) {
-      cfg = rsint::find_cfg(shapes[3 * k], shapes[3 * k + 1], shapes[3 * k + 2]);
+      const int* sh = shapes + 4 * k;
+      cfg = rsint::find_cfg(sh[0], sh[1], sh[2], sh[3]);
       if (cfg < 0)
-        return fail(RS_EINVAL, "shapes[%d] = (%d, %d, %d) is not a compiled launch shape", k, shapes[3 * k],
-                    shapes[3 * k + 1], shapes[3 * k + 2]);
+        return fail(RS_EINVAL, "shapes[%d] = (%d, %d, %d, %d) is not a compiled launch shape", k, sh[0], sh[1], sh[2],
+                    sh[3]);
     }
     const int grp = 2 * cfg + mass;
     const int warps = rsint::kCfgs[cfg].block / 32;

@@ -10,10 +10,9 @@ namespace {
 
 using namespace rsdev;
 
-// Two CTAs per SM as the occupancy floor for small CTAs (more registers, as for the plain kernel);
-// eight-warp CTAs keep the default allocation (a two-CTA floor would force spills there).
-template <int WARPS, int RPT, int TILE, bool MASS>
-__global__ void __launch_bounds__(WARPS * 32, WARPS <= 4 ? 2 : 1)
+// MINB resident CTAs per SM as the occupancy floor, as for the plain kernel.
+template <int WARPS, int RPT, int TILE, bool MASS, int MINB>
+__global__ void __launch_bounds__(WARPS * 32, MINB)
     batch_kernel(const ShootDesc* __restrict__ descs, const int2* __restrict__ items, int n_items, int* counter) {
   extern __shared__ __align__(128) unsigned char rs_smem[];
   auto& ss = *reinterpret_cast<ShootSmem<WARPS, RPT, TILE>*>(rs_smem);
@@ -43,35 +42,35 @@ __global__ void __launch_bounds__(WARPS * 32, WARPS <= 4 ? 2 : 1)
   }
 }
 
-template <int WARPS, int RPT, int TILE, bool MASS>
+template <int WARPS, int RPT, int TILE, bool MASS, int MINB>
 cudaError_t launch_batch_m(const ShootDesc* descs, const int2* items, int n_items, int* counter, int grid,
                            cudaStream_t s) {
   constexpr size_t smem = sizeof(ShootSmem<WARPS, RPT, TILE>);
-  cudaError_t e = rsint::smem_opt_in<batch_kernel<WARPS, RPT, TILE, MASS>>(smem);
+  cudaError_t e = rsint::smem_opt_in<batch_kernel<WARPS, RPT, TILE, MASS, MINB>>(smem);
   if (e != cudaSuccess) return e;
-  batch_kernel<WARPS, RPT, TILE, MASS><<<grid, WARPS * 32, smem, s>>>(descs, items, n_items, counter);
+  batch_kernel<WARPS, RPT, TILE, MASS, MINB><<<grid, WARPS * 32, smem, s>>>(descs, items, n_items, counter);
   return cudaGetLastError();
 }
 
-template <int WARPS, int RPT, int TILE>
+template <int WARPS, int RPT, int TILE, int MINB>
 cudaError_t launch_batch_t(bool mass, const ShootDesc* descs, const int2* items, int n_items, int* counter, int grid,
                            cudaStream_t s) {
-  return mass ? launch_batch_m<WARPS, RPT, TILE, true>(descs, items, n_items, counter, grid, s)
-              : launch_batch_m<WARPS, RPT, TILE, false>(descs, items, n_items, counter, grid, s);
+  return mass ? launch_batch_m<WARPS, RPT, TILE, true, MINB>(descs, items, n_items, counter, grid, s)
+              : launch_batch_m<WARPS, RPT, TILE, false, MINB>(descs, items, n_items, counter, grid, s);
 }
 
-template <int WARPS, int RPT, int TILE, bool MASS>
+template <int WARPS, int RPT, int TILE, bool MASS, int MINB>
 cudaError_t occ_m(int* blocks) {
   constexpr size_t smem = sizeof(ShootSmem<WARPS, RPT, TILE>);
-  cudaError_t e = rsint::smem_opt_in<batch_kernel<WARPS, RPT, TILE, MASS>>(smem);
+  cudaError_t e = rsint::smem_opt_in<batch_kernel<WARPS, RPT, TILE, MASS, MINB>>(smem);
   if (e != cudaSuccess) return e;
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, batch_kernel<WARPS, RPT, TILE, MASS>, WARPS * 32,
-                                                       smem);
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, batch_kernel<WARPS, RPT, TILE, MASS, MINB>,
+                                                       WARPS * 32, smem);
 }
 
-template <int WARPS, int RPT, int TILE>
+template <int WARPS, int RPT, int TILE, int MINB>
 cudaError_t occ_t(bool mass, int* blocks) {
-  return mass ? occ_m<WARPS, RPT, TILE, true>(blocks) : occ_m<WARPS, RPT, TILE, false>(blocks);
+  return mass ? occ_m<WARPS, RPT, TILE, true, MINB>(blocks) : occ_m<WARPS, RPT, TILE, false, MINB>(blocks);
 }
 
 }  // namespace
@@ -81,30 +80,22 @@ namespace rsint {
 cudaError_t launch_batch(int cfg, bool mass, const rsdev::ShootDesc* descs, const int2* items, int n_items,
                          int* counter, int grid, cudaStream_t s) {
   switch (cfg) {
-    case 0: return launch_batch_t<2, 8, 256>(mass, descs, items, n_items, counter, grid, s);
-    case 1: return launch_batch_t<4, 4, 256>(mass, descs, items, n_items, counter, grid, s);
-    case 2: return launch_batch_t<4, 8, 256>(mass, descs, items, n_items, counter, grid, s);
-    case 3: return launch_batch_t<8, 4, 256>(mass, descs, items, n_items, counter, grid, s);
-    case 4: return launch_batch_t<8, 8, 256>(mass, descs, items, n_items, counter, grid, s);
-    case 5: return launch_batch_t<8, 6, 256>(mass, descs, items, n_items, counter, grid, s);
-    case 6: return launch_batch_t<2, 8, 512>(mass, descs, items, n_items, counter, grid, s);
-    case 7: return launch_batch_t<4, 4, 512>(mass, descs, items, n_items, counter, grid, s);
-    case 8: return launch_batch_t<4, 8, 512>(mass, descs, items, n_items, counter, grid, s);
+#define RS_CASE(i, w, r, t, m) \
+  case i:                       \
+    return launch_batch_t<w, r, t, m>(mass, descs, items, n_items, counter, grid, s);
+    RS_LAUNCH_SHAPES(RS_CASE)
+#undef RS_CASE
     default: return cudaErrorInvalidValue;
   }
 }
 
 cudaError_t batch_blocks_per_sm(int cfg, bool mass, int* blocks) {
   switch (cfg) {
-    case 0: return occ_t<2, 8, 256>(mass, blocks);
-    case 1: return occ_t<4, 4, 256>(mass, blocks);
-    case 2: return occ_t<4, 8, 256>(mass, blocks);
-    case 3: return occ_t<8, 4, 256>(mass, blocks);
-    case 4: return occ_t<8, 8, 256>(mass, blocks);
-    case 5: return occ_t<8, 6, 256>(mass, blocks);
-    case 6: return occ_t<2, 8, 512>(mass, blocks);
-    case 7: return occ_t<4, 4, 512>(mass, blocks);
-    case 8: return occ_t<4, 8, 512>(mass, blocks);
+#define RS_CASE(i, w, r, t, m) \
+  case i:                       \
+    return occ_t<w, r, t, m>(mass, blocks);
+    RS_LAUNCH_SHAPES(RS_CASE)
+#undef RS_CASE
     default: return cudaErrorInvalidValue;
   }
 }

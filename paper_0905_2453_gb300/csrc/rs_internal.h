@@ -16,17 +16,26 @@ constexpr int kTile = 256;
 
 // Launch shapes compiled into the library; the per-ray arithmetic is identical for all (the lens
 // tile is a multiple of the 256-lens summation period, so the group and renormalisation schedule
-// does not depend on it).  A CTA of block / 32 warps covers block / 32 grid rows by 32 * rpt columns
-// and stages tile lenses per step.
+// does not depend on it).  A CTA of block / 32 warps covers block / 32 grid rows by 32 * rpt columns,
+// stages tile lenses per step, and is compiled for at least min_ctas resident CTAs per SM (the
+// register budget per thread follows: 2 -> up to 255 registers, 3 -> 168 for 128-thread CTAs).
+// X(index, warps, rays per thread, lens tile, min_ctas)
+#define RS_LAUNCH_SHAPES(X)                                                                           \
+  X(0, 2, 8, 256, 2) X(1, 4, 4, 256, 2) X(2, 4, 8, 256, 2) X(3, 8, 4, 256, 1) X(4, 8, 8, 256, 1)   \
+  X(5, 8, 6, 256, 1) X(6, 2, 8, 512, 2) X(7, 4, 4, 512, 2) X(8, 4, 8, 512, 2) X(9, 4, 8, 256, 3)   \
+  X(10, 4, 8, 512, 3)
+
 struct KernelCfg {
-  int block;  // threads per CTA (a multiple of 32)
-  int rpt;    // rays per thread (even: packed pairs)
-  int tile;   // lenses per shared-memory stage (256 or 512)
+  int block;     // threads per CTA (a multiple of 32)
+  int rpt;       // rays per thread (even: packed pairs)
+  int tile;      // lenses per shared-memory stage (256 or 512)
+  int min_ctas;  // resident CTAs per SM the kernel is compiled for
 };
-constexpr int kNumCfg = 9;
-constexpr KernelCfg kCfgs[kNumCfg] = {{64, 8, 256},  {128, 4, 256}, {128, 8, 256}, {256, 4, 256}, {256, 8, 256},
-                                      {256, 6, 256}, {64, 8, 512},  {128, 4, 512}, {128, 8, 512}};
-constexpr int kDefaultCfg = 8;
+#define RS_CFG_ENTRY(i, w, r, t, m) {32 * (w), r, t, m},
+constexpr KernelCfg kCfgs[] = {RS_LAUNCH_SHAPES(RS_CFG_ENTRY)};
+#undef RS_CFG_ENTRY
+constexpr int kNumCfg = (int)(sizeof(kCfgs) / sizeof(kCfgs[0]));
+constexpr int kDefaultCfg = 8;  // 128 threads x 8 rays x 512-lens tiles, two CTAs per SM
 
 // Dynamic shared memory beyond 48 KiB per CTA needs a one-time opt-in per kernel and device.
 template <auto Kernel>
@@ -43,9 +52,10 @@ cudaError_t smem_opt_in(size_t bytes) {
   return e;
 }
 
-inline int find_cfg(int block, int rpt, int tile) {
+inline int find_cfg(int block, int rpt, int tile, int min_ctas) {
   for (int i = 0; i < kNumCfg; ++i)
-    if (kCfgs[i].block == block && kCfgs[i].rpt == rpt && kCfgs[i].tile == tile) return i;
+    if (kCfgs[i].block == block && kCfgs[i].rpt == rpt && kCfgs[i].tile == tile && kCfgs[i].min_ctas == min_ctas)
+      return i;
   return -1;
 }
 

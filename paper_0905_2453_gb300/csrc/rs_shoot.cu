@@ -5,11 +5,11 @@ namespace {
 
 using namespace rsdev;
 
-// Two CTAs per SM as the occupancy floor: lets the compiler keep a small CTA's eight rays per thread,
-// their two-float accumulators and a deeper instruction window in registers (measured faster than the
-// default allocation, which spills); eight-warp CTAs keep the default allocation.
-template <int WARPS, int RPT, int TILE, bool MASS>
-__global__ void __launch_bounds__(WARPS * 32, WARPS <= 4 ? 2 : 1) shoot_kernel(const ShootDesc d) {
+// MINB resident CTAs per SM as the occupancy floor: two let the compiler keep a small CTA's eight rays
+// per thread, their two-float accumulators and a deep instruction window in up to 255 registers;
+// three (168 registers) hide more latency with twelve warps per SM; eight-warp CTAs take one.
+template <int WARPS, int RPT, int TILE, bool MASS, int MINB>
+__global__ void __launch_bounds__(WARPS * 32, MINB) shoot_kernel(const ShootDesc d) {
   extern __shared__ __align__(128) unsigned char rs_smem[];
   auto& ss = *reinterpret_cast<ShootSmem<WARPS, RPT, TILE>*>(rs_smem);
   PipeState ps;
@@ -61,36 +61,36 @@ __global__ void __launch_bounds__(BLOCK)
   }
 }
 
-template <int WARPS, int RPT, int TILE, bool MASS>
+template <int WARPS, int RPT, int TILE, bool MASS, int MINB>
 cudaError_t launch_shoot_m(const ShootDesc& d, int64_t grid, cudaStream_t s) {
   constexpr size_t smem = sizeof(ShootSmem<WARPS, RPT, TILE>);
-  cudaError_t e = rsint::smem_opt_in<shoot_kernel<WARPS, RPT, TILE, MASS>>(smem);
+  cudaError_t e = rsint::smem_opt_in<shoot_kernel<WARPS, RPT, TILE, MASS, MINB>>(smem);
   if (e != cudaSuccess) return e;
-  shoot_kernel<WARPS, RPT, TILE, MASS><<<(unsigned)grid, WARPS * 32, smem, s>>>(d);
+  shoot_kernel<WARPS, RPT, TILE, MASS, MINB><<<(unsigned)grid, WARPS * 32, smem, s>>>(d);
   return cudaGetLastError();
 }
 
-template <int WARPS, int RPT, int TILE>
+template <int WARPS, int RPT, int TILE, int MINB>
 cudaError_t launch_shoot_t(const ShootDesc& d, cudaStream_t s) {
   const int64_t grid = shoot_tiles<WARPS, RPT>(d.n_rows, d.n0);
   if (grid <= 0) return cudaSuccess;
   if (grid >= ((int64_t)1 << 31)) return cudaErrorInvalidValue;
-  return d.f.has_mass ? launch_shoot_m<WARPS, RPT, TILE, true>(d, grid, s)
-                      : launch_shoot_m<WARPS, RPT, TILE, false>(d, grid, s);
+  return d.f.has_mass ? launch_shoot_m<WARPS, RPT, TILE, true, MINB>(d, grid, s)
+                      : launch_shoot_m<WARPS, RPT, TILE, false, MINB>(d, grid, s);
 }
 
-template <int WARPS, int RPT, int TILE, bool MASS>
+template <int WARPS, int RPT, int TILE, bool MASS, int MINB>
 cudaError_t occupancy_m(int* blocks) {
   constexpr size_t smem = sizeof(ShootSmem<WARPS, RPT, TILE>);
-  cudaError_t e = rsint::smem_opt_in<shoot_kernel<WARPS, RPT, TILE, MASS>>(smem);
+  cudaError_t e = rsint::smem_opt_in<shoot_kernel<WARPS, RPT, TILE, MASS, MINB>>(smem);
   if (e != cudaSuccess) return e;
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, shoot_kernel<WARPS, RPT, TILE, MASS>, WARPS * 32,
-                                                       smem);
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, shoot_kernel<WARPS, RPT, TILE, MASS, MINB>,
+                                                       WARPS * 32, smem);
 }
 
-template <int WARPS, int RPT, int TILE>
+template <int WARPS, int RPT, int TILE, int MINB>
 cudaError_t occupancy_t(bool mass, int* blocks) {
-  return mass ? occupancy_m<WARPS, RPT, TILE, true>(blocks) : occupancy_m<WARPS, RPT, TILE, false>(blocks);
+  return mass ? occupancy_m<WARPS, RPT, TILE, true, MINB>(blocks) : occupancy_m<WARPS, RPT, TILE, false, MINB>(blocks);
 }
 
 }  // namespace
@@ -99,30 +99,22 @@ namespace rsint {
 
 cudaError_t shoot_blocks_per_sm(int cfg, bool mass, int* blocks) {
   switch (cfg) {
-    case 0: return occupancy_t<2, 8, 256>(mass, blocks);
-    case 1: return occupancy_t<4, 4, 256>(mass, blocks);
-    case 2: return occupancy_t<4, 8, 256>(mass, blocks);
-    case 3: return occupancy_t<8, 4, 256>(mass, blocks);
-    case 4: return occupancy_t<8, 8, 256>(mass, blocks);
-    case 5: return occupancy_t<8, 6, 256>(mass, blocks);
-    case 6: return occupancy_t<2, 8, 512>(mass, blocks);
-    case 7: return occupancy_t<4, 4, 512>(mass, blocks);
-    case 8: return occupancy_t<4, 8, 512>(mass, blocks);
+#define RS_CASE(i, w, r, t, m) \
+  case i:                       \
+    return occupancy_t<w, r, t, m>(mass, blocks);
+    RS_LAUNCH_SHAPES(RS_CASE)
+#undef RS_CASE
     default: return cudaErrorInvalidValue;
   }
 }
 
 cudaError_t launch_shoot(int cfg, const rsdev::ShootDesc& d, cudaStream_t s) {
   switch (cfg) {
-    case 0: return launch_shoot_t<2, 8, 256>(d, s);
-    case 1: return launch_shoot_t<4, 4, 256>(d, s);
-    case 2: return launch_shoot_t<4, 8, 256>(d, s);
-    case 3: return launch_shoot_t<8, 4, 256>(d, s);
-    case 4: return launch_shoot_t<8, 8, 256>(d, s);
-    case 5: return launch_shoot_t<8, 6, 256>(d, s);
-    case 6: return launch_shoot_t<2, 8, 512>(d, s);
-    case 7: return launch_shoot_t<4, 4, 512>(d, s);
-    case 8: return launch_shoot_t<4, 8, 512>(d, s);
+#define RS_CASE(i, w, r, t, m) \
+  case i:                       \
+    return launch_shoot_t<w, r, t, m>(d, s);
+    RS_LAUNCH_SHAPES(RS_CASE)
+#undef RS_CASE
     default: return cudaErrorInvalidValue;
   }
 }

@@ -1,7 +1,8 @@
 """Launch-shape autotuner.
 
 The library carries kernels for several launch shapes (threads per CTA x rays per
-thread x lenses per shared-memory stage, see ``rs_launch_configs``).  All of them
+thread x lenses per shared-memory stage x resident CTAs per SM compiled for, see
+``rs_launch_configs``).  All of them
 compute bitwise identical results, so the choice only affects speed.  ``autotune`` times every shape on a
 proxy run (a block of the workload's own grid rows; for fields larger than the proxy,
 one whole wave of CTAs per launch, and the proxy's best three again on the field itself
@@ -49,7 +50,7 @@ def wave_rows(n0: int, block: int, rpt: int, sms: int, ctas_per_sm: int = 2) -> 
 
 
 def shape_rates(field, grid, cache_path: str = None) -> dict:
-    """Steady-state interactions/s per launch shape ("block x rpt x lens_tile") from the tuner's cache entry for
+    """Steady-state interactions/s per launch shape ("block x rpt x lens_tile x min_ctas") from the tuner's cache entry for
     (field, grid): the shapes verified on the field itself if any, else every shape on the proxy ({} if the pair
     was never tuned)."""
     cache = _load(cache_path or os.environ.get("RS_TUNE_CACHE", DEFAULT_CACHE))
@@ -74,11 +75,12 @@ def _verify_on_field(field, grid, window, counts, st, rates, timings, shape_rows
     verified = {}
     field_handle = field.handle
     for name in cands:
-        block, rpt, tile = (int(v) for v in name.split("x"))
-        unit = wave_rows(n0, block, rpt, sms, rs_launch_occupancy(has_mass, block, rpt, tile))
+        shape = tuple(int(v) for v in name.split("x"))
+        block, rpt = shape[0], shape[1]
+        unit = wave_rows(n0, block, rpt, sms, rs_launch_occupancy(has_mass, *shape))
         if 2 * unit > n1 or unit * n0 * n_lens > verify_interactions:
             continue  # this shape's whole-wave unit does not fit the grid or the budget
-        rs_set_launch_config(has_mass, block, rpt, tile)
+        rs_set_launch_config(has_mass, *shape)
         warps = block // 32
         r0 = (n1 - 2 * unit) // 2 // warps * warps
 
@@ -101,16 +103,16 @@ def _verify_on_field(field, grid, window, counts, st, rates, timings, shape_rows
 def autotune(field, grid, window, min_rays: float = 8e6, max_interactions: float = 3e11, reps: int = 3,
              cache_path: str = None, force: bool = False, stream=None, max_proxy_lenses: int = 1 << 16,
              verify_interactions: float = 2e12):
-    """Pick and set the fastest launch shape for this (field, grid); returns (block, rpt, lens_tile,
+    """Pick and set the fastest launch shape for this (field, grid); returns (block, rpt, lens_tile, min_ctas,
     timings_ms) with each shape's time for its own (largest) proxy block of rows."""
     cache_path = cache_path or os.environ.get("RS_TUNE_CACHE", DEFAULT_CACHE)
     n_lens, has_mass = field.info()
     key = cache_key(field, grid)
     cache = _load(cache_path)
     if not force and key in cache:
-        b, r, t = cache[key]["block"], cache[key]["rpt"], cache[key].get("tile", 256)
-        rs_set_launch_config(has_mass, b, r, t)
-        return b, r, t, cache[key].get("ms", {})
+        sh = tuple(cache[key]["shape"])
+        rs_set_launch_config(has_mass, *sh)
+        return (*sh, cache[key].get("ms", {}))
     # proxy: blocks of the grid's rows, capped in work; very large fields through a view of their
     # first lenses.  Where the grid allows, each shape shoots k and 2k units of rows holding a whole
     # number of waves (a multiple of 2 x SMs CTAs: whole waves at one or two resident CTAs per SM) and
@@ -139,17 +141,18 @@ def autotune(field, grid, window, min_rays: float = 8e6, max_interactions: float
 
     timings, rates, shape_rows = {}, {}, {}
     try:
-        for block, rpt, tile in rs_launch_configs():
+        for shape in rs_launch_configs():
+            block, rpt = shape[0], shape[1]
             unit = wave_rows(n0, block, rpt, sms)
             k = min(max(1, round(rows / unit)), n1 // (2 * unit))
-            name = f"{block}x{rpt}x{tile}"
-            rs_set_launch_config(has_mass, block, rpt, tile)
+            name = "x".join(str(v) for v in shape)
+            rs_set_launch_config(has_mass, *shape)
             if proxy is not field:
                 # A large field's CTAs each run for seconds, all CTAs of a wave in step with one another
                 # (their warps then compete for the same pipe at the same time); short proxy CTAs drift
                 # apart over many waves and hide that.  So each launch here is exactly the rows of one
                 # whole wave at the shape's real occupancy, as a block of the large field runs.
-                wave = wave_rows(n0, block, rpt, sms, rs_launch_occupancy(has_mass, block, rpt, tile))
+                wave = wave_rows(n0, block, rpt, sms, rs_launch_occupancy(has_mass, *shape))
                 if wave <= n1:
                     rs_shoot_rows(proxy.handle, grid, 0, wave, window, counts, None, st)  # warm-up
                     timings[name], shape_rows[name] = timed(wave), [wave]
@@ -174,9 +177,9 @@ def autotune(field, grid, window, min_rays: float = 8e6, max_interactions: float
             proxy.close()
     ranked = field_rates or rates
     best = max(ranked, key=ranked.get)
-    b, r, t = (int(v) for v in best.split("x"))
-    rs_set_launch_config(has_mass, b, r, t)
-    cache[key] = {"block": b, "rpt": r, "tile": t, "ms": timings, "rows": shape_rows, "interactions_per_s": rates,
+    sh = tuple(int(v) for v in best.split("x"))
+    rs_set_launch_config(has_mass, *sh)
+    cache[key] = {"shape": list(sh), "ms": timings, "rows": shape_rows, "interactions_per_s": rates,
                   "field_interactions_per_s": field_rates, "proxy_lenses": n_proxy}
     try:
         os.makedirs(os.path.dirname(cache_path), exist_ok=True)
@@ -186,13 +189,13 @@ def autotune(field, grid, window, min_rays: float = 8e6, max_interactions: float
         os.replace(tmp, cache_path)
     except OSError:
         pass
-    return b, r, t, timings
+    return (*sh, timings)
 
 
 def batch_shapes(fields, grids, windows, stream=None, cache_path: str = None, **kw):
     """A launch shape per field of a batch: fields are grouped by mass mode and lens-count bucket (the cache
     key's), the largest field (most rays) of each group is tuned, and its shape serves the group.  Returns a list
-    of (block, rpt, lens_tile) for rs_batch_create_shaped.  The launch configuration of each mass mode is left as
+    of (block, rpt, lens_tile, min_ctas) for rs_batch_create_shaped.  The launch configuration of each mass mode is left as
     it was."""
     from . import rs_get_launch_config
     saved = {m: rs_get_launch_config(m) for m in (False, True)}
@@ -204,9 +207,9 @@ def batch_shapes(fields, grids, windows, stream=None, cache_path: str = None, **
     try:
         for members in groups.values():
             big = max(members, key=lambda k: int(grids[k].n[0]) * int(grids[k].n[1]))
-            b, r, t, _ = autotune(fields[big], grids[big], windows[big], stream=stream, cache_path=cache_path, **kw)
+            sh = tuple(autotune(fields[big], grids[big], windows[big], stream=stream, cache_path=cache_path, **kw)[:4])
             for k in members:
-                shapes[k] = (b, r, t)
+                shapes[k] = sh
     finally:
         for m, sh in saved.items():
             rs_set_launch_config(m, *sh)

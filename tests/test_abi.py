@@ -105,14 +105,16 @@ def test_grid_window_validation(rs):
     assert lib.rs_shoot_rows(fake, ctypes.byref(g), 2, 9, ctypes.byref(w), ctypes.c_void_p(16), None,
                              None) == rs.RS_EINVAL
     # unknown launch shape
-    assert lib.rs_set_launch_config(0, 96, 3, 256) == rs.RS_EINVAL
-    assert lib.rs_set_launch_config(0, 128, 8, 384) == rs.RS_EINVAL   # no such lens tile
+    assert lib.rs_set_launch_config(0, 96, 3, 256, 2) == rs.RS_EINVAL
+    assert lib.rs_set_launch_config(0, 128, 8, 384, 2) == rs.RS_EINVAL   # no such lens tile
+    assert lib.rs_set_launch_config(0, 128, 8, 512, 5) == rs.RS_EINVAL   # no such occupancy floor
     shapes = rs.rs_launch_configs()
-    assert len(shapes) >= 4 and {t for _, _, t in shapes} == {256, 512}
+    assert len(shapes) >= 4 and {s[2] for s in shapes} == {256, 512} and {s[3] for s in shapes} >= {2, 3}
+    assert len(set(shapes)) == len(shapes)
     saved = rs.rs_get_launch_config(False)
     try:
-        rs.rs_set_launch_config(False, 128, 8, 512)
-        assert rs.rs_get_launch_config(False) == (128, 8, 512)
+        rs.rs_set_launch_config(False, 128, 8, 512, 3)
+        assert rs.rs_get_launch_config(False) == (128, 8, 512, 3)
     finally:
         rs.rs_set_launch_config(False, *saved)
 

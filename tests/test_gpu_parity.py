@@ -133,8 +133,8 @@ def test_launch_shapes_and_runs_bitwise_identical():
         saved = m.rs_get_launch_config(has_m)
         results = []
         try:
-            for block, rpt, tile in m.rs_launch_configs():
-                m.rs_set_launch_config(has_m, block, rpt, tile)
+            for shape in m.rs_launch_configs():
+                m.rs_set_launch_config(has_m, *shape)
                 results.append(shoot_gpu(spec))
                 results.append(shoot_gpu(spec))
         finally:
