@@ -71,6 +71,7 @@ int rs_batch_create_shaped(int n_fields, const rs_field_t* fields, const rs_ray_
         return fail(RS_EINVAL, "shapes[%d] = (%d, %d, %d, %d) is not a compiled launch shape", k, sh[0], sh[1], sh[2],
                     sh[3]);
     }
+    cfg = rsint::batch_cfg(cfg);
     const int grp = 2 * cfg + mass;
     const int warps = rsint::kCfgs[cfg].block / 32;
     const int64_t seg = 32 * (int64_t)rsint::kCfgs[cfg].rpt;

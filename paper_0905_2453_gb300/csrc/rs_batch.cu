@@ -10,7 +10,16 @@ namespace {
 
 using namespace rsdev;
 
-// MINB resident CTAs per SM as the occupancy floor, as for the plain kernel.
+// MINB resident CTAs per SM as the occupancy floor, as for the plain kernel, but at most two: the
+// launch shapes compiled for three CTAs per SM (168 registers) run here as their two-CTA twins.
+// Inside the item loop the 168-register build of the tile body ran 1.6-3 % slower than the plain
+// kernel's (one-field batches of 1e3-1e5 lenses), whatever held the descriptor (shared memory,
+// kernel parameter, constant bank, global) and with the tile body out of line; at two CTAs per SM
+// (up to 255 registers) the batch kernel matches the plain one.  Counts do not depend on the shape.
+template <int MINB>
+constexpr int batch_minb() {
+  return MINB > 2 ? 2 : MINB;
+}
 template <int WARPS, int RPT, int TILE, bool MASS, int MINB>
 __global__ void __launch_bounds__(WARPS * 32, MINB)
     batch_kernel(const ShootDesc* __restrict__ descs, const int2* __restrict__ items, int n_items, int* counter) {
@@ -82,7 +91,7 @@ cudaError_t launch_batch(int cfg, bool mass, const rsdev::ShootDesc* descs, cons
   switch (cfg) {
 #define RS_CASE(i, w, r, t, m) \
   case i:                       \
-    return launch_batch_t<w, r, t, m>(mass, descs, items, n_items, counter, grid, s);
+    return launch_batch_t<w, r, t, batch_minb<m>()>(mass, descs, items, n_items, counter, grid, s);
     RS_LAUNCH_SHAPES(RS_CASE)
 #undef RS_CASE
     default: return cudaErrorInvalidValue;
@@ -93,7 +102,7 @@ cudaError_t batch_blocks_per_sm(int cfg, bool mass, int* blocks) {
   switch (cfg) {
 #define RS_CASE(i, w, r, t, m) \
   case i:                       \
-    return occ_t<w, r, t, m>(mass, blocks);
+    return occ_t<w, r, t, batch_minb<m>()>(mass, blocks);
     RS_LAUNCH_SHAPES(RS_CASE)
 #undef RS_CASE
     default: return cudaErrorInvalidValue;

@@ -59,6 +59,14 @@ inline int find_cfg(int block, int rpt, int tile, int min_ctas) {
   return -1;
 }
 
+// The shape a batch runs for launch shape cfg: batch kernels are built for at most two resident CTAs
+// per SM (rs_batch.cu), so a three-CTA shape runs as its two-CTA twin, in the twin's group.
+inline int batch_cfg(int cfg) {
+  if (kCfgs[cfg].min_ctas <= 2) return cfg;
+  const int twin = find_cfg(kCfgs[cfg].block, kCfgs[cfg].rpt, kCfgs[cfg].tile, 2);
+  return twin >= 0 ? twin : cfg;
+}
+
 // Plain launch: one CTA per ray tile of block * rpt rays.
 cudaError_t launch_shoot(int cfg, const rsdev::ShootDesc& d, cudaStream_t s);
 // Resident CTAs per SM of the plain shoot kernel of launch shape cfg.
