@@ -587,8 +587,10 @@ def run_ours(args):
 def run_batched_small(rs, torch, device, stream, n_fields=256, reps=5):
     """Many small maps (the 100-lens, 1000^2-ray configuration, seeds 2000 + k): one persistent graph
     launch against one rs_shoot call per field (each: list allocation, shoot, re-evaluation)."""
+    from paper_0905_2453_gb300 import tune
     specs = [ri.tiny_field(seed=2000 + k) for k in range(n_fields)]
     fields = [rs.Field.from_spec(s, stream) for s in specs]
+    shape = tune.autotune(fields[0], specs[0].grid, specs[0].window, stream=stream)[:4]  # the fields' own shape
     b = rs.Batch(fields, [s.grid for s in specs], [s.window for s in specs])
     counts_plain = [torch.zeros_like(c) for c in b.counts]
     oow_plain = torch.zeros(len(specs), dtype=torch.int64, device=device)
@@ -624,6 +626,7 @@ def run_batched_small(rs, torch, device, stream, n_fields=256, reps=5):
     for f in fields:
         f.close()
     return {"workload": f"{n_fields} fields of 100 equal-mass lenses, 1000^2 rays, 256^2 maps",
+            "launch_shape": "x".join(str(v) for v in shape),
             "maps_per_s": n_fields / t_batch, "plain_maps_per_s": n_fields / t_plain, "speedup": t_plain / t_batch,
             "interactions_per_s": inter / t_batch, "bitwise_equal": bool(same), "reps": reps}
 

@@ -318,9 +318,9 @@ int rs_magnification(const uint32_t* d_counts, const rs_ray_grid* g, const rs_wi
  * rs_batch_create_shaped -- as rs_batch_create with a launch shape per field: shapes = host int[4 *
  *   n_fields] of (block, rays per thread, lens tile, min_ctas) from rs_launch_configs (NULL: every field
  *   takes its mass mode's rs_set_launch_config shape).  The items of each (shape, mass mode) form one
- *   persistent launch of the graph; the counts are the same bits for every choice.  Persistent
- *   launches keep at most two CTAs per SM: a shape compiled for three runs as the shape with the
- *   same block, rays per thread and lens tile compiled for two (in that shape's launch).
+ *   persistent launch of the graph; the counts are the same bits for every choice.  A shape compiled
+ *   for three CTAs per SM runs in a batch as the shape with the same block, rays per thread and lens
+ *   tile compiled for two (in that shape's launch).
  * rs_batch_launch -- replay the plan's graph on `stream`.
  * rs_batch_destroy -- release the plan (synchronises first).  NULL is a no-op.
  * rs_shoot_batch -- create + launch + destroy in one call (synchronous).

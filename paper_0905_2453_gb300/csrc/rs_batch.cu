@@ -10,15 +10,17 @@ namespace {
 
 using namespace rsdev;
 
-// MINB resident CTAs per SM as the occupancy floor, as for the plain kernel, but at most two: the
+// MINB resident CTAs per SM as the occupancy floor, as for the plain kernel, except three: the
 // launch shapes compiled for three CTAs per SM (168 registers) run here as their two-CTA twins.
 // Inside the item loop the 168-register build of the tile body ran 1.6-3 % slower than the plain
 // kernel's (one-field batches of 1e3-1e5 lenses), whatever held the descriptor (shared memory,
 // kernel parameter, constant bank, global) and with the tile body out of line; at two CTAs per SM
-// (up to 255 registers) the batch kernel matches the plain one.  Counts do not depend on the shape.
+// (up to 255 registers) the batch kernel matches the plain one.  The four-CTA shape (4 rays per
+// thread, 128 registers) is for small fields, whose batches it speeds up by a third.  Counts do not
+// depend on the shape.
 template <int MINB>
 constexpr int batch_minb() {
-  return MINB > 2 ? 2 : MINB;
+  return MINB == 3 ? 2 : MINB;
 }
 template <int WARPS, int RPT, int TILE, bool MASS, int MINB>
 __global__ void __launch_bounds__(WARPS * 32, MINB)

@@ -140,4 +140,18 @@ __device__ __forceinline__ float4 deflect_ff_group(const FieldDev& f, float x1, 
   return make_float4(A1h, A1l, A2h, A2l);
 }
 
+// Eq. 6 and the pixel of a re-evaluated ray in float64: y = lam x - alpha with alpha1 = a.x + a.y,
+// alpha2 = a.z + a.w (float pairs, exact in float64), u = (y - lo) * sc.  True with pix = p2 * np0 + p1
+// (p = floor(u)) inside the window; false outside it (or for a ray on a lens: NaN compares false).
+__device__ __forceinline__ bool ff_map_bin(const ShootDesc& d, float x1, float x2, float4 a, size_t& pix) {
+  const double a1 = (double)a.x + (double)a.y, a2 = (double)a.z + (double)a.w;
+  const double y1 = __dsub_rn(__dmul_rn(d.f.lam1, (double)x1), a1);
+  const double y2 = __dsub_rn(__dmul_rn(d.f.lam2, (double)x2), a2);
+  const double u1 = __dmul_rn(__dsub_rn(y1, d.lo0), d.sc0);
+  const double u2 = __dmul_rn(__dsub_rn(y2, d.lo1), d.sc1);
+  if (!((u1 >= 0.0) && (u1 < (double)d.np0) && (u2 >= 0.0) && (u2 < (double)d.np1))) return false;
+  pix = (size_t)(int)floor(u2) * (size_t)d.np0 + (size_t)(int)floor(u1);
+  return true;
+}
+
 }  // namespace rsdev

@@ -23,7 +23,7 @@ constexpr int kTile = 256;
 #define RS_LAUNCH_SHAPES(X)                                                                           \
   X(0, 2, 8, 256, 2) X(1, 4, 4, 256, 2) X(2, 4, 8, 256, 2) X(3, 8, 4, 256, 1) X(4, 8, 8, 256, 1)   \
   X(5, 8, 6, 256, 1) X(6, 2, 8, 512, 2) X(7, 4, 4, 512, 2) X(8, 4, 8, 512, 2) X(9, 4, 8, 256, 3)   \
-  X(10, 4, 8, 512, 3)
+  X(10, 4, 8, 512, 3) X(11, 4, 4, 256, 4)
 
 struct KernelCfg {
   int block;     // threads per CTA (a multiple of 32)
@@ -59,10 +59,10 @@ inline int find_cfg(int block, int rpt, int tile, int min_ctas) {
   return -1;
 }
 
-// The shape a batch runs for launch shape cfg: batch kernels are built for at most two resident CTAs
+// The shape a batch runs for launch shape cfg: the batch kernel is not built for three resident CTAs
 // per SM (rs_batch.cu), so a three-CTA shape runs as its two-CTA twin, in the twin's group.
 inline int batch_cfg(int cfg) {
-  if (kCfgs[cfg].min_ctas <= 2) return cfg;
+  if (kCfgs[cfg].min_ctas != 3) return cfg;
   const int twin = find_cfg(kCfgs[cfg].block, kCfgs[cfg].rpt, kCfgs[cfg].tile, 2);
   return twin >= 0 ? twin : cfg;
 }

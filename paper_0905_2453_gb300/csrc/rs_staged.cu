@@ -148,15 +148,9 @@ __global__ void __launch_bounds__(128) recheck_bin_kernel(const ShootDesc d, con
     const int64_t i = r - jrel * d.n0;
     const float x1 = ray_coord(i, d.sp0, d.or0);
     const float x2 = ray_coord(d.j_begin + jrel, d.sp1, d.or1);
-    const float4 a = ff[e];
-    const double a1 = (double)a.x + (double)a.y, a2 = (double)a.z + (double)a.w;
-    const double y1 = __dsub_rn(__dmul_rn(d.f.lam1, (double)x1), a1);
-    const double y2 = __dsub_rn(__dmul_rn(d.f.lam2, (double)x2), a2);
-    const double u1 = __dmul_rn(__dsub_rn(y1, d.lo0), d.sc0);
-    const double u2 = __dmul_rn(__dsub_rn(y2, d.lo1), d.sc1);
-    const bool inwin = (u1 >= 0.0) && (u1 < (double)d.np0) && (u2 >= 0.0) && (u2 < (double)d.np1);
-    if (inwin) {
-      atomicAdd(d.counts + (size_t)(int)floor(u2) * (size_t)d.np0 + (size_t)(int)floor(u1), 1u);
+    size_t pix = 0;
+    if (ff_map_bin(d, x1, x2, ff[e], pix)) {
+      atomicAdd(d.counts + pix, 1u);
     } else if (d.oow != nullptr) {
       atomicAdd(d.oow, 1ull);
     }

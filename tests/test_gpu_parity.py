@@ -251,6 +251,42 @@ def test_magnification_matches_oracle():
     assert np.allclose(mu, mu_ref, rtol=2e-7, atol=0)
 
 
+@pytest.mark.parametrize("n_lens,mass,side", [(100, "equal", 1024), (700, "salpeter", 768), (1024, "equal", 768)])
+def test_small_field_maps_agree_across_shoot_paths(n_lens, mass, side):
+    """Certified maps of small fields from rs_shoot (stream-ordered list), rs_shoot_rows_noalloc (static list)
+    and rs_shoot_staged (lens partitions of 256, re-evaluated partition by partition) agree bit for bit
+    (and the 100-lens one with the oracle's)."""
+    m = rs()
+    spec = ri.disc_field(f"paths-{n_lens}", n_lens, 0.45, 0.05, 0.3, side, 256, seed=11, mass=mass)
+    n1 = int(spec.grid.n[1])
+    w = spec.window
+    cuts = list(range(0, n_lens, 256)) + [n_lens]
+    f = m.Field.from_spec(spec)
+    parts = [m.Field(spec.lens_xy[a:b], None if spec.masses is None else spec.masses[a:b], spec.kappa_c,
+                     spec.gamma) for a, b in zip(cuts, cuts[1:])]
+    try:
+        maps = []
+        for call in (lambda c, o: m.rs_shoot(f.handle, spec.grid, w, c, o),
+                     lambda c, o: m.rs_shoot_rows_noalloc(f.handle, spec.grid, 0, n1, w, c, o),
+                     lambda c, o: m.rs_shoot_staged([p.handle for p in parts], spec.grid, 0, n1, w, c, o)):
+            c = torch.zeros((int(w.npix[1]), int(w.npix[0])), dtype=torch.int32, device=dev())
+            o = torch.zeros(1, dtype=torch.int64, device=dev())
+            call(c, o)
+            torch.cuda.synchronize()
+            maps.append((c.cpu().numpy().view(np.uint32), int(o.item())))
+        assert f.status() == m.RS_OK and all(p.status() == m.RS_OK for p in parts)
+        for k in (1, 2):
+            assert np.array_equal(maps[0][0], maps[k][0]) and maps[0][1] == maps[k][1], k
+        assert int(maps[0][0].sum()) + maps[0][1] == spec.grid.n_rays
+        if n_lens == 100:
+            ref, oref = oracle.shoot_field(spec)
+            assert np.array_equal(maps[0][0], ref) and maps[0][1] == oref
+    finally:
+        f.close()
+        for p in parts:
+            p.close()
+
+
 def test_batch_equals_plain_launches_bitwise():
     m = rs()
     specs = ri.batch_fields(n_fields=6, ray_scale=0.125)
