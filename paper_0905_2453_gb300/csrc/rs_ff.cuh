@@ -140,6 +140,64 @@ __device__ __forceinline__ float4 deflect_ff_group(const FieldDev& f, float x1, 
   return make_float4(A1h, A1l, A2h, A2l);
 }
 
+// deflect_ff_group for R rays of one field in one pass over the lenses: every lens a lane loads serves
+// all R rays, and each ray's terms, shuffle tree and warp order are those of deflect_ff_group, so each
+// ray gets the same bits as alone.  red: W * R entries of shared memory.  Thread 0 of the group
+// returns the R results in out.
+template <bool MASS, int R>
+__device__ __forceinline__ void deflect_ff_group_rays(const FieldDev& f, const float (&x1)[R], const float (&x2)[R],
+                                                      int W, int w, float4* red, float4 (&out)[R]) {
+  const int lane = threadIdx.x & 31;
+  const int stride = 32 * W, n = f.n_lens;
+  float A1h[R], A1l[R], A2h[R], A2l[R];
+#pragma unroll
+  for (int r = 0; r < R; ++r) A1h[r] = A1l[r] = A2h[r] = A2l[r] = 0.f;
+  int l = w * 32 + lane;
+  for (; l + stride < n; l += 2 * stride) {  // two lenses in flight; each ray still adds them in lens order
+    const float4 L0 = __ldg(f.lens4 + l), L1 = __ldg(f.lens4 + l + stride);
+    const float m0 = MASS ? __ldg(f.mass2 + l).x : 0.f, m1 = MASS ? __ldg(f.mass2 + l + stride).x : 0.f;
+#pragma unroll
+    for (int r = 0; r < R; ++r) lens_term_ff_at<MASS>(L0, m0, x1[r], x2[r], A1h[r], A1l[r], A2h[r], A2l[r]);
+#pragma unroll
+    for (int r = 0; r < R; ++r) lens_term_ff_at<MASS>(L1, m1, x1[r], x2[r], A1h[r], A1l[r], A2h[r], A2l[r]);
+  }
+  if (l < n) {
+    const float4 L0 = __ldg(f.lens4 + l);
+    const float m0 = MASS ? __ldg(f.mass2 + l).x : 0.f;
+#pragma unroll
+    for (int r = 0; r < R; ++r) lens_term_ff_at<MASS>(L0, m0, x1[r], x2[r], A1h[r], A1l[r], A2h[r], A2l[r]);
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const float b1h = __shfl_down_sync(0xffffffffu, A1h[r], off);
+      const float b1l = __shfl_down_sync(0xffffffffu, A1l[r], off);
+      const float b2h = __shfl_down_sync(0xffffffffu, A2h[r], off);
+      const float b2l = __shfl_down_sync(0xffffffffu, A2l[r], off);
+      ff_add(A1h[r], A1l[r], b1h, b1l);
+      ff_add(A2h[r], A2l[r], b2h, b2l);
+    }
+  }
+  if (W > 1) {
+    if (lane == 0)
+#pragma unroll
+      for (int r = 0; r < R; ++r) red[w * R + r] = make_float4(A1h[r], A1l[r], A2h[r], A2l[r]);
+    __syncthreads();
+    if (w == 0 && lane == 0)
+      for (int k = 1; k < W; ++k)
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+          const float4 o = red[k * R + r];
+          ff_add(A1h[r], A1l[r], o.x, o.y);
+          ff_add(A2h[r], A2l[r], o.z, o.w);
+        }
+    __syncthreads();  // red is free again
+  }
+#pragma unroll
+  for (int r = 0; r < R; ++r) out[r] = make_float4(A1h[r], A1l[r], A2h[r], A2l[r]);
+}
+
 // Eq. 6 and the pixel of a re-evaluated ray in float64: y = lam x - alpha with alpha1 = a.x + a.y,
 // alpha2 = a.z + a.w (float pairs, exact in float64), u = (y - lo) * sc.  True with pix = p2 * np0 + p1
 // (p = floor(u)) inside the window; false outside it (or for a ray on a lens: NaN compares false).

@@ -65,6 +65,62 @@ __global__ void __launch_bounds__(32 * ff_cta_warps<W>()) recheck_kernel(const S
   }
 }
 
+// Listed rays of one field with W > 1 warps per ray, up to kRaysPerPass at a time: each ray of a
+// field this large streams the whole lens array, so one pass serves several (one field's lenses from
+// DRAM once per pass instead of once per ray).  CTA b takes entries [n b / grid, n (b + 1) / grid)
+// of the list; the per-ray arithmetic is recheck_kernel's, so the counts are the same bits.
+constexpr int kRaysPerPass = 4;
+
+template <int W, int R>
+__device__ __forceinline__ void recheck_rays(const ShootDesc& d, const uint2* __restrict__ list, unsigned int e,
+                                             float4* red) {
+  float x1[R], x2[R];
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const int64_t ray = (int64_t)list[e + r].y;
+    const int64_t jrel = ray / d.n0;
+    x1[r] = ray_coord(ray - jrel * d.n0, d.sp0, d.or0);
+    x2[r] = ray_coord(d.j_begin + jrel, d.sp1, d.or1);
+  }
+  float4 a[R];
+  const int w = (int)(threadIdx.x >> 5);
+  if (d.f.has_mass)
+    deflect_ff_group_rays<true, R>(d.f, x1, x2, W, w, red, a);
+  else
+    deflect_ff_group_rays<false, R>(d.f, x1, x2, W, w, red, a);
+  if (threadIdx.x != 0) return;
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    size_t pix = 0;
+    if (ff_map_bin(d, x1[r], x2[r], a[r], pix))
+      atomicAdd(d.counts + pix, 1u);
+    else if (d.oow != nullptr)
+      atomicAdd(d.oow, 1ull);
+  }
+}
+
+template <int W>
+__global__ void __launch_bounds__(32 * W) recheck_field_kernel(const ShootDesc d, const uint2* __restrict__ list,
+                                                               const unsigned int* __restrict__ count,
+                                                               unsigned int cap) {
+  __shared__ float4 red[W * kRaysPerPass];
+  const uint64_t n = min(*count, cap);
+  const unsigned int lo = (unsigned int)(n * blockIdx.x / gridDim.x);
+  const unsigned int hi = (unsigned int)(n * (blockIdx.x + 1) / gridDim.x);
+  for (unsigned int e = lo; e < hi;) {  // CTA-uniform
+    const unsigned int k = min(hi - e, (unsigned int)kRaysPerPass);
+    if (k == 4)
+      recheck_rays<W, 4>(d, list, e, red);
+    else if (k == 3)
+      recheck_rays<W, 3>(d, list, e, red);
+    else if (k == 2)
+      recheck_rays<W, 2>(d, list, e, red);
+    else
+      recheck_rays<W, 1>(d, list, e, red);
+    e += k;
+  }
+}
+
 // Listed rays of rs_trace_certified: the same evaluation as the re-evaluation above.
 template <int W>
 __global__ void __launch_bounds__(32 * ff_cta_warps<W>()) trace_ff_kernel(const FieldDev f, double or0, double or1,
@@ -112,8 +168,15 @@ cudaError_t launch_recheck(const rsdev::ShootDesc* single, const rsdev::ShootDes
   const bool large = single == nullptr || rsdev::ff_warps(single->f.n_lens) > 1;
   cudaError_t e = cudaSuccess;
   if (small) e = launch_recheck_w<1>(single, descs, list, count, cap, grid, s);
-  if (e == cudaSuccess && large)
-    e = launch_recheck_w<rsdev::kFfWarps>(single, descs, list, count, cap, std::max(1, grid / 4), s);
+  if (e == cudaSuccess && large) {
+    if (single != nullptr) {  // one field: several listed rays per pass over its lenses
+      recheck_field_kernel<rsdev::kFfWarps><<<std::max(1, grid / 4), 32 * rsdev::kFfWarps, 0, s>>>(*single, list,
+                                                                                                 count, cap);
+      e = cudaGetLastError();
+    } else {
+      e = launch_recheck_w<rsdev::kFfWarps>(single, descs, list, count, cap, std::max(1, grid / 4), s);
+    }
+  }
   return e;
 }
 

@@ -287,6 +287,31 @@ def test_small_field_maps_agree_across_shoot_paths(n_lens, mass, side):
             p.close()
 
 
+@pytest.mark.parametrize("mass", ["equal", "salpeter"])
+def test_large_field_re_evaluation_several_rays_per_pass_bitwise(mass):
+    """Above 2^16 lenses the listed rays of one field are re-evaluated several per pass over the lenses
+    (rs_shoot) and one per pass in a batch: each ray's float-float sum has the same order either way, so the
+    maps are the same bits."""
+    m = rs()
+    spec = ri.disc_field(f"rays-per-pass-{mass}", 70_000, 0.45, 0.05, 0.3, 1024, 256, seed=12, mass=mass)
+    f = m.Field.from_spec(spec)
+    try:
+        assert (spec.n_lens > 1 << 16) and m.rs_get_certified_binning()
+        w = spec.window
+        c = torch.zeros((int(w.npix[1]), int(w.npix[0])), dtype=torch.int32, device=dev())
+        o = torch.zeros(1, dtype=torch.int64, device=dev())
+        m.rs_shoot(f.handle, spec.grid, w, c, o)
+        b = m.Batch([f], [spec.grid], [w])
+        b.launch()
+        torch.cuda.synchronize()
+        assert f.status() == m.RS_OK
+        assert torch.equal(b.counts[0], c) and int(b.out_of_window[0].item()) == int(o.item())
+        assert int(c.sum().item()) + int(o.item()) == spec.grid.n_rays
+        b.close()
+    finally:
+        f.close()
+
+
 def test_batch_equals_plain_launches_bitwise():
     m = rs()
     specs = ri.batch_fields(n_fields=6, ray_scale=0.125)
