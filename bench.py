@@ -310,6 +310,17 @@ def headline_rows(rs, spec, field, sms, stream, launch_shape=None):
     return r0, r0 + unit, shape, note
 
 
+def tune_for(rs, spec, stream):
+    """Set (and return) the tuner's launch shape for spec's field, mass mode and grid (cached after the first
+    time)."""
+    from paper_0905_2453_gb300 import tune
+    f = rs.Field.from_spec(spec, stream)
+    try:
+        return tuple(tune.autotune(f, spec.grid, spec.window, stream=stream)[:4])
+    finally:
+        f.close()
+
+
 def parse_shape(text):
     """'128x8x512x2' (threads x rays per thread x lens tile x resident CTAs per SM; defaults 256 and 2)
     -> (128, 8, 512, 2)."""
@@ -507,6 +518,10 @@ def run_ours(args):
     if not args.no_light_curves and world == 1:
         light = run_light_curves(rs, torch, device, stream, cpu_baseline=not args.no_cpu_baseline)
 
+    # the zoom, time-series and partition sections shoot the 1e4-lens field: its own tuned shape
+    if world == 1 and not args.launch_shape and not (args.no_zoom and args.no_frames and args.no_staged):
+        tune_for(rs, side, stream)
+
     # ---------------- zoom into the 1e4-lens map (culled shooting) vs plain shooting of the finer grid
     zoom = None
     if not args.no_zoom and world == 1:
@@ -590,6 +605,7 @@ def run_batched_small(rs, torch, device, stream, n_fields=256, reps=5):
     from paper_0905_2453_gb300 import tune
     specs = [ri.tiny_field(seed=2000 + k) for k in range(n_fields)]
     fields = [rs.Field.from_spec(s, stream) for s in specs]
+    saved = rs.rs_get_launch_config(False)  # put back afterwards: later sections shoot other fields
     shape = tune.autotune(fields[0], specs[0].grid, specs[0].window, stream=stream)[:4]  # the fields' own shape
     b = rs.Batch(fields, [s.grid for s in specs], [s.window for s in specs])
     counts_plain = [torch.zeros_like(c) for c in b.counts]
@@ -625,6 +641,7 @@ def run_batched_small(rs, torch, device, stream, n_fields=256, reps=5):
     b.close()
     for f in fields:
         f.close()
+    rs.rs_set_launch_config(False, *saved)
     return {"workload": f"{n_fields} fields of 100 equal-mass lenses, 1000^2 rays, 256^2 maps",
             "launch_shape": "x".join(str(v) for v in shape),
             "maps_per_s": n_fields / t_batch, "plain_maps_per_s": n_fields / t_plain, "speedup": t_plain / t_batch,
