@@ -294,11 +294,7 @@ def headline_rows(rs, spec, field, sms, stream, launch_shape=None):
         occ = rs.rs_launch_occupancy(weighted, *sh)
         return tune.wave_rows(n0, sh[0], sh[1], sms, occ), occ
 
-    best = rates.get("x".join(str(v) for v in shape))
-    cands = [shape]
-    if best:
-        cands += [parse_shape(k) for k, v in rates.items() if v >= (1 - STEP_RATE_SLACK) * best]
-    shape = min(cands, key=lambda sh: (unit_of(sh)[0], -rates.get("x".join(str(v) for v in sh), 0.0)))
+    shape = choose_step_shape(shape, rates, lambda sh: unit_of(sh)[0])
     b, r = shape[0], shape[1]
     rs.rs_set_launch_config(weighted, *shape)
     unit, occ = unit_of(shape)
@@ -308,6 +304,18 @@ def headline_rows(rs, spec, field, sms, stream, launch_shape=None):
     note = (f"central rows [{r0}, {r0 + unit}) of the {n0} x {n1} grid: {ctas} CTAs of {b} threads = "
             f"{ctas // (occ * sms)} whole wave(s) of {occ} CTAs x {sms} SMs")
     return r0, r0 + unit, shape, note
+
+
+def choose_step_shape(best_shape, rates, unit_rows, slack=STEP_RATE_SLACK):
+    """Among best_shape and the shapes rated ({"BxRxTxM": interactions/s}) within slack of it, the one whose
+    whole-wave unit (unit_rows(shape)) takes the fewest rows; equal units go to the higher rate."""
+    def name(sh):
+        return "x".join(str(v) for v in sh)
+    best = rates.get(name(best_shape))
+    cands = [tuple(best_shape)]
+    if best:
+        cands += [parse_shape(k) for k, v in rates.items() if v >= (1 - slack) * best]
+    return min(cands, key=lambda sh: (unit_rows(sh), -rates.get(name(sh), 0.0)))
 
 
 def tune_for(rs, spec, stream):
