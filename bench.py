@@ -15,8 +15,10 @@ sub-objects with their own roofline.
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload NAME]
 
 --impl reference times the FP64 CPU oracle (the reference arm) on bounded samples of
-the same workload.  Under torchrun every rank shoots its own lens realisation of the
-workload (weak scaling, no collective on the data path).
+the same workload.  Under torchrun (--mode sharded, the default) every rank shoots one
+whole-wave block of rows of the same map and the count maps are summed with one NCCL
+all_reduce per step (weak scaling: the rows per rank stay fixed); --mode realisations
+gives every rank its own lens realisation instead, with no collective on the data path.
 """
 from __future__ import annotations
 
