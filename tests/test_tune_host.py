@@ -35,3 +35,41 @@ def test_wave_rows_at_other_occupancies(occ):
             assert unit % warps == 0 and ((unit // warps) * cpr) % (occ * 152) == 0
     # the 1e8-lens grid: 64-thread CTAs four to an SM fill one wave with 38 rows
     assert wave_rows(8192, 64, 8, 152, 4) == 38
+
+
+class _FakeField:
+    def __init__(self, n_lens, has_mass):
+        self.n_lens, self.has_mass = n_lens, has_mass
+
+    def info(self):
+        return self.n_lens, self.has_mass
+
+
+class _FakeGrid:
+    def __init__(self, side):
+        self.n = (side, side)
+
+
+def test_batch_shapes_tune_the_largest_field_of_each_mass_mode_and_lens_bucket(monkeypatch):
+    """Fields are grouped by (mass mode, lens-count bucket); the field with the most rays of each group is tuned
+    and its shape serves the group; the launch configuration of both mass modes is put back afterwards."""
+    import paper_0905_2453_gb300 as rs
+    from paper_0905_2453_gb300 import tune
+    tuned = []
+
+    def fake_autotune(field, grid, window, **kw):
+        tuned.append((field.n_lens, field.has_mass, grid.n[0]))
+        shape = (128, 8, 512, 3) if field.n_lens > 5000 else (128, 4, 256, 4)
+        rs.rs_set_launch_config(field.has_mass, *shape)  # as the tuner does
+        return (*shape, {})
+
+    monkeypatch.setattr(tune, "autotune", fake_autotune)
+    before = {m: rs.rs_get_launch_config(m) for m in (False, True)}
+    fields = [_FakeField(100, False), _FakeField(110, False), _FakeField(100, True), _FakeField(10000, True),
+              _FakeField(11000, True), _FakeField(100, False)]
+    grids = [_FakeGrid(s) for s in (1024, 2048, 1024, 1024, 4096, 512)]
+    shapes = tune.batch_shapes(fields, grids, [None] * len(fields))
+    # groups: unit masses ~100 lenses (fields 0, 1, 5), masses ~100 (2), masses ~1e4 (3, 4)
+    assert sorted(tuned) == sorted([(110, False, 2048), (100, True, 1024), (11000, True, 4096)])
+    assert shapes == [(128, 4, 256, 4)] * 3 + [(128, 8, 512, 3)] * 2 + [(128, 4, 256, 4)]
+    assert {m: rs.rs_get_launch_config(m) for m in (False, True)} == before
