@@ -395,6 +395,13 @@ def run_ours(args):
     field = rs.Field.from_spec(spec, stream)
     sms, max_mhz = peaks(local)
     r0, r1, shape, rows_note = headline_rows(rs, spec, field, sms, stream, args.launch_shape)
+    if dist is not None and sharded:
+        # rank 0's rows and launch shape hold on every rank: the ranks' blocks must tile one block of the map
+        # (each rank's tuner times its own GPU and could, in a close call, rank two shapes the other way round)
+        chosen = [(r0, r1, tuple(shape), rows_note)]
+        dist.broadcast_object_list(chosen, src=0)
+        r0, r1, shape, rows_note = chosen[0]
+        rs.rs_set_launch_config(field.info()[1], *shape)
     from paper_0905_2453_gb300 import tune
     from paper_0905_2453_gb300.shard import device_row_shooter, shoot_sharded
     rates_headline = {} if args.launch_shape else tune.shape_rates(field, spec.grid)
